@@ -1,0 +1,59 @@
+"""Small configurations and helpers shared by the tests."""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from paper_2602_15883_b300 import synth
+
+
+def tiny(kind: str, width=4, depth=2, **kw) -> dict:
+    """Tiny multi-net configurations for exhaustive derivative checks."""
+    if kind == "2s":      # steady 2D, 2 x 2 nets
+        cfg = synth.config("kovasznay", splits=[2, 2, 1, 1], lo=[-0.5, -0.5, 0, 0], hi=[1.0, 1.5, 0, 0],
+                           anchor=[0.1, 0.2, 0.0])
+    elif kind == "2u":    # unsteady 2D, 2 x 1 x 2 nets
+        cfg = synth.config("tgv", splits=[2, 1, 2, 1], anchor=[1.0, 2.0, 0.0])
+    elif kind == "3u":    # unsteady 3D, 1 x 2 x 1 x 2 nets
+        cfg = synth.config("beltrami32", splits=[1, 2, 1, 2], anchor=[0.3, -0.4, 0.2])
+    elif kind == "3s":    # steady 3D (d_in = 3 without time), 2 x 1 x 1 nets
+        cfg = synth.config("beltrami32", unsteady=0, splits=[2, 1, 1, 1], anchor=[-0.2, 0.1, 0.3])
+    else:
+        raise ValueError(kind)
+    cfg.update(width=width, depth=depth, nu=0.37, lambda_obs=1.3, lambda_pde=0.7, lambda_gh_u=0.45,
+               lambda_gh_p_space=0.8, lambda_gh_p_time=0.55, comp_w=[1.0, 2.5, 0.6])
+    cfg.update(kw)
+    return cfg
+
+
+def tiny_problem(cfg, seed=0, n_res=5, n_obs=4, n_face=3, bias_std=0.3):
+    nn = synth.n_nets(cfg)
+    nf = len(synth.faces(cfg))
+    rng = np.random.default_rng(seed + 100)
+    res = rng.integers(max(n_res - 2, 0), n_res + 3, nn)
+    obs = rng.integers(max(n_obs - 2, 0), n_obs + 3, nn)
+    fc = rng.integers(max(n_face - 1, 0), n_face + 2, nf)
+    return synth.make_problem(cfg, seed=seed, res_counts=res, obs_counts=obs, face_counts=fc,
+                              bias_std=bias_std)
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    d = np.linalg.norm((a - b).ravel())
+    n = np.linalg.norm(b.ravel())
+    return d / n if n > 0 else d
+
+
+def net_params(pb, k):
+    npar = synth.n_params_net(pb.cfg)
+    return np.asarray(pb.theta0[k * npar:(k + 1) * npar], np.float64)
+
+
+def random_points_around(cfg, k, n, seed=0, pad=0.2):
+    """Points in net k's box enlarged by ``pad`` of its size (outside allowed)."""
+    lo, hi = synth.net_box(cfg, k)
+    rng = np.random.default_rng(seed)
+    span = hi - lo
+    return lo - pad * span + (1 + 2 * pad) * span * rng.uniform(size=(n, lo.size))
