@@ -1,0 +1,308 @@
+"""Benchmark: residual points per second of one full training step of all
+subdomain networks (grouped jet forward + residuals + losses + reverse pass +
+Adam) on synthetic analytic-flow data.
+
+Default workload: the 2D unsteady Taylor-Green vortex, 4 x 4 x 2 = 32 nets
+of 6 x 64 tanh, 8,192 residual + 1,024 noisy velocity points per net and 512
+points per shared face (64 faces).  --workload picks another configuration.
+
+Prints one JSON line (rank 0).  `value` is device-timed with CUDA events
+around each step, L2 flushed (a 512 MiB buffer is written) between steps;
+`e2e` is the same metric through the C ABI with the residual points copied
+from pinned host memory and the loss record copied back every step.
+--impl reference times the FP64 CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2602_15883_b300 import synth  # noqa: E402
+
+METRIC = "residual-points/s per train step (fwd+jets+bwd+Adam)"
+
+
+def flops_per_point(cfg, jets=True):
+    """Algorithmic FLOPs per point of forward + reverse (3x the forward).
+
+    Forward with jets: 2*C*W^2*(L-1) (hidden contractions) + 2*W*(d_in + C*d_out)
+    (first and output maps); value-only: the same with C = 1."""
+    W, L = cfg["width"], cfg["depth"]
+    din, dout = synth.d_in(cfg), synth.d_out(cfg)
+    C = din + 2 if jets else 1
+    return 3 * (2 * C * W * W * (L - 1) + 2 * W * (din + C * dout))
+
+
+def step_flops(cfg, pb):
+    n_val = int(pb.obs_counts.sum()) + 2 * int(pb.face_counts.sum())
+    return flops_per_point(cfg, True) * pb.n_res + flops_per_point(cfg, False) * n_val
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during timing."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.p is None:
+            return
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                self.rows.append(f)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows),
+                "power_w_max": max(float(r[3]) for r in self.rows) if self.rows else None}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def fp32_alu_peak_tflops(sm_mhz):
+    # 148 SMs x 128 FP32 lanes x 2 FLOP per FFMA x clock
+    return 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def make_problem(args, rank=0):
+    cfg = synth.config(args.workload)
+    pb = synth.make_problem(cfg, seed=args.seed + rank)
+    return cfg, pb
+
+
+def cpu_baseline(cfg, pb, budget_s=15.0):
+    """The FP64 oracle on a bounded sample: every net keeps the same
+    architecture, faces and structure, with 1/f of its points."""
+    import oracle
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    f = 64
+    while True:
+        sub = synth.make_problem(cfg, seed=pb.seed,
+                                 res_counts=np.maximum(pb.res_counts // f, 1),
+                                 obs_counts=np.maximum(pb.obs_counts // f, 1),
+                                 face_counts=np.maximum(pb.face_counts // f, 1))
+        ora = oracle.Oracle(cfg, sub)
+        th = np.asarray(sub.theta0, np.float64)
+        t0 = time.perf_counter()
+        ora.step(th, np.zeros_like(th), np.zeros_like(th), 0)
+        dt = time.perf_counter() - t0
+        if dt > 1.0 or f == 1:
+            break
+        f = max(1, f // 8)
+    reps = max(1, int(budget_s / max(dt, 1e-3)))
+    reps = min(reps, 20)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        ora.step(th, np.zeros_like(th), np.zeros_like(th), 0)
+    dt = (time.perf_counter() - t0) / reps
+    return {"value": sub.n_res / dt, "unit": "residual-points/s", "cores": cores, "kind": "oracle",
+            "sample": f"all {synth.n_nets(cfg)} nets with 1/{f} of their points ({sub.n_res} residual pts), "
+                      f"FP64 loss+gradient+Adam, {reps} steps"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfg, pb = make_problem(args)
+    cb = cpu_baseline(cfg, pb, budget_s=max(5.0, 2.0 * args.steps))
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "residual-points/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n_nets": synth.n_nets(cfg), "residual_points": pb.n_res},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "residual-points/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def plain_form_rate(cfg, pb, steps=2):
+    """Plain form (per-net eager PyTorch autograd loop, FP32) on the GPU."""
+    import torch
+    from baseline.plain_form import PlainForm
+    pf = PlainForm(pb, device="cuda", dtype=torch.float32)
+    pf.step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        pf.step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    return {"value": pb.n_res / dt, "unit": "residual-points/s", "ms_per_step": dt * 1e3,
+            "kind": "per-net eager PyTorch autograd double backward + torch.optim.Adam, FP32"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="tgv", choices=list(synth.CONFIGS))
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-baselines", action="store_true", help="skip the plain-form and CPU legs")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2602_15883_b300 import build
+    build.build()
+    from paper_2602_15883_b300.binding import POINTS_RESIDUAL, Dpinn
+
+    cfg, pb = make_problem(args, rank)
+    cfg["device"] = local
+    d = Dpinn(cfg)
+    d.set_problem(pb)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    d.step(args.warmup, stream)
+    d.loss()
+    # ---- device-timed region
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            starts[i].record(stream)
+            d.step(1, stream)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
+    loss = d.loss()
+    assert np.all(np.isfinite(loss)), "non-finite loss"
+    step_ms = float(np.median(ms))
+    total_ms = float(ms.sum())
+    if dist:
+        t = torch.tensor([total_ms, step_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, step_ms = float(t[0]), float(t[1])
+    value = world * pb.n_res * args.steps / (total_ms / 1e3)
+
+    # ---- per-kernel timing of the same kernels (events on this stream)
+    kt = {}
+    for i in range(max(3, min(args.steps, 10))):
+        flush.fill_(0.0)
+        for k, v in d.step_timed(stream).items():
+            kt.setdefault(k, []).append(v)
+    kms = {k: float(np.mean(v)) for k, v in kt.items()}
+    jet_ms = kms.get("train_jet", float("nan"))
+    clocks = clk.summary()
+    pk, pk_kind = peaks()
+    sm_mhz = float(pk.get("sm_max_mhz", 2032.0))
+    peak = fp32_alu_peak_tflops(sm_mhz)
+    jet_flops = flops_per_point(cfg, True) * pb.n_res
+    achieved = jet_flops / (jet_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_pinn train (jets)",
+                "peak_source": f"148 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (max SM clock, {pk_kind})",
+                "kernel_ms": kms}
+
+    # ---- end to end through the C ABI with host buffers
+    pinned = torch.from_numpy(np.ascontiguousarray(pb.res_pts, np.float32)).pin_memory()
+    counts = pb.res_counts
+    out = np.zeros((d.n_nets, 6), np.float32)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(3, args.steps // 2)
+    for _ in range(e2e_steps):
+        d.set_points(POINTS_RESIDUAL, pinned, counts)
+        d.step(1, stream)
+        out = d.loss()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t[0])
+    e2e = {"value": world * pb.n_res * e2e_steps / e2e_s, "unit": "residual-points/s",
+           "h2d_bytes_per_step": int(pinned.numel() * 4), "d2h_bytes_per_step": int(out.nbytes)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "residual-points/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": args.workload, "n_nets": d.n_nets, "width": cfg["width"],
+                           "depth": cfg["depth"], "residual_points": pb.n_res,
+                           "obs_points": int(pb.obs_counts.sum()), "face_points": int(pb.face_counts.sum()),
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                           "l2": "flushed between steps (512 MiB write)"},
+                "roofline": roofline, "clocks": clocks, "e2e": e2e,
+                "gpu_launches": d.launches_per_step * args.steps,
+                "step_gflop": step_flops(cfg, pb) / 1e9}
+        if not args.no_baselines:
+            try:
+                line["plain_form"] = plain_form_rate(cfg, pb)
+            except Exception as ex:   # reported, not fatal
+                line["plain_form"] = {"error": str(ex)[:200]}
+            line["cpu_baseline"] = cpu_baseline(cfg, pb)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

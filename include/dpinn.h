@@ -1,0 +1,203 @@
+/*
+ * dpinn.h - C ABI of libdpinn, a single-GPU (B300, sm_103a) implementation of
+ * one training step of the domain-decomposed physics-informed neural network
+ * of arXiv 2602.15883 ("Distributed physics-informed neural networks via
+ * domain decomposition for fast flow reconstruction"), and of queries on the
+ * trained ensemble.
+ *
+ * Method (paper section / equation numbers count numbered equations in order):
+ *   - The space-time box is split into K x M disjoint cells, one independent
+ *     fully connected tanh network ("local expert") per cell, mapping
+ *     (x, [t]) -> (u, [w], p)                                     Sec. 2.2
+ *   - Per net, the local objective (Eq. (16)):
+ *       L = l_obs L_obs + l_PDE L_PDE + l_gh_u L_gh_u
+ *           + l_space L_gh_p^space + l_time L_gh_p^time
+ *     with L_obs (Eq. (3)), L_PDE over the incompressible Navier-Stokes
+ *     residuals (Eqs. (5)-(10), 1/Re = nu), the ghost consistency terms
+ *     (Eqs. (13)-(14)) against the neighbours' predictions held constant,
+ *     the anchor normalisation of the pressure a master sends
+ *     (p~ = p(x,t) - p(x_anc,t), Eq. (15)), and l_space = 0 for masters.
+ *   - One step (Algorithm 1 with I_comm = 1): neighbour messages at the
+ *     current parameters, losses and gradients of every net, then Adam.
+ *
+ * Readings of the paper used here (where it is silent):
+ *   - inputs are mapped from the net's own cell to [-1, 1];
+ *   - the ghost set of a net is the union of the points on its shared faces
+ *     (one point set per face, used by both sides); L_gh_* of net A divide by
+ *     the number of points on all of A's faces, split by face type;
+ *   - the anchor is evaluated at each ghost point's own time;
+ *   - Adam follows PyTorch (no weight decay); optional per-net clipping
+ *     g *= min(1, clip / (||g||_2 + 1e-6)).
+ *
+ * Conventions
+ *   - Every call returns an int status: DPINN_OK (0) or a negative
+ *     DPINN_ERR_* code; dpinn_last_error() gives a message.  No C++ exception
+ *     crosses the ABI.
+ *   - "device pointer" = memory on the handle's GPU; "host pointer" = CPU
+ *     memory (pinned or pageable).  Calls that copy accept either (the copy
+ *     direction is inferred from the pointer, unified addressing).
+ *   - Coordinates are float32 [n][d_in], spatial axes first, time last
+ *     (d_in = d_space + unsteady).  Outputs are (u, v, [w], p): d_out =
+ *     d_space + 1.
+ *   - Nets are numbered over the cell grid with axis 0 fastest:
+ *     net = sum_a cell_a * stride_a, stride_0 = 1, stride_a = stride_{a-1} *
+ *     splits_{a-1}.  Cell a of a coordinate is decided in float32:
+ *     floor((x - (float)lo_a) * (float)(splits_a / (hi_a - lo_a))) clamped to
+ *     [0, splits_a - 1] (half-open cells, the last one closed); x outside
+ *     [(float)lo_a, (float)hi_a] is outside the domain.
+ *   - Faces join net k and k + stride_a for every cell with cell_a <
+ *     splits_a - 1; they are numbered axis by axis (ascending), then by k.
+ *     A face along the time axis is temporal, all others are spatial.
+ *   - Masters are the nets whose spatial cell contains x_anc (one per time
+ *     slab).  x_anc is taken at float32 precision.
+ *   - Per-net parameter block (the order of get/set_state): for each affine
+ *     map l = 0..L (L = depth hidden layers, width W), the weight [out][in]
+ *     row-major then the bias [out]; in_0 = d_in, out_L = d_out.
+ *   - Loss record of a net: {L_obs, L_PDE, L_gh_u, L_gh_p^space,
+ *     L_gh_p^time, L_total} (the spatial pressure term of a master is
+ *     reported although its weight is 0).
+ */
+#ifndef DPINN_H
+#define DPINN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dpinn dpinn_t;
+/* A cudaStream_t, passed as an opaque pointer (NULL = the legacy stream). */
+typedef void* dpinn_stream_t;
+
+enum {
+  DPINN_OK = 0,
+  DPINN_ERR_INVALID_ARG = -1,
+  DPINN_ERR_OOM = -2,
+  DPINN_ERR_CUDA = -3,
+  DPINN_ERR_NONFINITE = -4,
+  DPINN_ERR_TIMEOUT = -5,
+  DPINN_ERR_BUSY = -6,
+  DPINN_ERR_STATE = -7
+};
+
+enum { DPINN_POINTS_RESIDUAL = 0, DPINN_POINTS_OBS = 1, DPINN_POINTS_FACE = 2 };
+enum { DPINN_ACT_TANH = 0 };
+enum { DPINN_PREC_FP32 = 0 };
+
+typedef struct dpinn_config {
+  int d_space;            /* 2 or 3 */
+  int unsteady;           /* 1: time is an input */
+  double lo[4], hi[4];    /* global box per input axis */
+  int splits[4];          /* cells per input axis */
+  int depth;              /* hidden layers L (2..16) */
+  int width;              /* neurons per hidden layer: 32, 64 or 128 */
+  int activation;         /* DPINN_ACT_TANH */
+  double nu;              /* kinematic viscosity = 1/Re */
+  double anchor_x[3];     /* x_anc (spatial) */
+  double p_ref;           /* pressure value assigned to x_anc in queries */
+  double lambda_obs, lambda_pde, lambda_gh_u;
+  double lambda_gh_p_space; /* base value; masters use 0 */
+  double lambda_gh_p_time;
+  double comp_w[3];       /* velocity component weights in L_obs, L_gh_u */
+  double lr, beta1, beta2, eps;
+  double clip_norm;       /* per-net gradient-norm clip, 0 = off */
+  uint64_t seed;          /* Xavier-normal initialisation seed */
+  int precision;          /* DPINN_PREC_FP32 */
+  int device;             /* CUDA device ordinal */
+} dpinn_config;
+
+typedef struct dpinn_layout {
+  int n_nets, n_faces, d_in, d_out, n_params; /* n_params per net */
+  int n_masters;
+} dpinn_layout;
+
+/* Fill *cfg with defaults (Adam 1e-3 / 0.9 / 0.999 / 1e-8, unit weights). */
+int dpinn_config_default(dpinn_config* cfg);
+
+/* Validate cfg, build the decomposition (cells, faces, masters), allocate
+ * all device state on cfg->device and initialise the parameters
+ * (Xavier-normal weights from cfg->seed, zero biases).  *out owns everything
+ * until dpinn_destroy.  Errors: INVALID_ARG (bad shape, anchor outside the
+ * domain, unsupported width/depth), OOM, CUDA. */
+int dpinn_create(const dpinn_config* cfg, dpinn_t** out);
+void dpinn_destroy(dpinn_t* h);
+/* Message of the last failing call on h (h may be NULL for create errors). */
+const char* dpinn_last_error(dpinn_t* h);
+
+int dpinn_get_layout(dpinn_t* h, dpinn_layout* out);
+/* Master flag and cell box (lo[4], hi[4], unused axes 0) of net k. */
+int dpinn_net_info(dpinn_t* h, int net, int* is_master, double* lo4, double* hi4);
+/* Nets on the low / high side of face f, its axis and 1 if temporal. */
+int dpinn_face_info(dpinn_t* h, int face, int* net_lo, int* net_hi, int* axis, int* is_time);
+
+/* Deliver a point set (copied into handle-owned device memory).
+ *   kind RESIDUAL: pts [n][d_in], counts[n_nets] (points of net 0 first).
+ *   kind OBS:      pts [n][d_in], vals [n][d_space] (observed velocity),
+ *                  counts[n_nets].
+ *   kind FACE:     pts [n][d_in], counts[n_faces] (points of face 0 first;
+ *                  each point must lie on its face).
+ * pts/vals may be host or device pointers.  n_counts must equal n_nets (or
+ * n_faces).  Counts may be 0.  Re-delivering the same counts only copies;
+ * new counts rebuild the work lists and the captured step.  Errors:
+ * INVALID_ARG, OOM, CUDA. */
+int dpinn_set_points(dpinn_t* h, int kind, const float* pts, const float* vals,
+                     const int64_t* counts, int n_counts);
+
+/* Run n_steps training iterations asynchronously on `stream` (one captured
+ * CUDA graph per step: exchange, losses + gradients of all nets, Adam).
+ * Errors: STATE (points missing), CUDA. */
+int dpinn_step(dpinn_t* h, dpinn_stream_t stream, int n_steps);
+
+/* Like one step without the optimiser update: losses and gradients at the
+ * current parameters; the gradient is readable with dpinn_get_grad. */
+int dpinn_eval_grad(dpinn_t* h, dpinn_stream_t stream);
+
+/* Synchronise with the handle's work and copy the loss record of the most
+ * recent step (evaluated at its pre-update parameters) to host_out
+ * [n_nets][6].  Errors: NONFINITE (a loss is NaN/Inf; host_out still
+ * filled), TIMEOUT (a device wait gave up), CUDA. */
+int dpinn_loss(dpinn_t* h, float* host_out);
+
+/* Gradient of the most recent step or dpinn_eval_grad (before clipping),
+ * host_out [n_nets][n_params] in the parameter-block order.  Synchronises. */
+int dpinn_get_grad(dpinn_t* h, float* host_out);
+
+/* Query the resident ensemble: route each point to its cell, evaluate the
+ * net.  out row = (u, v, [w], p_out) or, with want_residual, followed by the
+ * d_space + 1 residuals (momentum then continuity; the raw-pressure
+ * gradient enters them).  p_out = p - p(x_anc, t) + p_ref in master cells,
+ * p + p_ref elsewhere (Eq. (18)).  pts [n][d_in] and out [n][row] are device
+ * pointers owned by the caller; asynchronous on `stream`.  A point outside
+ * the domain sets an error that the next dpinn_query_status reports
+ * (INVALID_ARG); its row is left untouched. */
+int dpinn_query(dpinn_t* h, const float* dev_pts, int64_t n, int want_residual,
+                float* dev_out, dpinn_stream_t stream);
+/* Synchronise `stream` and report (then clear) out-of-domain errors. */
+int dpinn_query_status(dpinn_t* h, dpinn_stream_t stream);
+
+/* Parameters, Adam moments and step count, host buffers of
+ * [n_nets][n_params] floats (any pointer may be NULL to skip it). */
+int dpinn_get_state(dpinn_t* h, float* params, float* m, float* v, int64_t* step);
+int dpinn_set_state(dpinn_t* h, const float* params, const float* m, const float* v,
+                    int64_t step);
+
+/* Apply one optimiser update with a given gradient (host [n_nets][n_params]);
+ * the same kernels as the step's update. */
+int dpinn_apply_grad(dpinn_t* h, const float* host_grad);
+
+/* Kernels launched by one dpinn_step (for accounting). */
+int dpinn_launches_per_step(dpinn_t* h);
+
+/* One training step (identical kernels and launch configuration to
+ * dpinn_step, launched individually instead of as a graph) with a CUDA event
+ * recorded on `stream` around every kernel.  Synchronises; writes up to
+ * max_kernels durations (ms) to ms[], their count to *n_kernels and static
+ * kernel names to names[] (may be NULL). */
+int dpinn_step_timed(dpinn_t* h, dpinn_stream_t stream, float* ms, int max_kernels, int* n_kernels,
+                     const char** names);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DPINN_H */

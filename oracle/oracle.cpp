@@ -375,14 +375,17 @@ T value_p(const Geo& g, int net, const T* th, const double* x) {
   return Y[g.ds];
 }
 
-Nbr exchange(const Prob& pb, const double* th_all) {
+// Only faces touching a net flagged in `need` are evaluated (all when null);
+// the others keep zeros and are never read by those nets' losses.
+Nbr exchange(const Prob& pb, const double* th_all, const std::vector<char>* need = nullptr) {
   const Geo& g = pb.g;
   Nbr nb;
   int64_t nf = pb.face_off.back();
   nb.val.assign((size_t)nf * 2 * g.dout, 0.0);
   nb.anc.assign((size_t)nf * 2, 0.0);
   std::vector<double> Z((size_t)g.L * g.W), Y(g.dout);
-  for (int f = 0; f < g.n_faces; ++f)
+  for (int f = 0; f < g.n_faces; ++f) {
+    if (need && !(*need)[g.face[f][0]] && !(*need)[g.face[f][1]]) continue;
     for (int64_t i = pb.face_off[f]; i < pb.face_off[f + 1]; ++i) {
       double x[4], xa[4];
       pb.face_x(i, x);
@@ -397,6 +400,7 @@ Nbr exchange(const Prob& pb, const double* th_all) {
         }
       }
     }
+  }
   return nb;
 }
 
@@ -711,7 +715,9 @@ int ora_grad_nets(const ora_config* c, const ora_problem* p, const double* th, c
                   int n_sel, double* grad, double* loss) {
   Geo g(*c);
   Prob pb(g, *p);
-  Nbr nb = exchange(pb, th);
+  std::vector<char> need(g.n_nets, 0);
+  for (int s = 0; s < n_sel; ++s) need[nets[s]] = 1;
+  Nbr nb = exchange(pb, th, &need);
   for (int s = 0; s < n_sel; ++s) {
     int A = nets[s];
     net_grad(pb, nb, A, th + (size_t)A * g.n_params, grad + (size_t)s * g.n_params, loss ? loss + s * 6 : nullptr);

@@ -1,0 +1,292 @@
+"""ctypes binding of libdpinn (C ABI in ``include/dpinn.h``).
+
+Argument marshalling only: every step of the training step and of the query
+path runs in the library's CUDA kernels.  There is no CPU fallback - if the
+library is missing or cannot be loaded, constructing ``Dpinn`` raises.
+Arrays may be NumPy arrays (host memory) or torch tensors (host or device);
+torch is used only for device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdpinn.so")
+
+POINTS_RESIDUAL, POINTS_OBS, POINTS_FACE = 0, 1, 2
+
+ERRORS = {
+    -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NONFINITE", -5: "TIMEOUT", -6: "BUSY", -7: "STATE",
+}
+
+EXPORTS = (
+    "dpinn_config_default", "dpinn_create", "dpinn_destroy", "dpinn_last_error", "dpinn_get_layout",
+    "dpinn_net_info", "dpinn_face_info", "dpinn_set_points", "dpinn_step", "dpinn_eval_grad", "dpinn_loss",
+    "dpinn_get_grad", "dpinn_query", "dpinn_query_status", "dpinn_get_state", "dpinn_set_state",
+    "dpinn_apply_grad", "dpinn_launches_per_step", "dpinn_step_timed",
+)
+
+
+class DpinnError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"dpinn error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class Config(C.Structure):
+    _fields_ = [
+        ("d_space", C.c_int), ("unsteady", C.c_int),
+        ("lo", C.c_double * 4), ("hi", C.c_double * 4), ("splits", C.c_int * 4),
+        ("depth", C.c_int), ("width", C.c_int), ("activation", C.c_int),
+        ("nu", C.c_double), ("anchor_x", C.c_double * 3), ("p_ref", C.c_double),
+        ("lambda_obs", C.c_double), ("lambda_pde", C.c_double), ("lambda_gh_u", C.c_double),
+        ("lambda_gh_p_space", C.c_double), ("lambda_gh_p_time", C.c_double),
+        ("comp_w", C.c_double * 3),
+        ("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
+        ("clip_norm", C.c_double),
+        ("seed", C.c_uint64), ("precision", C.c_int), ("device", C.c_int),
+    ]
+
+
+class Layout(C.Structure):
+    _fields_ = [("n_nets", C.c_int), ("n_faces", C.c_int), ("d_in", C.c_int), ("d_out", C.c_int),
+                ("n_params", C.c_int), ("n_masters", C.c_int)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libdpinn.so (raises OSError when it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"libdpinn.so not built at {path}: run paper_2602_15883_b300/build.py")
+    lib = C.CDLL(path)
+    vp, i32, i64 = C.c_void_p, C.c_int, C.c_int64
+    sig = {
+        "dpinn_config_default": ([vp], i32),
+        "dpinn_create": ([vp, vp], i32),
+        "dpinn_destroy": ([vp], None),
+        "dpinn_last_error": ([vp], C.c_char_p),
+        "dpinn_get_layout": ([vp, vp], i32),
+        "dpinn_net_info": ([vp, i32, vp, vp, vp], i32),
+        "dpinn_face_info": ([vp, i32, vp, vp, vp, vp], i32),
+        "dpinn_set_points": ([vp, i32, vp, vp, vp, i32], i32),
+        "dpinn_step": ([vp, vp, i32], i32),
+        "dpinn_eval_grad": ([vp, vp], i32),
+        "dpinn_loss": ([vp, vp], i32),
+        "dpinn_get_grad": ([vp, vp], i32),
+        "dpinn_query": ([vp, vp, i64, i32, vp, vp], i32),
+        "dpinn_query_status": ([vp, vp], i32),
+        "dpinn_get_state": ([vp, vp, vp, vp, vp], i32),
+        "dpinn_set_state": ([vp, vp, vp, vp, i64], i32),
+        "dpinn_apply_grad": ([vp, vp], i32),
+        "dpinn_launches_per_step": ([vp], i32),
+        "dpinn_step_timed": ([vp, vp, vp, i32, vp, vp], i32),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def make_config(cfg: dict) -> Config:
+    c = Config()
+    load_library().dpinn_config_default(C.addressof(c))
+    c.d_space, c.unsteady = int(cfg["d_space"]), int(cfg["unsteady"])
+    for a in range(4):
+        c.lo[a] = float(cfg["lo"][a])
+        c.hi[a] = float(cfg["hi"][a])
+        c.splits[a] = int(cfg["splits"][a])
+    c.depth, c.width = int(cfg["depth"]), int(cfg["width"])
+    c.activation = int(cfg.get("activation", 0))
+    c.nu = float(cfg["nu"])
+    for a in range(3):
+        c.anchor_x[a] = float(cfg["anchor"][a])
+        c.comp_w[a] = float(cfg["comp_w"][a])
+    c.p_ref = float(cfg["p_ref"])
+    for k in ("lambda_obs", "lambda_pde", "lambda_gh_u", "lambda_gh_p_space", "lambda_gh_p_time",
+              "lr", "beta1", "beta2", "eps", "clip_norm"):
+        setattr(c, k, float(cfg[k]))
+    c.seed = int(cfg.get("seed", 0))
+    c.precision = int(cfg.get("precision", 0))
+    c.device = int(cfg.get("device", 0))
+    return c
+
+
+def _ptr(a):
+    """(pointer, keep-alive) for a NumPy array or a torch tensor."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        a = np.ascontiguousarray(a)
+        return a.ctypes.data, a
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            a = a.contiguous()
+            return a.data_ptr(), a
+    except ImportError:
+        pass
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Dpinn:
+    """One resident ensemble of subdomain networks on one GPU."""
+
+    def __init__(self, cfg: dict):
+        self.lib = load_library()
+        self.cfg = dict(cfg)
+        self._c = make_config(cfg)
+        h = C.c_void_p()
+        rc = self.lib.dpinn_create(C.addressof(self._c), C.addressof(h))
+        if rc != 0:
+            raise DpinnError(rc, self.lib.dpinn_last_error(None).decode())
+        self.h = h
+        lay = Layout()
+        self._check(self.lib.dpinn_get_layout(self.h, C.addressof(lay)))
+        self.n_nets, self.n_faces = lay.n_nets, lay.n_faces
+        self.d_in, self.d_out, self.n_params = lay.d_in, lay.d_out, lay.n_params
+        self.n_masters = lay.n_masters
+        self.d_space = self.d_out - 1
+
+    def _check(self, rc):
+        if rc != 0:
+            raise DpinnError(rc, self.lib.dpinn_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dpinn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- layout -------------------------------------------------------------
+    def net_info(self, k):
+        m = C.c_int()
+        lo = (C.c_double * 4)()
+        hi = (C.c_double * 4)()
+        self._check(self.lib.dpinn_net_info(self.h, k, C.addressof(m), C.addressof(lo), C.addressof(hi)))
+        return m.value, np.array(lo[:]), np.array(hi[:])
+
+    def face_info(self, f):
+        v = [C.c_int() for _ in range(4)]
+        self._check(self.lib.dpinn_face_info(self.h, f, *[C.addressof(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    # -- points ---------------------------------------------------------------
+    def set_points(self, kind, pts, counts, vals=None):
+        counts = np.ascontiguousarray(counts, np.int64)
+        p, kp = _ptr(pts)
+        q, kq = _ptr(vals)
+        self._check(self.lib.dpinn_set_points(self.h, kind, p, q, counts.ctypes.data, len(counts)))
+
+    def set_problem(self, pb, set_params=True):
+        self.set_points(POINTS_RESIDUAL, np.asarray(pb.res_pts, np.float32), pb.res_counts)
+        self.set_points(POINTS_OBS, np.asarray(pb.obs_pts, np.float32), pb.obs_counts,
+                        np.asarray(pb.obs_vals, np.float32))
+        self.set_points(POINTS_FACE, np.asarray(pb.face_pts, np.float32), pb.face_counts)
+        if set_params:
+            self.set_state(params=pb.theta0, step=0, zero_moments=True)
+
+    # -- training -------------------------------------------------------------
+    def step(self, n=1, stream=None):
+        self._check(self.lib.dpinn_step(self.h, _stream(stream), int(n)))
+
+    def eval_grad(self, stream=None):
+        self._check(self.lib.dpinn_eval_grad(self.h, _stream(stream)))
+
+    def loss(self, check=True):
+        out = np.zeros((self.n_nets, 6), np.float32)
+        rc = self.lib.dpinn_loss(self.h, out.ctypes.data)
+        if check:
+            self._check(rc)
+        return out
+
+    def grad(self):
+        out = np.zeros((self.n_nets, self.n_params), np.float32)
+        self._check(self.lib.dpinn_get_grad(self.h, out.ctypes.data))
+        return out
+
+    def get_state(self):
+        n = self.n_nets * self.n_params
+        th, m, v = (np.zeros(n, np.float32) for _ in range(3))
+        st = C.c_int64()
+        self._check(self.lib.dpinn_get_state(self.h, th.ctypes.data, m.ctypes.data, v.ctypes.data,
+                                             C.addressof(st)))
+        return th, m, v, st.value
+
+    def set_state(self, params=None, m=None, v=None, step=0, zero_moments=False):
+        n = self.n_nets * self.n_params
+        if zero_moments:
+            m = np.zeros(n, np.float32) if m is None else m
+            v = np.zeros(n, np.float32) if v is None else v
+        arrs = [None if a is None else np.ascontiguousarray(a, np.float32).reshape(-1) for a in (params, m, v)]
+        for a in arrs:
+            if a is not None and a.size != n:
+                raise ValueError(f"state arrays need {n} floats, got {a.size}")
+        ptrs = [None if a is None else a.ctypes.data for a in arrs]
+        self._check(self.lib.dpinn_set_state(self.h, *ptrs, int(step)))
+
+    def apply_grad(self, g):
+        g = np.ascontiguousarray(g, np.float32).reshape(-1)
+        self._check(self.lib.dpinn_apply_grad(self.h, g.ctypes.data))
+
+    def step_timed(self, stream=None):
+        """One step launched kernel by kernel with CUDA events between them:
+        {kernel name: milliseconds}."""
+        ms = (C.c_float * 8)()
+        names = (C.c_char_p * 8)()
+        n = C.c_int()
+        self._check(self.lib.dpinn_step_timed(self.h, _stream(stream), C.addressof(ms), 8, C.addressof(n),
+                                              C.addressof(names)))
+        return {names[i].decode(): ms[i] for i in range(n.value)}
+
+    @property
+    def launches_per_step(self):
+        return self.lib.dpinn_launches_per_step(self.h)
+
+    # -- queries --------------------------------------------------------------
+    def query(self, pts, want_residual=False, out=None, stream=None, check=True):
+        """Evaluate the ensemble at device points (torch CUDA tensor [n][d_in])."""
+        import torch
+        n = pts.shape[0]
+        w = self.d_out + (self.d_space + 1 if want_residual else 0)
+        if out is None:
+            out = torch.empty((n, w), dtype=torch.float32, device=pts.device)
+        p, kp = _ptr(pts)
+        o, ko = _ptr(out)
+        s = _stream(stream)
+        self._check(self.lib.dpinn_query(self.h, p, n, int(bool(want_residual)), o, s))
+        if check:
+            self._check(self.lib.dpinn_query_status(self.h, s))
+        return out
+
+    def query_status(self, stream=None):
+        return self.lib.dpinn_query_status(self.h, _stream(stream))

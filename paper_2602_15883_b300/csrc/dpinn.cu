@@ -1,0 +1,865 @@
+// Host runtime and C ABI of libdpinn (declarations and conventions in
+// include/dpinn.h).
+//
+// The handle owns the decomposition (cells, faces, masters - Sec. 2.2 and
+// Algorithm 1), every device buffer, the work lists of the grouped kernels
+// and two captured CUDA graphs: one training step (neighbour exchange,
+// grouped jet/value forward + loss + reverse, deterministic gradient
+// reduction, Adam) and the same without the optimiser update.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/dpinn.h"
+#include "pinn_kernels.cuh"
+
+namespace {
+
+struct KernelSet {
+  const void* train_jet = nullptr;
+  const void* train_val = nullptr;
+  const void* eval_val = nullptr;
+  const void* query_val = nullptr;
+  const void* query_jet = nullptr;
+  size_t smem_jet = 0, smem_val = 0;
+  int P_jet = 0, P_val = 0;
+  long long stash_jet = 0, stash_val = 0;   // floats per CTA
+};
+
+template <int W, int DS, int UNST>
+KernelSet make_set(int L) {
+  constexpr int DIN = DS + UNST, CJ = DIN + 2, DOUT = DS + 1;
+  KernelSet k;
+  k.train_jet = (const void*)dk::k_pinn<W, DS, UNST, true, dk::M_TRAIN>;
+  k.train_val = (const void*)dk::k_pinn<W, DS, UNST, false, dk::M_TRAIN>;
+  k.eval_val = (const void*)dk::k_pinn<W, DS, UNST, false, dk::M_EVAL>;
+  k.query_val = (const void*)dk::k_pinn<W, DS, UNST, false, dk::M_QUERY>;
+  k.query_jet = (const void*)dk::k_pinn<W, DS, UNST, true, dk::M_QUERY>;
+  k.smem_jet = dk::smem_floats<W, CJ, DOUT>(L) * sizeof(float);
+  k.smem_val = dk::smem_floats<W, 1, DOUT>(L) * sizeof(float);
+  k.P_jet = dk::Tile<W, CJ>::P;
+  k.P_val = dk::Tile<W, 1>::P;
+  k.stash_jet = (long long)(L > 1 ? L - 1 : 0) * dk::Tile<W, CJ>::NQ * dk::NT * 4;
+  k.stash_val = (long long)(L > 1 ? L - 1 : 0) * dk::Tile<W, 1>::NQ * dk::NT * 4;
+  return k;
+}
+
+template <int W>
+bool pick_ds(int ds, int unst, int L, KernelSet* k) {
+  if (ds == 2 && unst == 0) { *k = make_set<W, 2, 0>(L); return true; }
+  if (ds == 2 && unst == 1) { *k = make_set<W, 2, 1>(L); return true; }
+  if (ds == 3 && unst == 0) { *k = make_set<W, 3, 0>(L); return true; }
+  if (ds == 3 && unst == 1) { *k = make_set<W, 3, 1>(L); return true; }
+  return false;
+}
+
+bool pick_kernels(int W, int ds, int unst, int L, KernelSet* k) {
+  if (W == 32) return pick_ds<32>(ds, unst, L, k);
+  if (W == 64) return pick_ds<64>(ds, unst, L, k);
+  if (W == 128) return pick_ds<128>(ds, unst, L, k);
+  return false;
+}
+
+// float32 cell rule of the C ABI
+int cell_fp32(const dpinn_config& c, int a, float x) {
+  const float lo = (float)c.lo[a], hi = (float)c.hi[a];
+  const float inv_h = (float)((double)c.splits[a] / (c.hi[a] - c.lo[a]));
+  if (!(x >= lo && x <= hi)) return -1;
+  volatile float d = x - lo;
+  volatile float q = d * inv_h;
+  int k = (int)std::floor((float)q);
+  return std::min(std::max(k, 0), c.splits[a] - 1);
+}
+
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  void free_() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  cudaError_t ensure(size_t cnt) {
+    if (cnt <= n && p) return cudaSuccess;
+    free_();
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(cnt, 1) * sizeof(T));
+    if (e == cudaSuccess) n = std::max<size_t>(cnt, 1);
+    else p = nullptr;
+    return e;
+  }
+};
+
+}  // namespace
+
+struct dpinn {
+  dpinn_config cfg{};
+  int ds = 0, unst = 0, din = 0, dout = 0, W = 0, L = 0;
+  int n_nets = 0, n_faces = 0, n_params = 0, npp = 0, nTp = 0;
+  std::vector<int> stride, master;
+  std::vector<std::array<int, 4>> cell;
+  std::vector<std::array<double, 4>> blo, bhi;
+  std::vector<std::array<int, 3>> faces;   // lo, hi, axis
+  std::vector<std::vector<int>> net_faces; // face ids per net
+  dk::Shape shape{};
+  KernelSet ks;
+  int dev = 0, n_sms = 0;
+  std::string err;
+
+  // parameters and optimiser state
+  DevBuf<float> theta, thetaT, m, v, grad, norm_part, coef;
+  DevBuf<long long> step_d;
+  DevBuf<dk::NetInfo> nets_d;
+  DevBuf<int> face_info_d, err_d, counters, n_items_d, slot_begin_d, iota_d;
+  // points
+  DevBuf<float> res_pts, obs_pts, obs_vals, face_pts;
+  std::vector<int64_t> res_counts, obs_counts, face_counts;
+  bool have[3] = {false, false, false};
+  // plan
+  DevBuf<dk::Item> items_eval, items_jet, items_val;
+  int n_eval = 0, n_jet = 0, n_val = 0, n_slots = 0;
+  int grid_eval = 0, grid_jet = 0, grid_val = 0;
+  DevBuf<float> grad_part, stash, nbr_val, nbr_anc, loss_rec;
+  DevBuf<double> loss_part;
+  float* loss_host = nullptr;
+  bool plan_ok = false;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t g_step = nullptr, g_grad = nullptr;
+  cudaEvent_t done = nullptr;
+  int launches = 0;
+  // query scratch
+  DevBuf<int> q_net, q_perm, q_counts, q_off, q_cursor, q_nitems;
+  DevBuf<dk::Item> q_items;
+
+  ~dpinn() {
+    if (g_step) cudaGraphExecDestroy(g_step);
+    if (g_grad) cudaGraphExecDestroy(g_grad);
+    if (done) cudaEventDestroy(done);
+    if (cap) cudaStreamDestroy(cap);
+    if (loss_host) cudaFreeHost(loss_host);
+    for (auto* b : {&theta, &thetaT, &m, &v, &grad, &norm_part, &coef, &res_pts, &obs_pts, &obs_vals, &face_pts,
+                    &grad_part, &stash, &nbr_val, &nbr_anc, &loss_rec})
+      b->free_();
+    step_d.free_(); nets_d.free_(); loss_part.free_();
+    for (auto* b : {&face_info_d, &err_d, &counters, &n_items_d, &slot_begin_d, &iota_d, &q_net, &q_perm,
+                    &q_counts, &q_off, &q_cursor, &q_nitems})
+      b->free_();
+    items_eval.free_(); items_jet.free_(); items_val.free_(); q_items.free_();
+  }
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+int fail(dpinn* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_err = msg;
+  return code;
+}
+
+int cuda_fail(dpinn* h, cudaError_t e, const char* what) {
+  return fail(h, e == cudaErrorMemoryAllocation ? DPINN_ERR_OOM : DPINN_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                      \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+dk::Bufs make_bufs(dpinn* h) {
+  dk::Bufs b{};
+  b.theta = h->theta.p;
+  b.thetaT = h->thetaT.p;
+  b.nets = h->nets_d.p;
+  b.res_pts = h->res_pts.p;
+  b.obs_pts = h->obs_pts.p;
+  b.obs_vals = h->obs_vals.p;
+  b.face_pts = h->face_pts.p;
+  b.face_info = h->face_info_d.p;
+  b.nbr_val = h->nbr_val.p;
+  b.nbr_anc = h->nbr_anc.p;
+  b.grad_part = h->grad_part.p;
+  b.loss_part = h->loss_part.p;
+  b.stash = h->stash.p;
+  b.stash_per_cta = 0;
+  b.counter = h->counters.p;
+  b.err = h->err_d.p;
+  return b;
+}
+
+cudaError_t launch_pinn(const void* fn, int grid, size_t smem, const dk::Shape& sh, const dk::Bufs& b,
+                        const dk::Item* items, const int* n_items, cudaStream_t s) {
+  void* args[] = {(void*)&sh, (void*)&b, (void*)&items, (void*)&n_items};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(dk::NT), args, smem, s);
+}
+
+int occupancy(const void* fn, size_t smem) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, dk::NT, smem) != cudaSuccess) return 1;
+  return std::max(occ, 1);
+}
+
+// Split `count` points starting at `begin` into chunks of at most `chunk`.
+template <class F>
+void chunks(int64_t begin, int64_t count, int64_t chunk, F f) {
+  for (int64_t s = 0; s < count; s += chunk) f(begin + s, std::min(chunk, count - s));
+}
+
+int build_plan(dpinn* h);
+
+// Enqueue one step's work on stream s.  With `ev` (an array of at least 8
+// events) an event is recorded before the first and after every kernel, and
+// the kernel names are reported in `names` (for per-kernel timing).
+cudaError_t enqueue_step(dpinn* h, bool with_adam, cudaStream_t s, int* n_launch, cudaEvent_t* ev = nullptr,
+                         const char** names = nullptr) {
+  int launches = 0;
+  int ne = 0;
+  auto mark = [&](const char* name) {
+    if (ev) {
+      if (names && ne > 0) names[ne - 1] = name;
+      cudaEventRecord(ev[ne++], s);
+    }
+  };
+  dk::Bufs b = make_bufs(h);
+  cudaError_t e = cudaMemsetAsync(h->counters.p, 0, 4 * sizeof(int), s);
+  mark(nullptr);
+  if (e == cudaSuccess && h->n_eval) {
+    dk::Bufs bb = b;
+    bb.counter = h->counters.p + 0;
+    e = launch_pinn(h->ks.eval_val, h->grid_eval, h->ks.smem_val, h->shape, bb, h->items_eval.p, h->n_items_d.p + 0, s);
+    ++launches;
+    mark("exchange");
+  }
+  if (e == cudaSuccess && h->n_jet) {
+    dk::Bufs bb = b;
+    bb.counter = h->counters.p + 1;
+    bb.stash_per_cta = h->ks.stash_jet;
+    e = launch_pinn(h->ks.train_jet, h->grid_jet, h->ks.smem_jet, h->shape, bb, h->items_jet.p, h->n_items_d.p + 1, s);
+    ++launches;
+    mark("train_jet");
+  }
+  if (e == cudaSuccess && h->n_val) {
+    dk::Bufs bb = b;
+    bb.counter = h->counters.p + 2;
+    bb.stash_per_cta = h->ks.stash_val;
+    e = launch_pinn(h->ks.train_val, h->grid_val, h->ks.smem_val, h->shape, bb, h->items_val.p, h->n_items_d.p + 2, s);
+    ++launches;
+    mark("train_val");
+  }
+  const int nblk = (h->n_params + dk::NT - 1) / dk::NT;
+  if (e == cudaSuccess) {
+    dk::k_reduce_grad<<<dim3(nblk, h->n_nets), dk::NT, 0, s>>>(h->grad_part.p, h->slot_begin_d.p, h->grad.p,
+                                                                h->norm_part.p, h->npp, h->n_params);
+    e = cudaGetLastError();
+    ++launches;
+    mark("reduce_grad");
+  }
+  if (e == cudaSuccess && with_adam) {
+    if (h->cfg.clip_norm > 0) {
+      dk::k_clip_coef<<<h->n_nets, dk::NT, 0, s>>>(h->norm_part.p, nblk, (float)h->cfg.clip_norm, h->coef.p);
+      ++launches;
+      mark("clip");
+    }
+    dk::AdamArgs ar{h->cfg.lr, h->cfg.beta1, h->cfg.beta2, h->cfg.eps, h->cfg.clip_norm > 0 ? 1 : 0};
+    dk::k_adam<<<dim3(nblk, h->n_nets), dk::NT, 0, s>>>(h->shape, ar, h->theta.p, h->thetaT.p, h->m.p, h->v.p,
+                                                         h->grad.p, h->coef.p, h->step_d.p, h->n_params);
+    e = cudaGetLastError();
+    launches += 1;
+    mark("adam");
+  }
+  if (e == cudaSuccess) {
+    dk::k_loss_record<<<(h->n_nets + 127) / 128, 128, 0, s>>>(h->shape, h->loss_part.p, h->slot_begin_d.p,
+                                                             h->nets_d.p, h->n_nets, h->loss_rec.p, h->err_d.p,
+                                                             h->step_d.p, with_adam ? 1 : 0);
+    e = cudaGetLastError();
+    ++launches;
+    mark("loss_record");
+  }
+  *n_launch = launches;
+  return e;
+}
+
+int capture(dpinn* h, bool with_adam, cudaGraphExec_t* out) {
+  if (*out) {
+    cudaGraphExecDestroy(*out);
+    *out = nullptr;
+  }
+  cudaStream_t s = h->cap;
+  CK(h, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  int launches = 0;
+  cudaError_t e = enqueue_step(h, with_adam, s, &launches);
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(s, &g);
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(h, e, "capture");
+  }
+  if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+  if (with_adam) h->launches = launches;
+  return DPINN_OK;
+}
+
+int build_plan(dpinn* h) {
+  h->plan_ok = false;
+  if (!(h->have[0] && h->have[1] && (h->have[2] || h->n_faces == 0)))
+    return DPINN_OK;   // built when every point set is present
+  if (!h->have[2]) h->face_counts.assign(h->n_faces, 0);
+  const int nn = h->n_nets, nf = h->n_faces;
+  std::vector<int64_t> res_off(nn + 1, 0), obs_off(nn + 1, 0), face_off(nf + 1, 0);
+  for (int k = 0; k < nn; ++k) res_off[k + 1] = res_off[k] + h->res_counts[k];
+  for (int k = 0; k < nn; ++k) obs_off[k + 1] = obs_off[k] + h->obs_counts[k];
+  for (int f = 0; f < nf; ++f) face_off[f + 1] = face_off[f] + h->face_counts[f];
+  const int64_t n_face_pts = face_off[nf];
+
+  // chunk sizes: enough items for several waves, multiples of the tile
+  auto pick_chunk = [&](int64_t total, int P) {
+    const int64_t target = std::max<int64_t>(1, total / (8LL * h->n_sms));
+    int64_t c = ((target + P - 1) / P) * P;
+    return std::min<int64_t>(std::max<int64_t>(c, P), 64LL * P);
+  };
+  const int64_t cj = pick_chunk(res_off[nn], h->ks.P_jet);
+  const int64_t cv = pick_chunk(obs_off[nn] + 2 * n_face_pts, h->ks.P_val);
+
+  std::vector<dk::Item> ij, iv, ie;
+  std::vector<int> slot_begin(nn + 1, 0);
+  std::vector<dk::NetInfo> ni(nn);
+  int slot = 0;
+  for (int k = 0; k < nn; ++k) {
+    slot_begin[k] = slot;
+    chunks(res_off[k], h->res_counts[k], cj, [&](int64_t b, int64_t c) {
+      ij.push_back({dk::K_PDE, k, (int)b, (int)c, slot++, 0, 0, 0});
+    });
+    chunks(obs_off[k], h->obs_counts[k], cv, [&](int64_t b, int64_t c) {
+      iv.push_back({dk::K_OBS, k, (int)b, (int)c, slot++, 0, 0, 0});
+    });
+    int64_t ngh = 0;
+    for (int f : h->net_faces[k]) {
+      const int side = (h->faces[f][0] == k) ? 0 : 1;
+      ngh += h->face_counts[f];
+      chunks(face_off[f], h->face_counts[f], cv, [&](int64_t b, int64_t c) {
+        iv.push_back({dk::K_FACE, k, (int)b, (int)c, slot++, f, side, 0});
+      });
+    }
+    dk::NetInfo& n = ni[k];
+    std::memset(&n, 0, sizeof(n));
+    for (int q = 0; q < 4; ++q) {
+      if (q < h->din) {
+        n.center[q] = (float)(0.5 * (h->blo[k][q] + h->bhi[k][q]));
+        n.scale[q] = (float)(2.0 / (h->bhi[k][q] - h->blo[k][q]));
+      }
+    }
+    n.inv_npde = h->res_counts[k] ? (float)(1.0 / (double)h->res_counts[k]) : 0.f;
+    n.inv_nobs = h->obs_counts[k] ? (float)(1.0 / (double)h->obs_counts[k]) : 0.f;
+    n.inv_ngh = ngh ? (float)(1.0 / (double)ngh) : 0.f;
+    n.master = h->master[k];
+    n.lam_space = h->master[k] ? 0.f : (float)h->cfg.lambda_gh_p_space;
+  }
+  slot_begin[nn] = slot;
+  h->n_slots = slot;
+  for (int f = 0; f < nf; ++f)
+    for (int side = 0; side < 2; ++side) {
+      const int k = h->faces[f][side];
+      chunks(face_off[f], h->face_counts[f], cv, [&](int64_t b, int64_t c) {
+        ie.push_back({dk::K_EVAL, k, (int)b, (int)c, 0, f, side, 0});
+        if (h->master[k]) ie.push_back({dk::K_EVAL_ANC, k, (int)b, (int)c, 0, f, side, 0});
+      });
+    }
+  // longest chunks first (the scheduler hands items out in this order)
+  auto by_count = [](const dk::Item& a, const dk::Item& b) { return a.count > b.count; };
+  std::stable_sort(ij.begin(), ij.end(), by_count);
+  std::stable_sort(iv.begin(), iv.end(), by_count);
+  std::stable_sort(ie.begin(), ie.end(), by_count);
+  h->n_jet = (int)ij.size();
+  h->n_val = (int)iv.size();
+  h->n_eval = (int)ie.size();
+
+  const int occ_j = occupancy(h->ks.train_jet, h->ks.smem_jet);
+  const int occ_v = occupancy(h->ks.train_val, h->ks.smem_val);
+  h->grid_jet = (int)std::min<int64_t>(h->n_jet, (int64_t)h->n_sms * occ_j);
+  h->grid_val = (int)std::min<int64_t>(h->n_val, (int64_t)h->n_sms * occ_v);
+  h->grid_eval = (int)std::min<int64_t>(h->n_eval, (int64_t)h->n_sms * occ_v);
+
+  CK(h, h->items_jet.ensure(ij.size()));
+  CK(h, h->items_val.ensure(iv.size()));
+  CK(h, h->items_eval.ensure(ie.size()));
+  if (!ij.empty()) CK(h, cudaMemcpy(h->items_jet.p, ij.data(), ij.size() * sizeof(dk::Item), cudaMemcpyHostToDevice));
+  if (!iv.empty()) CK(h, cudaMemcpy(h->items_val.p, iv.data(), iv.size() * sizeof(dk::Item), cudaMemcpyHostToDevice));
+  if (!ie.empty()) CK(h, cudaMemcpy(h->items_eval.p, ie.data(), ie.size() * sizeof(dk::Item), cudaMemcpyHostToDevice));
+  int nitems[3] = {h->n_eval, h->n_jet, h->n_val};
+  CK(h, cudaMemcpy(h->n_items_d.p, nitems, sizeof(nitems), cudaMemcpyHostToDevice));
+  CK(h, h->slot_begin_d.ensure(nn + 1));
+  CK(h, cudaMemcpy(h->slot_begin_d.p, slot_begin.data(), (nn + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  CK(h, cudaMemcpy(h->nets_d.p, ni.data(), nn * sizeof(dk::NetInfo), cudaMemcpyHostToDevice));
+  CK(h, h->grad_part.ensure((size_t)std::max(slot, 1) * h->npp));
+  CK(h, h->loss_part.ensure((size_t)std::max(slot, 1) * 5));
+  CK(h, cudaMemset(h->loss_part.p, 0, (size_t)std::max(slot, 1) * 5 * sizeof(double)));
+  const size_t st = std::max((size_t)h->grid_jet * h->ks.stash_jet, (size_t)h->grid_val * h->ks.stash_val);
+  CK(h, h->stash.ensure(std::max<size_t>(st, 4)));
+  CK(h, h->nbr_val.ensure((size_t)std::max<int64_t>(n_face_pts, 1) * 2 * h->dout));
+  CK(h, h->nbr_anc.ensure((size_t)std::max<int64_t>(n_face_pts, 1) * 2));
+  CK(h, cudaMemset(h->nbr_anc.p, 0, (size_t)std::max<int64_t>(n_face_pts, 1) * 2 * sizeof(float)));
+  int rc = capture(h, true, &h->g_step);
+  if (rc) return rc;
+  rc = capture(h, false, &h->g_grad);
+  if (rc) return rc;
+  h->plan_ok = true;
+  return DPINN_OK;
+}
+
+int copy_state_in(dpinn* h, float* dst, const float* src) {
+  CK(h, cudaMemcpy2D(dst, (size_t)h->npp * 4, src, (size_t)h->n_params * 4, (size_t)h->n_params * 4, h->n_nets,
+                     cudaMemcpyDefault));
+  return DPINN_OK;
+}
+
+int copy_state_out(dpinn* h, float* dst, const float* src) {
+  CK(h, cudaMemcpy2D(dst, (size_t)h->n_params * 4, src, (size_t)h->npp * 4, (size_t)h->n_params * 4, h->n_nets,
+                     cudaMemcpyDefault));
+  return DPINN_OK;
+}
+
+int refresh_transpose(dpinn* h) {
+  if (h->L < 2) return DPINN_OK;
+  const int nblk = ((h->L - 1) * h->W * h->W + dk::NT - 1) / dk::NT;
+  dk::k_transpose<<<dim3(nblk, h->n_nets), dk::NT>>>(h->shape, h->theta.p, h->thetaT.p);
+  CK(h, cudaGetLastError());
+  CK(h, cudaDeviceSynchronize());
+  return DPINN_OK;
+}
+
+int check_errors(dpinn* h) {
+  int e[3] = {0, 0, 0};
+  CK(h, cudaMemcpy(e, h->err_d.p, sizeof(e), cudaMemcpyDeviceToHost));
+  if (e[dk::ERR_TIMEOUT]) return fail(h, DPINN_ERR_TIMEOUT, "a device wait gave up (bulk copy never completed)");
+  if (e[dk::ERR_NONFINITE]) {
+    CK(h, cudaMemset(h->err_d.p + dk::ERR_NONFINITE, 0, sizeof(int)));
+    return fail(h, DPINN_ERR_NONFINITE, "non-finite loss");
+  }
+  return DPINN_OK;
+}
+
+}  // namespace
+
+// =================================================================== ABI ===
+extern "C" {
+
+int dpinn_config_default(dpinn_config* c) {
+  if (!c) return DPINN_ERR_INVALID_ARG;
+  std::memset(c, 0, sizeof(*c));
+  c->d_space = 2;
+  for (int a = 0; a < 4; ++a) { c->lo[a] = 0.0; c->hi[a] = 1.0; c->splits[a] = 1; }
+  c->depth = 4;
+  c->width = 32;
+  c->nu = 0.01;
+  c->lambda_obs = c->lambda_pde = c->lambda_gh_u = c->lambda_gh_p_space = c->lambda_gh_p_time = 1.0;
+  c->comp_w[0] = c->comp_w[1] = c->comp_w[2] = 1.0;
+  c->lr = 1e-3; c->beta1 = 0.9; c->beta2 = 0.999; c->eps = 1e-8;
+  return DPINN_OK;
+}
+
+const char* dpinn_last_error(dpinn_t* h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+int dpinn_create(const dpinn_config* cfg, dpinn_t** out) {
+  if (!cfg || !out) return fail(nullptr, DPINN_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  const dpinn_config& c = *cfg;
+  if (c.d_space != 2 && c.d_space != 3) return fail(nullptr, DPINN_ERR_INVALID_ARG, "d_space must be 2 or 3");
+  if (c.unsteady != 0 && c.unsteady != 1) return fail(nullptr, DPINN_ERR_INVALID_ARG, "unsteady must be 0 or 1");
+  if (c.width != 32 && c.width != 64 && c.width != 128) return fail(nullptr, DPINN_ERR_INVALID_ARG, "width must be 32, 64 or 128");
+  if (c.depth < 1 || c.depth > dk::MAXL) return fail(nullptr, DPINN_ERR_INVALID_ARG, "depth must be in [1, 16]");
+  if (c.activation != DPINN_ACT_TANH) return fail(nullptr, DPINN_ERR_INVALID_ARG, "only tanh is supported");
+  if (c.precision != DPINN_PREC_FP32) return fail(nullptr, DPINN_ERR_INVALID_ARG, "only FP32 is supported");
+  if (!(c.nu >= 0)) return fail(nullptr, DPINN_ERR_INVALID_ARG, "nu must be >= 0");
+  const int din = c.d_space + c.unsteady;
+  int64_t nn = 1;
+  for (int a = 0; a < din; ++a) {
+    if (c.splits[a] < 1) return fail(nullptr, DPINN_ERR_INVALID_ARG, "splits must be >= 1");
+    if (!(c.hi[a] > c.lo[a])) return fail(nullptr, DPINN_ERR_INVALID_ARG, "hi must exceed lo");
+    nn *= c.splits[a];
+  }
+  if (nn > 65535) return fail(nullptr, DPINN_ERR_INVALID_ARG, "too many nets");
+  for (int a = 0; a < c.d_space; ++a)
+    if (cell_fp32(c, a, (float)c.anchor_x[a]) < 0) return fail(nullptr, DPINN_ERR_INVALID_ARG, "anchor outside the domain");
+
+  std::unique_ptr<dpinn> h(new dpinn());
+  h->cfg = c;
+  h->ds = c.d_space; h->unst = c.unsteady; h->din = din; h->dout = c.d_space + 1;
+  h->W = c.width; h->L = c.depth;
+  h->n_nets = (int)nn;
+  if (!pick_kernels(h->W, h->ds, h->unst, h->L, &h->ks)) return fail(nullptr, DPINN_ERR_INVALID_ARG, "unsupported shape");
+  // decomposition
+  int s = 1;
+  for (int a = 0; a < din; ++a) { h->stride.push_back(s); s *= c.splits[a]; }
+  for (int k = 0; k < h->n_nets; ++k) {
+    std::array<int, 4> ce{0, 0, 0, 0};
+    std::array<double, 4> lo{0, 0, 0, 0}, hi{0, 0, 0, 0};
+    int r = k;
+    for (int a = 0; a < din; ++a) {
+      ce[a] = r % c.splits[a];
+      r /= c.splits[a];
+      const double hh = (c.hi[a] - c.lo[a]) / c.splits[a];
+      lo[a] = c.lo[a] + ce[a] * hh;
+      hi[a] = c.lo[a] + (ce[a] + 1) * hh;
+    }
+    h->cell.push_back(ce); h->blo.push_back(lo); h->bhi.push_back(hi);
+  }
+  int acell[3] = {0, 0, 0};
+  for (int a = 0; a < h->ds; ++a) acell[a] = cell_fp32(c, a, (float)c.anchor_x[a]);
+  for (int k = 0; k < h->n_nets; ++k) {
+    bool mm = true;
+    for (int a = 0; a < h->ds; ++a) mm = mm && h->cell[k][a] == acell[a];
+    h->master.push_back(mm ? 1 : 0);
+  }
+  h->net_faces.resize(h->n_nets);
+  for (int a = 0; a < din; ++a)
+    for (int k = 0; k < h->n_nets; ++k)
+      if (h->cell[k][a] < c.splits[a] - 1) {
+        const int f = (int)h->faces.size();
+        h->faces.push_back({k, k + h->stride[a], a});
+        h->net_faces[k].push_back(f);
+        h->net_faces[k + h->stride[a]].push_back(f);
+      }
+  h->n_faces = (int)h->faces.size();
+  // parameter layout
+  dk::Shape& sh = h->shape;
+  std::memset(&sh, 0, sizeof(sh));
+  sh.ds = h->ds; sh.unst = h->unst; sh.din = din; sh.dout = h->dout; sh.W = h->W; sh.L = h->L;
+  int off = 0;
+  for (int l = 0; l <= h->L; ++l) {
+    const int o = (l == h->L) ? h->dout : h->W;
+    const int i = (l == 0) ? din : h->W;
+    sh.woff[l] = off; off += o * i;
+    sh.boff[l] = off; off += o;
+  }
+  h->n_params = off;
+  h->npp = ((off + 63) / 64) * 64;
+  h->nTp = std::max(1, (h->L - 1) * h->W * h->W);
+  sh.npp = h->npp; sh.nTp = h->nTp;
+  sh.nu = (float)c.nu; sh.p_ref = (float)c.p_ref;
+  for (int a = 0; a < 3; ++a) { sh.anchor[a] = (float)c.anchor_x[a]; sh.comp_w[a] = (float)c.comp_w[a]; }
+  sh.lam_obs = (float)c.lambda_obs; sh.lam_pde = (float)c.lambda_pde; sh.lam_gh_u = (float)c.lambda_gh_u;
+  sh.lam_time = (float)c.lambda_gh_p_time;
+
+  dpinn* hp = h.get();
+  CK(hp, cudaSetDevice(c.device));
+  h->dev = c.device;
+  CK(hp, cudaDeviceGetAttribute(&h->n_sms, cudaDevAttrMultiProcessorCount, c.device));
+  for (const void* fn : {h->ks.train_jet, h->ks.query_jet})
+    CK(hp, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ks.smem_jet));
+  for (const void* fn : {h->ks.train_val, h->ks.eval_val, h->ks.query_val})
+    CK(hp, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ks.smem_val));
+  const size_t NP = (size_t)h->n_nets * h->npp;
+  CK(hp, h->theta.ensure(NP)); CK(hp, h->m.ensure(NP)); CK(hp, h->v.ensure(NP)); CK(hp, h->grad.ensure(NP));
+  CK(hp, h->thetaT.ensure((size_t)h->n_nets * h->nTp));
+  const int nblk = (h->n_params + dk::NT - 1) / dk::NT;
+  CK(hp, h->norm_part.ensure((size_t)h->n_nets * nblk));
+  CK(hp, h->coef.ensure(h->n_nets));
+  CK(hp, h->step_d.ensure(1));
+  CK(hp, h->nets_d.ensure(h->n_nets));
+  CK(hp, h->face_info_d.ensure((size_t)std::max(h->n_faces, 1) * 3));
+  CK(hp, h->err_d.ensure(4)); CK(hp, h->counters.ensure(4)); CK(hp, h->n_items_d.ensure(4));
+  CK(hp, h->loss_rec.ensure((size_t)h->n_nets * 6));
+  CK(hp, h->iota_d.ensure(h->n_nets + 1));
+  CK(hp, cudaMallocHost(&h->loss_host, (size_t)h->n_nets * 6 * sizeof(float)));
+  CK(hp, cudaMemset(h->theta.p, 0, NP * 4)); CK(hp, cudaMemset(h->m.p, 0, NP * 4));
+  CK(hp, cudaMemset(h->v.p, 0, NP * 4)); CK(hp, cudaMemset(h->grad.p, 0, NP * 4));
+  CK(hp, cudaMemset(h->step_d.p, 0, sizeof(long long)));
+  CK(hp, cudaMemset(h->err_d.p, 0, 4 * sizeof(int)));
+  CK(hp, cudaMemset(h->loss_rec.p, 0, (size_t)h->n_nets * 6 * sizeof(float)));
+  CK(hp, cudaMemset(h->coef.p, 0, (size_t)h->n_nets * sizeof(float)));
+  std::vector<int> fi((size_t)std::max(h->n_faces, 1) * 3, 0);
+  for (int f = 0; f < h->n_faces; ++f) {
+    fi[f * 3] = h->faces[f][0];
+    fi[f * 3 + 1] = h->faces[f][1];
+    fi[f * 3 + 2] = (h->unst && h->faces[f][2] == h->ds) ? 1 : 0;
+  }
+  CK(hp, cudaMemcpy(h->face_info_d.p, fi.data(), fi.size() * sizeof(int), cudaMemcpyHostToDevice));
+  std::vector<int> iota(h->n_nets + 1);
+  for (int k = 0; k <= h->n_nets; ++k) iota[k] = k;
+  CK(hp, cudaMemcpy(h->iota_d.p, iota.data(), iota.size() * sizeof(int), cudaMemcpyHostToDevice));
+  // empty per-net info until points arrive
+  std::vector<dk::NetInfo> ni(h->n_nets);
+  for (int k = 0; k < h->n_nets; ++k) {
+    std::memset(&ni[k], 0, sizeof(dk::NetInfo));
+    for (int q = 0; q < din; ++q) {
+      ni[k].center[q] = (float)(0.5 * (h->blo[k][q] + h->bhi[k][q]));
+      ni[k].scale[q] = (float)(2.0 / (h->bhi[k][q] - h->blo[k][q]));
+    }
+    ni[k].master = h->master[k];
+    ni[k].lam_space = h->master[k] ? 0.f : (float)c.lambda_gh_p_space;
+  }
+  CK(hp, cudaMemcpy(h->nets_d.p, ni.data(), ni.size() * sizeof(dk::NetInfo), cudaMemcpyHostToDevice));
+  dk::k_init<<<dim3(nblk, h->n_nets), dk::NT>>>(h->shape, (uint64_t)c.seed, h->theta.p, h->n_params);
+  CK(hp, cudaGetLastError());
+  int rc = refresh_transpose(hp);
+  if (rc) { g_create_err = h->err; return rc; }
+  CK(hp, cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  CK(hp, cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming));
+  CK(hp, cudaDeviceSynchronize());
+  *out = h.release();
+  return DPINN_OK;
+}
+
+void dpinn_destroy(dpinn_t* h) {
+  if (!h) return;
+  cudaSetDevice(h->dev);
+  cudaDeviceSynchronize();
+  delete h;
+}
+
+int dpinn_get_layout(dpinn_t* h, dpinn_layout* o) {
+  if (!h || !o) return DPINN_ERR_INVALID_ARG;
+  o->n_nets = h->n_nets; o->n_faces = h->n_faces; o->d_in = h->din; o->d_out = h->dout;
+  o->n_params = h->n_params;
+  int nm = 0;
+  for (int x : h->master) nm += x;
+  o->n_masters = nm;
+  return DPINN_OK;
+}
+
+int dpinn_net_info(dpinn_t* h, int net, int* is_master, double* lo4, double* hi4) {
+  if (!h) return DPINN_ERR_INVALID_ARG;
+  if (net < 0 || net >= h->n_nets) return fail(h, DPINN_ERR_INVALID_ARG, "net out of range");
+  if (is_master) *is_master = h->master[net];
+  for (int q = 0; q < 4; ++q) {
+    if (lo4) lo4[q] = h->blo[net][q];
+    if (hi4) hi4[q] = h->bhi[net][q];
+  }
+  return DPINN_OK;
+}
+
+int dpinn_face_info(dpinn_t* h, int f, int* lo, int* hi, int* axis, int* is_time) {
+  if (!h) return DPINN_ERR_INVALID_ARG;
+  if (f < 0 || f >= h->n_faces) return fail(h, DPINN_ERR_INVALID_ARG, "face out of range");
+  if (lo) *lo = h->faces[f][0];
+  if (hi) *hi = h->faces[f][1];
+  if (axis) *axis = h->faces[f][2];
+  if (is_time) *is_time = (h->unst && h->faces[f][2] == h->ds) ? 1 : 0;
+  return DPINN_OK;
+}
+
+int dpinn_set_points(dpinn_t* h, int kind, const float* pts, const float* vals, const int64_t* counts, int n_counts) {
+  if (!h) return DPINN_ERR_INVALID_ARG;
+  if (kind < 0 || kind > 2) return fail(h, DPINN_ERR_INVALID_ARG, "bad point kind");
+  const int expect = kind == DPINN_POINTS_FACE ? h->n_faces : h->n_nets;
+  if (n_counts != expect || (!counts && expect > 0)) return fail(h, DPINN_ERR_INVALID_ARG, "counts length mismatch");
+  int64_t n = 0;
+  for (int i = 0; i < n_counts; ++i) {
+    if (counts[i] < 0) return fail(h, DPINN_ERR_INVALID_ARG, "negative count");
+    n += counts[i];
+  }
+  if (n > (int64_t)1 << 30) return fail(h, DPINN_ERR_INVALID_ARG, "too many points");
+  if (n > 0 && !pts) return fail(h, DPINN_ERR_INVALID_ARG, "null points");
+  if (kind == DPINN_POINTS_OBS && n > 0 && !vals) return fail(h, DPINN_ERR_INVALID_ARG, "null observation values");
+  CK(h, cudaSetDevice(h->dev));
+  std::vector<int64_t> cv(counts, counts + n_counts);
+  std::vector<int64_t>* dst = kind == 0 ? &h->res_counts : (kind == 1 ? &h->obs_counts : &h->face_counts);
+  const bool same = h->have[kind] && *dst == cv;
+  DevBuf<float>* pb = kind == 0 ? &h->res_pts : (kind == 1 ? &h->obs_pts : &h->face_pts);
+  if (!same) {
+    // the captured graphs reference the old buffers: drop them first
+    CK(h, cudaDeviceSynchronize());
+  }
+  CK(h, pb->ensure((size_t)std::max<int64_t>(n, 1) * h->din));
+  if (n) CK(h, cudaMemcpy(pb->p, pts, (size_t)n * h->din * sizeof(float), cudaMemcpyDefault));
+  if (kind == DPINN_POINTS_OBS) {
+    CK(h, h->obs_vals.ensure((size_t)std::max<int64_t>(n, 1) * h->ds));
+    if (n) CK(h, cudaMemcpy(h->obs_vals.p, vals, (size_t)n * h->ds * sizeof(float), cudaMemcpyDefault));
+  }
+  *dst = cv;
+  h->have[kind] = true;
+  if (same && h->plan_ok) return DPINN_OK;
+  return build_plan(h);
+}
+
+int dpinn_step(dpinn_t* h, dpinn_stream_t stream, int n_steps) {
+  if (!h) return DPINN_ERR_INVALID_ARG;
+  if (!h->plan_ok) {
+    int rc = build_plan(h);
+    if (rc) return rc;
+    if (!h->plan_ok) return fail(h, DPINN_ERR_STATE, "residual, observation and face points must be set first");
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int i = 0; i < n_steps; ++i) CK(h, cudaGraphLaunch(h->g_step, s));
+  CK(h, cudaEventRecord(h->done, s));
+  return DPINN_OK;
+}
+
+int dpinn_eval_grad(dpinn_t* h, dpinn_stream_t stream) {
+  if (!h) return DPINN_ERR_INVALID_ARG;
+  if (!h->plan_ok) {
+    int rc = build_plan(h);
+    if (rc) return rc;
+    if (!h->plan_ok) return fail(h, DPINN_ERR_STATE, "residual, observation and face points must be set first");
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(h, cudaGraphLaunch(h->g_grad, s));
+  CK(h, cudaEventRecord(h->done, s));
+  return DPINN_OK;
+}
+
+int dpinn_loss(dpinn_t* h, float* host_out) {
+  if (!h || !host_out) return DPINN_ERR_INVALID_ARG;
+  CK(h, cudaEventSynchronize(h->done));
+  CK(h, cudaMemcpy(host_out, h->loss_rec.p, (size_t)h->n_nets * 6 * sizeof(float), cudaMemcpyDeviceToHost));
+  return check_errors(h);
+}
+
+int dpinn_get_grad(dpinn_t* h, float* host_out) {
+  if (!h || !host_out) return DPINN_ERR_INVALID_ARG;
+  CK(h, cudaEventSynchronize(h->done));
+  return copy_state_out(h, host_out, h->grad.p);
+}
+
+int dpinn_get_state(dpinn_t* h, float* params, float* m, float* v, int64_t* step) {
+  if (!h) return DPINN_ERR_INVALID_ARG;
+  CK(h, cudaDeviceSynchronize());
+  int rc = DPINN_OK;
+  if (params && (rc = copy_state_out(h, params, h->theta.p))) return rc;
+  if (m && (rc = copy_state_out(h, m, h->m.p))) return rc;
+  if (v && (rc = copy_state_out(h, v, h->v.p))) return rc;
+  if (step) {
+    long long t = 0;
+    CK(h, cudaMemcpy(&t, h->step_d.p, sizeof(t), cudaMemcpyDeviceToHost));
+    *step = t;
+  }
+  return DPINN_OK;
+}
+
+int dpinn_set_state(dpinn_t* h, const float* params, const float* m, const float* v, int64_t step) {
+  if (!h) return DPINN_ERR_INVALID_ARG;
+  if (step < 0) return fail(h, DPINN_ERR_INVALID_ARG, "negative step");
+  CK(h, cudaDeviceSynchronize());
+  int rc = DPINN_OK;
+  if (params && (rc = copy_state_in(h, h->theta.p, params))) return rc;
+  if (m && (rc = copy_state_in(h, h->m.p, m))) return rc;
+  if (v && (rc = copy_state_in(h, h->v.p, v))) return rc;
+  long long t = step;
+  CK(h, cudaMemcpy(h->step_d.p, &t, sizeof(t), cudaMemcpyHostToDevice));
+  return refresh_transpose(h);
+}
+
+int dpinn_apply_grad(dpinn_t* h, const float* host_grad) {
+  if (!h || !host_grad) return DPINN_ERR_INVALID_ARG;
+  CK(h, cudaDeviceSynchronize());
+  int rc = copy_state_in(h, h->grad.p, host_grad);
+  if (rc) return rc;
+  const int nblk = (h->n_params + dk::NT - 1) / dk::NT;
+  // per-net norms of the given gradient (slot k = net k of the grad buffer)
+  dk::k_reduce_grad<<<dim3(nblk, h->n_nets), dk::NT>>>(h->grad.p, h->iota_d.p, h->grad.p, h->norm_part.p, h->npp,
+                                                        h->n_params);
+  if (h->cfg.clip_norm > 0)
+    dk::k_clip_coef<<<h->n_nets, dk::NT>>>(h->norm_part.p, nblk, (float)h->cfg.clip_norm, h->coef.p);
+  dk::AdamArgs ar{h->cfg.lr, h->cfg.beta1, h->cfg.beta2, h->cfg.eps, h->cfg.clip_norm > 0 ? 1 : 0};
+  dk::k_adam<<<dim3(nblk, h->n_nets), dk::NT>>>(h->shape, ar, h->theta.p, h->thetaT.p, h->m.p, h->v.p, h->grad.p,
+                                                 h->coef.p, h->step_d.p, h->n_params);
+  dk::k_loss_record<<<1, 32>>>(h->shape, h->loss_part.p, h->slot_begin_d.p, h->nets_d.p, 0, h->loss_rec.p,
+                                h->err_d.p, h->step_d.p, 1);
+  CK(h, cudaGetLastError());
+  CK(h, cudaDeviceSynchronize());
+  return DPINN_OK;
+}
+
+int dpinn_query(dpinn_t* h, const float* pts, int64_t n, int want_residual, float* out, dpinn_stream_t stream) {
+  if (!h) return DPINN_ERR_INVALID_ARG;
+  if (n < 0 || n > ((int64_t)1 << 30)) return fail(h, DPINN_ERR_INVALID_ARG, "bad point count");
+  if (n == 0) return DPINN_OK;
+  if (!pts || !out) return fail(h, DPINN_ERR_INVALID_ARG, "null pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int P = want_residual ? h->ks.P_jet : h->ks.P_val;
+  const int chunk = 4 * P;
+  const size_t max_items = (size_t)(n / chunk) + h->n_nets + 1;
+  CK(h, h->q_net.ensure(n));
+  CK(h, h->q_perm.ensure(n));
+  CK(h, h->q_counts.ensure(h->n_nets));
+  CK(h, h->q_off.ensure(h->n_nets));
+  CK(h, h->q_cursor.ensure(h->n_nets));
+  CK(h, h->q_nitems.ensure(2));
+  CK(h, h->q_items.ensure(max_items));
+  dk::Route rt{};
+  for (int a = 0; a < h->din; ++a) {
+    rt.lo[a] = (float)h->cfg.lo[a];
+    rt.hi[a] = (float)h->cfg.hi[a];
+    rt.inv_h[a] = (float)((double)h->cfg.splits[a] / (h->cfg.hi[a] - h->cfg.lo[a]));
+    rt.splits[a] = h->cfg.splits[a];
+    rt.stride[a] = h->stride[a];
+  }
+  rt.din = h->din;
+  rt.n_nets = h->n_nets;
+  CK(h, cudaMemsetAsync(h->q_counts.p, 0, h->n_nets * sizeof(int), s));
+  CK(h, cudaMemsetAsync(h->q_nitems.p, 0, 2 * sizeof(int), s));
+  const int nb = (int)((n + 255) / 256);
+  dk::k_route<<<nb, 256, 0, s>>>(rt, pts, n, h->q_net.p, h->q_counts.p, h->err_d.p);
+  dk::k_route_plan<<<1, 32, 0, s>>>(h->q_counts.p, h->n_nets, chunk, h->q_off.p, h->q_cursor.p, h->q_items.p,
+                                     h->q_nitems.p);
+  dk::k_route_scatter<<<nb, 256, 0, s>>>(h->q_net.p, n, h->q_cursor.p, h->q_perm.p);
+  CK(h, cudaGetLastError());
+  dk::Bufs b = make_bufs(h);
+  b.counter = h->q_nitems.p + 1;
+  b.q_pts = pts;
+  b.q_perm = h->q_perm.p;
+  b.q_out = out;
+  b.q_w = h->dout + (want_residual ? h->ds + 1 : 0);
+  const void* fn = want_residual ? h->ks.query_jet : h->ks.query_val;
+  const size_t smem = want_residual ? h->ks.smem_jet : h->ks.smem_val;
+  const int grid = (int)std::min<size_t>(max_items, (size_t)h->n_sms * occupancy(fn, smem));
+  CK(h, launch_pinn(fn, grid, smem, h->shape, b, h->q_items.p, h->q_nitems.p, s));
+  return DPINN_OK;
+}
+
+int dpinn_query_status(dpinn_t* h, dpinn_stream_t stream) {
+  if (!h) return DPINN_ERR_INVALID_ARG;
+  CK(h, cudaStreamSynchronize((cudaStream_t)stream));
+  int e[3] = {0, 0, 0};
+  CK(h, cudaMemcpy(e, h->err_d.p, sizeof(e), cudaMemcpyDeviceToHost));
+  if (e[dk::ERR_TIMEOUT]) return fail(h, DPINN_ERR_TIMEOUT, "a device wait gave up");
+  if (e[dk::ERR_DOMAIN]) {
+    CK(h, cudaMemset(h->err_d.p + dk::ERR_DOMAIN, 0, sizeof(int)));
+    return fail(h, DPINN_ERR_INVALID_ARG, "query point outside the domain");
+  }
+  return DPINN_OK;
+}
+
+int dpinn_launches_per_step(dpinn_t* h) { return h ? h->launches : 0; }
+
+int dpinn_step_timed(dpinn_t* h, dpinn_stream_t stream, float* ms, int max_kernels, int* n_kernels,
+                     const char** names) {
+  if (!h || !ms || max_kernels < 1) return DPINN_ERR_INVALID_ARG;
+  if (!h->plan_ok) {
+    int rc = build_plan(h);
+    if (rc) return rc;
+    if (!h->plan_ok) return fail(h, DPINN_ERR_STATE, "residual, observation and face points must be set first");
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t ev[9];
+  for (auto& e : ev) CK(h, cudaEventCreate(&e));
+  const char* nm[8] = {nullptr};
+  int launches = 0;
+  cudaError_t e = enqueue_step(h, true, s, &launches, ev, nm);
+  if (e == cudaSuccess) e = cudaEventRecord(h->done, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(ev[launches]);
+  const int n = std::min(launches, max_kernels);
+  for (int i = 0; e == cudaSuccess && i < n; ++i) {
+    e = cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
+    if (names) names[i] = nm[i];
+  }
+  for (auto& x : ev) cudaEventDestroy(x);
+  if (e != cudaSuccess) return cuda_fail(h, e, "dpinn_step_timed");
+  if (n_kernels) *n_kernels = n;
+  return DPINN_OK;
+}
+
+}  // extern "C"

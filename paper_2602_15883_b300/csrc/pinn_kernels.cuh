@@ -1,0 +1,975 @@
+// Device kernels of libdpinn (sm_103a).
+//
+// One persistent, grouped kernel (`k_pinn`) processes a work list of
+// (net, point-chunk) items for every subdomain net of the decomposition in a
+// single launch.  Per chunk it runs, for tiles of P points:
+//
+//   forward  - jets (value, d/dx_q for every input, spatial Laplacian) through
+//              the tanh MLP (Sec. 2.1, Eq. (2)); hidden-layer products are
+//              dense (P*C) x W x W FP32 contractions, register-tiled, with the
+//              tanh-jet recursion fused into the epilogue;
+//   loss     - Navier-Stokes residuals (Eqs. (7)-(10)) and L_PDE (Eq. (5)),
+//              or L_obs (Eq. (3)), or the ghost terms (Eqs. (13)-(14)) with
+//              the anchor-normalised neighbour pressure (Eq. (15)) and the
+//              asymmetric weights of Eq. (16);
+//   reverse  - hand-written adjoint through residual, jets and layers;
+//              weight gradients accumulate per work item (deterministic).
+//
+// The same kernel, without the reverse pass, evaluates the neighbour
+// messages of Algorithm 1 (face values and master anchor values) and serves
+// queries (values, or values + residuals, with the anchored pressure of
+// Eq. (18)).
+//
+// Shared memory holds two activation buffers [W][RS] (RS = P*C padded so that
+// rows fall on distinct banks), one weight matrix staged by a TMA bulk copy
+// (cp.async.bulk + mbarrier), and small per-net tensors.  Pre-activation jets
+// of every hidden layer are stashed per thread (coalesced) in a per-CTA
+// global scratch and re-read in the reverse pass.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dk {
+
+constexpr int NT = 256;     // threads per CTA of the grouped kernel
+constexpr int MAXL = 16;    // maximum hidden layers
+
+enum { K_PDE = 0, K_OBS = 1, K_FACE = 2, K_EVAL = 3, K_EVAL_ANC = 4, K_QUERY = 5 };
+enum { M_TRAIN = 0, M_EVAL = 1, M_QUERY = 2 };
+enum { ERR_TIMEOUT = 0, ERR_NONFINITE = 1, ERR_DOMAIN = 2 };
+
+struct Shape {
+  int ds, unst, din, dout, W, L;
+  int npp;                     // padded per-net parameter stride (floats)
+  int nTp;                     // per-net stride of the transposed hidden weights
+  int woff[MAXL + 1], boff[MAXL + 1];
+  float nu, p_ref;
+  float anchor[3];
+  float lam_obs, lam_pde, lam_gh_u, lam_time;
+  float comp_w[3];
+};
+
+struct NetInfo {
+  float center[4], scale[4];
+  float inv_npde, inv_nobs, inv_ngh, lam_space;
+  int master, pad0, pad1, pad2;
+};
+
+struct Item {
+  int kind, net, begin, count, slot, face, side, pad;
+};
+
+struct Bufs {
+  const float* theta;      // [n_nets][npp] canonical parameters
+  const float* thetaT;     // [n_nets][nTp] transposed hidden weights W_l^T
+  const NetInfo* nets;
+  const float* res_pts;
+  const float* obs_pts;
+  const float* obs_vals;
+  const float* face_pts;
+  const int* face_info;    // [n_faces][3] = net_lo, net_hi, is_time
+  float* nbr_val;          // [n_face_pts][2][dout]
+  float* nbr_anc;          // [n_face_pts][2]
+  float* grad_part;        // [n_slots][npp]
+  double* loss_part;       // [n_slots][5]
+  float* stash;            // [grid][stash_per_cta]
+  long long stash_per_cta;
+  int* counter;            // work counter (reset before each launch)
+  int* err;                // [3] error words
+  const float* q_pts;      // query points [n][din]
+  const int* q_perm;       // query segment order -> point index
+  float* q_out;            // query output rows
+  int q_w;                 // query row width
+};
+
+// ------------------------------------------------------------ tiling ---
+template <int W, int C>
+struct Tile {
+  static constexpr int TM = 4;                    // neurons per thread
+  static constexpr int NG = W / TM;               // neuron groups
+  static constexpr int PG = NT / NG;              // point groups
+  static constexpr int TP = (W == 128) ? (C == 1 ? 8 : (C == 4 ? 4 : 2))
+                          : (W == 64) ? (C == 6 ? 2 : 4)
+                          : 2;                    // points per thread
+  static constexpr int P = PG * TP;               // points per tile
+  static constexpr int NCOL = TP * C;             // columns per thread
+  static constexpr int PC = P * C;
+  static constexpr int RS = ((PC + 27) / 32) * 32 + 4;   // row stride, = 4 mod 32
+  static constexpr int VEC = (NCOL % 4 == 0) ? 4 : ((NCOL % 2 == 0) ? 2 : 1);
+  static constexpr int DI = W / 16;               // weight-gradient tile (DI x DI)
+  static constexpr int NQ = TM * NCOL / 4;        // stashed float4 per thread per layer
+  static_assert(NG >= 8 && PG >= 4 && PG * NG == NT, "tile");
+  static_assert(PC % 4 == 0, "tile columns");
+};
+
+template <int W, int C, int DOUT>
+constexpr size_t smem_floats(int L) {
+  using T = Tile<W, C>;
+  return (size_t)2 * W * T::RS + (size_t)W * W + (size_t)2 * DOUT * T::RS + (size_t)T::P * 4 +
+         (size_t)W * 4 + W + 4 + (size_t)(L > 1 ? L - 1 : 0) * W;
+}
+
+// ------------------------------------------------------- PTX helpers ---
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// One thread stages `bytes` (multiple of 16, both addresses 16-byte aligned)
+// from global memory into shared memory with a bulk async copy completing on
+// `bar`.  All earlier shared-memory reads of dst must be finished (a CTA
+// barrier precedes every call).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for phase `parity` of `bar`.  Bounded: after ~2 s of waiting the
+// kernel records ERR_TIMEOUT and continues (its results are then invalid and
+// the host reports DPINN_ERR_TIMEOUT) instead of spinning forever.
+__device__ __forceinline__ void mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+  const uint32_t a = smem_u32(bar);
+  uint64_t t0 = 0;
+  for (int it = 0;; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return;
+    if (it == 0) t0 = global_ns();
+    else if (global_ns() - t0 > 2000000000ull) {
+      atomicExch(err + ERR_TIMEOUT, 1);
+      return;
+    }
+  }
+}
+
+// ------------------------------------------------------ jet algebra ---
+// tanh jets per neuron: a = tanh(z), s1 = 1 - a^2, s2 = -2 a s1,
+// d_q a = s1 d_q z, lap a = s2 * sum_{spatial q} (d_q z)^2 + s1 * lap z.
+template <int C, int DS, int DIN>
+__device__ __forceinline__ void act_fwd(const float* z, float* a) {
+  const float t = tanhf(z[0]);
+  a[0] = t;
+  if constexpr (C > 1) {
+    const float s1 = 1.f - t * t;
+    const float s2 = -2.f * t * s1;
+    float S = 0.f;
+#pragma unroll
+    for (int q = 0; q < DS; ++q) S = fmaf(z[1 + q], z[1 + q], S);
+#pragma unroll
+    for (int q = 0; q < DIN; ++q) a[1 + q] = s1 * z[1 + q];
+    a[C - 1] = fmaf(s2, S, s1 * z[C - 1]);
+  }
+}
+
+// Adjoint of act_fwd: from the activation-jet adjoints ab to the
+// pre-activation-jet adjoints zb (s3 = d s2 / dz = -2 s1 (1 - 3 a^2)).
+template <int C, int DS, int DIN>
+__device__ __forceinline__ void act_bwd(const float* z, const float* ab, float* zb) {
+  const float t = tanhf(z[0]);
+  const float s1 = 1.f - t * t;
+  if constexpr (C == 1) {
+    zb[0] = ab[0] * s1;
+  } else {
+    const float s2 = -2.f * t * s1;
+    const float s3 = -2.f * s1 * (1.f - 3.f * t * t);
+    const float al = ab[C - 1];
+    float S = 0.f;
+#pragma unroll
+    for (int q = 0; q < DS; ++q) S = fmaf(z[1 + q], z[1 + q], S);
+    float v = fmaf(ab[0], s1, al * fmaf(s3, S, s2 * z[C - 1]));
+#pragma unroll
+    for (int q = 0; q < DIN; ++q) {
+      float g = ab[1 + q] * s1;
+      if (q < DS) g = fmaf(2.f * al * s2, z[1 + q], g);
+      zb[1 + q] = g;
+      v = fmaf(ab[1 + q] * s2, z[1 + q], v);
+    }
+    zb[0] = v;
+    zb[C - 1] = al * s1;
+  }
+}
+
+// ----------------------------------------------------- smem vectors ---
+template <int N, int VEC>
+__device__ __forceinline__ void lds_vec(float* x, const float* p) {
+  if constexpr (VEC == 4) {
+#pragma unroll
+    for (int j = 0; j < N; j += 4) {
+      float4 v = *reinterpret_cast<const float4*>(p + j);
+      x[j] = v.x; x[j + 1] = v.y; x[j + 2] = v.z; x[j + 3] = v.w;
+    }
+  } else if constexpr (VEC == 2) {
+#pragma unroll
+    for (int j = 0; j < N; j += 2) {
+      float2 v = *reinterpret_cast<const float2*>(p + j);
+      x[j] = v.x; x[j + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < N; ++j) x[j] = p[j];
+  }
+}
+
+template <int N, int VEC>
+__device__ __forceinline__ void sts_vec(float* p, const float* x) {
+  if constexpr (VEC == 4) {
+#pragma unroll
+    for (int j = 0; j < N; j += 4) *reinterpret_cast<float4*>(p + j) = make_float4(x[j], x[j + 1], x[j + 2], x[j + 3]);
+  } else if constexpr (VEC == 2) {
+#pragma unroll
+    for (int j = 0; j < N; j += 2) *reinterpret_cast<float2*>(p + j) = make_float2(x[j], x[j + 1]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < N; ++j) p[j] = x[j];
+  }
+}
+
+// acc[m][j] += sum_k Ws[k][n0 + m] * Xs[k][col0 + j],  m < 4, j < NCOL.
+// Ws rows have stride ws, Xs rows stride xs (both multiples of 4 floats).
+template <int NCOL, int VEC>
+__device__ __forceinline__ void contract(float (&acc)[4][NCOL], const float* __restrict__ Ws, int ws, int n0,
+                                         const float* __restrict__ Xs, int xs, int col0, int K) {
+#pragma unroll 2
+  for (int k = 0; k < K; ++k) {
+    const float4 w = *reinterpret_cast<const float4*>(Ws + k * ws + n0);
+    float x[NCOL];
+    lds_vec<NCOL, VEC>(x, Xs + k * xs + col0);
+#pragma unroll
+    for (int j = 0; j < NCOL; ++j) {
+      acc[0][j] = fmaf(w.x, x[j], acc[0][j]);
+      acc[1][j] = fmaf(w.y, x[j], acc[1][j]);
+      acc[2][j] = fmaf(w.z, x[j], acc[2][j]);
+      acc[3][j] = fmaf(w.w, x[j], acc[3][j]);
+    }
+  }
+}
+
+// Deterministic block sum of one float per thread (fixed tree order).
+__device__ __forceinline__ float block_sum(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  float s = 0.f;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) s += red[w];
+  }
+  return s;   // valid in thread 0
+}
+
+__device__ __forceinline__ void grad_rmw(float* g, float v, bool first) {
+  *g = first ? v : (*g + v);
+}
+
+// ------------------------------------------------------ the kernel ---
+template <int W, int DS, int UNST, bool JETS, int MODE>
+__global__ void __launch_bounds__(NT, 1)
+    k_pinn(const Shape sh, const Bufs b, const Item* __restrict__ items, const int* __restrict__ n_items_ptr) {
+  constexpr int DIN = DS + UNST;
+  constexpr int C = JETS ? DIN + 2 : 1;
+  constexpr int DOUT = DS + 1;
+  using T = Tile<W, C>;
+  constexpr int P = T::P, RS = T::RS, TP = T::TP, NCOL = T::NCOL, VEC = T::VEC, PC = T::PC;
+  constexpr int TM = 4;
+  constexpr bool TRAIN = (MODE == M_TRAIN);
+
+  extern __shared__ float4 sm4[];
+  float* const sm = reinterpret_cast<float*>(sm4);
+  float* const bufA = sm;
+  float* const bufB = bufA + W * RS;
+  float* const wbuf = bufB + W * RS;
+  float* const ysm = wbuf + W * W;
+  float* const ybsm = ysm + DOUT * RS;
+  float* const xh = ybsm + DOUT * RS;   // [P][4]
+  float* const w0s = xh + P * 4;        // [W][4]
+  float* const b0s = w0s + W * 4;       // [W]
+  float* const bLs = b0s + W;           // [4]
+  float* const bls = bLs + 4;           // [L-1][W]
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ int s_item;
+  __shared__ float s_red[NT / 32];
+  __shared__ float s_scale[4];
+  __shared__ int s_other_master, s_is_time;
+
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int ng = (warp % (T::NG / 8)) * 8 + (lane & 7);
+  const int pg = (warp / (T::NG / 8)) * 4 + (lane >> 3);
+  const int n0 = ng * TM, p0 = pg * TP, col0 = p0 * C;
+  const int L = sh.L;
+  const int n_items = *n_items_ptr;
+
+  if (t == 0) mbar_init(&mbar, 1);
+  __syncthreads();
+  uint32_t phase = 0;
+  float4* const stash = reinterpret_cast<float4*>(b.stash + (TRAIN ? (size_t)blockIdx.x * b.stash_per_cta : 0));
+
+  // thread-tile helpers ----------------------------------------------
+  auto stash_st = [&](int l, const float (&z)[TM][NCOL]) {
+    const float* zf = &z[0][0];
+#pragma unroll
+    for (int q = 0; q < T::NQ; ++q)
+      stash[((size_t)(l - 1) * T::NQ + q) * NT + t] = make_float4(zf[4 * q], zf[4 * q + 1], zf[4 * q + 2], zf[4 * q + 3]);
+  };
+  auto stash_ld = [&](int l, float (&z)[TM][NCOL]) {
+    float* zf = &z[0][0];
+#pragma unroll
+    for (int q = 0; q < T::NQ; ++q) {
+      const float4 v = stash[((size_t)(l - 1) * T::NQ + q) * NT + t];
+      zf[4 * q] = v.x; zf[4 * q + 1] = v.y; zf[4 * q + 2] = v.z; zf[4 * q + 3] = v.w;
+    }
+  };
+  // Z of the first affine map for the thread tile: z = W0 xh + b0,
+  // d_q z = s_q W0[:, q], lap z = 0.
+  auto layer0 = [&](float (&z)[TM][NCOL]) {
+#pragma unroll
+    for (int m = 0; m < TM; ++m) {
+      const int i = n0 + m;
+#pragma unroll
+      for (int pp = 0; pp < TP; ++pp) {
+        const int p = p0 + pp;
+        float v = b0s[i];
+#pragma unroll
+        for (int q = 0; q < DIN; ++q) v = fmaf(w0s[i * 4 + q], xh[p * 4 + q], v);
+        z[m][pp * C] = v;
+        if constexpr (JETS) {
+#pragma unroll
+          for (int q = 0; q < DIN; ++q) z[m][pp * C + 1 + q] = w0s[i * 4 + q] * s_scale[q];
+          z[m][pp * C + C - 1] = 0.f;
+        }
+      }
+    }
+  };
+  // activations of the thread tile into an smem buffer
+  auto act_store = [&](float* buf, const float (&z)[TM][NCOL]) {
+#pragma unroll
+    for (int m = 0; m < TM; ++m) {
+      float a[NCOL];
+#pragma unroll
+      for (int pp = 0; pp < TP; ++pp) act_fwd<C, DS, DIN>(&z[m][pp * C], &a[pp * C]);
+      sts_vec<NCOL, VEC>(buf + (n0 + m) * RS + col0, a);
+    }
+  };
+
+  for (;;) {
+    if (t == 0) s_item = atomicAdd(b.counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= n_items) break;
+    const Item item = items[it];
+    const int net = item.net;
+    const float* const th = b.theta + (size_t)net * sh.npp;
+    const float* const thT = b.thetaT + (size_t)net * sh.nTp;
+    const NetInfo ni = b.nets[net];
+    for (int e = t; e < W * DIN; e += NT) w0s[(e / DIN) * 4 + e % DIN] = th[sh.woff[0] + e];
+    for (int e = t; e < W; e += NT) b0s[e] = th[sh.boff[0] + e];
+    for (int e = t; e < (L - 1) * W; e += NT) bls[e] = th[sh.boff[1 + e / W] + e % W];
+    if (t < DOUT) bLs[t] = th[sh.boff[L] + t];
+    if (t < 4) s_scale[t] = t < DIN ? ni.scale[t] : 0.f;
+    if (t == 0) {
+      if (item.kind == K_FACE) {
+        const int other = b.face_info[item.face * 3 + (1 - item.side)];
+        s_other_master = b.nets[other].master;
+        s_is_time = b.face_info[item.face * 3 + 2];
+      } else {
+        s_other_master = 0;
+        s_is_time = 0;
+      }
+    }
+    double lsum0 = 0.0, lsum1 = 0.0;   // thread 0: loss numerators of this item
+    const int npass = (MODE == M_QUERY && ni.master) ? 2 : 1;
+
+    for (int sub = 0; sub < item.count; sub += P) {
+      const int npts = min(P, item.count - sub);
+      const bool first = (sub == 0);
+      float pkeep = 0.f;   // query: raw pressure of a master point (thread t = point)
+      float* cur = bufA;   // holds A_{L-1} after the forward
+      float* oth = bufB;
+      for (int pass = 0; pass < npass; ++pass) {
+        // ---- inputs mapped to the net's box: xh = (x - c) * s
+        if (t < P) {
+          float x[4] = {0.f, 0.f, 0.f, 0.f};
+          const bool valid = t < npts;
+          if (valid) {
+            const float* src;
+            if (MODE == M_QUERY) src = b.q_pts + (size_t)b.q_perm[item.begin + sub + t] * DIN;
+            else if (item.kind == K_PDE) src = b.res_pts + (size_t)(item.begin + sub + t) * DIN;
+            else if (item.kind == K_OBS) src = b.obs_pts + (size_t)(item.begin + sub + t) * DIN;
+            else src = b.face_pts + (size_t)(item.begin + sub + t) * DIN;
+#pragma unroll
+            for (int q = 0; q < DIN; ++q) x[q] = src[q];
+            if (pass == 1 || item.kind == K_EVAL_ANC) {
+#pragma unroll
+              for (int q = 0; q < DS; ++q) x[q] = sh.anchor[q];
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) xh[t * 4 + q] = (valid && q < DIN) ? (x[q] - ni.center[q]) * ni.scale[q] : 0.f;
+        }
+        __syncthreads();
+        if (t == 0) {
+          if (L >= 2) bulk_load(wbuf, thT, W * W * 4, &mbar);
+          else bulk_load(wbuf, th + sh.woff[L], DOUT * W * 4, &mbar);
+        }
+        // ---- forward
+        {
+          float z[TM][NCOL];
+          layer0(z);
+          act_store(bufA, z);
+        }
+        cur = bufA;
+        oth = bufB;
+        for (int l = 1; l < L; ++l) {
+          mbar_wait(&mbar, phase & 1, b.err);
+          ++phase;
+          __syncthreads();
+          float z[TM][NCOL];
+#pragma unroll
+          for (int m = 0; m < TM; ++m)
+#pragma unroll
+            for (int j = 0; j < NCOL; ++j) z[m][j] = 0.f;
+          contract<NCOL, VEC>(z, wbuf, W, n0, cur, RS, col0, W);
+#pragma unroll
+          for (int m = 0; m < TM; ++m)
+#pragma unroll
+            for (int pp = 0; pp < TP; ++pp) z[m][pp * C] += bls[(l - 1) * W + n0 + m];
+          __syncthreads();
+          if (t == 0) {
+            if (l + 1 < L) bulk_load(wbuf, thT + (size_t)l * W * W, W * W * 4, &mbar);
+            else bulk_load(wbuf, th + sh.woff[L], DOUT * W * 4, &mbar);
+          }
+          if (TRAIN) stash_st(l, z);
+          act_store(oth, z);
+          float* tmp = cur; cur = oth; oth = tmp;
+        }
+        // ---- output layer: Y[j][p][c] = W_L[j] . A[.][p][c] (+ b_L on values)
+        mbar_wait(&mbar, phase & 1, b.err);
+        ++phase;
+        __syncthreads();
+        {
+          constexpr int PAIRS = DOUT * P;
+          constexpr int KS0 = NT / PAIRS;
+          constexpr int KS = KS0 >= 4 ? 4 : (KS0 >= 2 ? 2 : 1);
+          for (int pr = t / KS; pr < PAIRS; pr += NT / KS) {
+            const int j = pr / P, p = pr % P, lk = t % KS;
+            float acc[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) acc[c] = 0.f;
+            for (int k = lk; k < W; k += KS) {
+              const float w = wbuf[j * W + k];
+#pragma unroll
+              for (int c = 0; c < C; ++c) acc[c] = fmaf(w, cur[k * RS + p * C + c], acc[c]);
+            }
+#pragma unroll
+            for (int o = KS / 2; o > 0; o >>= 1)
+#pragma unroll
+              for (int c = 0; c < C; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+            if (lk == 0) {
+#pragma unroll
+              for (int c = 0; c < C; ++c) ysm[j * RS + p * C + c] = acc[c] + (c == 0 ? bLs[j] : 0.f);
+            }
+          }
+        }
+        __syncthreads();
+        // ---- per-point epilogue
+        float l0 = 0.f, l1 = 0.f;
+        if (t < P) {
+          const int p = t;
+          const bool valid = p < npts;
+          float Y[DOUT][C];
+#pragma unroll
+          for (int j = 0; j < DOUT; ++j)
+#pragma unroll
+            for (int c = 0; c < C; ++c) Y[j][c] = ysm[j * RS + p * C + c];
+          if constexpr (MODE == M_TRAIN) {
+            float Yb[DOUT][C];
+#pragma unroll
+            for (int j = 0; j < DOUT; ++j)
+#pragma unroll
+              for (int c = 0; c < C; ++c) Yb[j][c] = 0.f;
+            if constexpr (JETS) {
+              // residuals, Eqs. (7)-(10): r_j = [d_t u_j] + u_i d_i u_j + d_j p - nu lap u_j
+              float r[DS + 1];
+#pragma unroll
+              for (int j = 0; j < DS; ++j) {
+                float v = UNST ? Y[j][1 + DS] : 0.f;
+#pragma unroll
+                for (int i = 0; i < DS; ++i) v = fmaf(Y[i][0], Y[j][1 + i], v);
+                v += Y[DS][1 + j];
+                v = fmaf(-sh.nu, Y[j][C - 1], v);
+                r[j] = v;
+              }
+              float dv = 0.f;
+#pragma unroll
+              for (int i = 0; i < DS; ++i) dv += Y[i][1 + i];
+              r[DS] = dv;
+              float r2 = 0.f;
+#pragma unroll
+              for (int j = 0; j <= DS; ++j) r2 = fmaf(r[j], r[j], r2);
+              const float sc = valid ? 2.f * sh.lam_pde * ni.inv_npde : 0.f;
+              float rb[DS + 1];
+#pragma unroll
+              for (int j = 0; j <= DS; ++j) rb[j] = sc * r[j];
+#pragma unroll
+              for (int j = 0; j < DS; ++j) {
+                if (UNST) Yb[j][1 + DS] += rb[j];
+#pragma unroll
+                for (int i = 0; i < DS; ++i) {
+                  Yb[i][0] = fmaf(rb[j], Y[j][1 + i], Yb[i][0]);
+                  Yb[j][1 + i] = fmaf(rb[j], Y[i][0], Yb[j][1 + i]);
+                }
+                Yb[DS][1 + j] += rb[j];
+                Yb[j][C - 1] = fmaf(-sh.nu, rb[j], Yb[j][C - 1]);
+              }
+#pragma unroll
+              for (int i = 0; i < DS; ++i) Yb[i][1 + i] += rb[DS];
+              l0 = valid ? r2 : 0.f;
+            } else if (item.kind == K_OBS) {
+              float e[DS];
+#pragma unroll
+              for (int c = 0; c < DS; ++c) e[c] = 0.f;
+              if (valid) {
+                const float* ov = b.obs_vals + (size_t)(item.begin + sub + p) * DS;
+#pragma unroll
+                for (int c = 0; c < DS; ++c) e[c] = Y[c][0] - ov[c];
+              }
+              float s = 0.f;
+#pragma unroll
+              for (int c = 0; c < DS; ++c) {
+                s = fmaf(sh.comp_w[c] * e[c], e[c], s);
+                Yb[c][0] = 2.f * sh.lam_obs * sh.comp_w[c] * e[c] * ni.inv_nobs;
+              }
+              l0 = s;
+            } else {   // K_FACE: own side item.side, neighbour 1 - side
+              float e[DS];
+              float ep = 0.f;
+#pragma unroll
+              for (int c = 0; c < DS; ++c) e[c] = 0.f;
+              if (valid) {
+                const size_t pt = (size_t)(item.begin + sub + p);
+                const int o = 1 - item.side;
+                const float* nv = b.nbr_val + (pt * 2 + o) * DOUT;
+#pragma unroll
+                for (int c = 0; c < DS; ++c) e[c] = Y[c][0] - nv[c];
+                float Pn = nv[DS];
+                if (s_other_master) Pn = Pn - b.nbr_anc[pt * 2 + o];   // Eq. (15)
+                ep = Y[DS][0] - Pn;
+              }
+              float su = 0.f;
+#pragma unroll
+              for (int c = 0; c < DS; ++c) {
+                su = fmaf(sh.comp_w[c] * e[c], e[c], su);
+                Yb[c][0] = 2.f * sh.lam_gh_u * sh.comp_w[c] * e[c] * ni.inv_ngh;
+              }
+              const float lam = s_is_time ? sh.lam_time : ni.lam_space;
+              Yb[DS][0] = 2.f * lam * ep * ni.inv_ngh;
+              l0 = su;
+              l1 = ep * ep;
+            }
+#pragma unroll
+            for (int j = 0; j < DOUT; ++j)
+#pragma unroll
+              for (int c = 0; c < C; ++c) ybsm[j * RS + p * C + c] = Yb[j][c];
+          } else if constexpr (MODE == M_EVAL) {
+            if (valid) {
+              const size_t pt = (size_t)(item.begin + sub + p);
+              if (item.kind == K_EVAL) {
+#pragma unroll
+                for (int j = 0; j < DOUT; ++j) b.nbr_val[(pt * 2 + item.side) * DOUT + j] = Y[j][0];
+              } else {
+                b.nbr_anc[pt * 2 + item.side] = Y[DS][0];
+              }
+            }
+          } else {   // M_QUERY
+            if (valid) {
+              float* o = b.q_out + (size_t)b.q_perm[item.begin + sub + p] * b.q_w;
+              if (pass == 0) {
+#pragma unroll
+                for (int j = 0; j < DS; ++j) o[j] = Y[j][0];
+                if (npass == 1) o[DS] = Y[DS][0] + sh.p_ref;
+                else pkeep = Y[DS][0];
+                if constexpr (JETS) {
+#pragma unroll
+                  for (int j = 0; j < DS; ++j) {
+                    float v = UNST ? Y[j][1 + DS] : 0.f;
+#pragma unroll
+                    for (int i = 0; i < DS; ++i) v = fmaf(Y[i][0], Y[j][1 + i], v);
+                    v += Y[DS][1 + j];
+                    v = fmaf(-sh.nu, Y[j][C - 1], v);
+                    o[DOUT + j] = v;
+                  }
+                  float dv = 0.f;
+#pragma unroll
+                  for (int i = 0; i < DS; ++i) dv += Y[i][1 + i];
+                  o[DOUT + DS] = dv;
+                }
+              } else {
+                o[DS] = (pkeep - Y[DS][0]) + sh.p_ref;
+              }
+            }
+          }
+        }
+        if constexpr (TRAIN) {
+          const float s0 = block_sum(l0, s_red);
+          if (t == 0) lsum0 += (double)s0;
+          if (item.kind == K_FACE) {
+            const float s1 = block_sum(l1, s_red);
+            if (t == 0) lsum1 += (double)s1;
+          }
+        }
+        __syncthreads();
+      }   // pass
+      if constexpr (!TRAIN) continue;
+
+      // ================= reverse pass =================
+      float* const g = b.grad_part + (size_t)item.slot * sh.npp;
+      // output layer: dW_L, db_L, and A_{L-1} adjoints
+      for (int e = t; e < DOUT * W; e += NT) {
+        const int j = e / W, k = e % W;
+        float s = 0.f;
+        for (int pc = 0; pc < PC; ++pc) s = fmaf(ybsm[j * RS + pc], cur[k * RS + pc], s);
+        grad_rmw(g + sh.woff[L] + e, s, first);
+      }
+      if (t < DOUT) {
+        float s = 0.f;
+        for (int p = 0; p < P; ++p) s += ybsm[t * RS + p * C];
+        grad_rmw(g + sh.boff[L] + t, s, first);
+      }
+      float* zb = oth;
+      float* ab = cur;
+      {
+        float a[TM][NCOL];
+#pragma unroll
+        for (int m = 0; m < TM; ++m)
+#pragma unroll
+          for (int j = 0; j < NCOL; ++j) a[m][j] = 0.f;
+        contract<NCOL, VEC>(a, wbuf, W, n0, ybsm, RS, col0, DOUT);
+        __syncthreads();
+        if (t == 0 && L >= 2) bulk_load(wbuf, th + sh.woff[L - 1], W * W * 4, &mbar);
+        float z[TM][NCOL];
+        if (L - 1 >= 1) stash_ld(L - 1, z); else layer0(z);
+#pragma unroll
+        for (int m = 0; m < TM; ++m) {
+          float zz[NCOL];
+#pragma unroll
+          for (int pp = 0; pp < TP; ++pp) act_bwd<C, DS, DIN>(&z[m][pp * C], &a[m][pp * C], &zz[pp * C]);
+          sts_vec<NCOL, VEC>(zb + (n0 + m) * RS + col0, zz);
+        }
+      }
+      for (int l = L - 1; l >= 1; --l) {
+        __syncthreads();
+        {   // A_{l-1} into ab
+          float z[TM][NCOL];
+          if (l - 1 >= 1) stash_ld(l - 1, z); else layer0(z);
+          act_store(ab, z);
+        }
+        __syncthreads();
+        {   // dW_l[i][k] += sum_pc Zb_l[i][pc] A_{l-1}[k][pc]
+          constexpr int DI = T::DI;
+          const int kg = t % 16, ig = t / 16;
+          float acc[DI][DI];
+#pragma unroll
+          for (int a = 0; a < DI; ++a)
+#pragma unroll
+            for (int c = 0; c < DI; ++c) acc[a][c] = 0.f;
+          for (int pc = 0; pc < PC; pc += 4) {
+            float4 zv[DI], av[DI];
+#pragma unroll
+            for (int a = 0; a < DI; ++a) zv[a] = *reinterpret_cast<const float4*>(zb + (ig + 16 * a) * RS + pc);
+#pragma unroll
+            for (int c = 0; c < DI; ++c) av[c] = *reinterpret_cast<const float4*>(ab + (kg + 16 * c) * RS + pc);
+#pragma unroll
+            for (int a = 0; a < DI; ++a)
+#pragma unroll
+              for (int c = 0; c < DI; ++c) {
+                float s = acc[a][c];
+                s = fmaf(zv[a].x, av[c].x, s);
+                s = fmaf(zv[a].y, av[c].y, s);
+                s = fmaf(zv[a].z, av[c].z, s);
+                s = fmaf(zv[a].w, av[c].w, s);
+                acc[a][c] = s;
+              }
+          }
+#pragma unroll
+          for (int a = 0; a < DI; ++a)
+#pragma unroll
+            for (int c = 0; c < DI; ++c) grad_rmw(g + sh.woff[l] + (ig + 16 * a) * W + kg + 16 * c, acc[a][c], first);
+          for (int e = t; e < W; e += NT) {
+            float s = 0.f;
+            for (int p = 0; p < P; ++p) s += zb[e * RS + p * C];
+            grad_rmw(g + sh.boff[l] + e, s, first);
+          }
+        }
+        // A_{l-1} adjoint = W_l^T Zb_l
+        mbar_wait(&mbar, phase & 1, b.err);
+        ++phase;
+        float a[TM][NCOL];
+#pragma unroll
+        for (int m = 0; m < TM; ++m)
+#pragma unroll
+          for (int j = 0; j < NCOL; ++j) a[m][j] = 0.f;
+        contract<NCOL, VEC>(a, wbuf, W, n0, zb, RS, col0, W);
+        __syncthreads();
+        if (t == 0 && l - 1 >= 1) bulk_load(wbuf, th + sh.woff[l - 1], W * W * 4, &mbar);
+        float z[TM][NCOL];
+        if (l - 1 >= 1) stash_ld(l - 1, z); else layer0(z);
+#pragma unroll
+        for (int m = 0; m < TM; ++m) {
+          float zz[NCOL];
+#pragma unroll
+          for (int pp = 0; pp < TP; ++pp) act_bwd<C, DS, DIN>(&z[m][pp * C], &a[m][pp * C], &zz[pp * C]);
+          sts_vec<NCOL, VEC>(zb + (n0 + m) * RS + col0, zz);
+        }
+      }
+      __syncthreads();
+      // first affine map: dW_0[i][q] += sum_p (Zb_val xh_q + s_q Zb_q), db_0
+      for (int e = t; e < W * DIN; e += NT) {
+        const int i = e / DIN, q = e % DIN;
+        float s = 0.f;
+        for (int p = 0; p < P; ++p) {
+          s = fmaf(zb[i * RS + p * C], xh[p * 4 + q], s);
+          if constexpr (JETS) s = fmaf(s_scale[q], zb[i * RS + p * C + 1 + q], s);
+        }
+        grad_rmw(g + sh.woff[0] + e, s, first);
+      }
+      for (int e = t; e < W; e += NT) {
+        float s = 0.f;
+        for (int p = 0; p < P; ++p) s += zb[e * RS + p * C];
+        grad_rmw(g + sh.boff[0] + e, s, first);
+      }
+      __syncthreads();
+    }   // sub-tiles
+    if (TRAIN && t == 0) {
+      double* lp = b.loss_part + (size_t)item.slot * 5;
+      for (int q = 0; q < 5; ++q) lp[q] = 0.0;
+      if (item.kind == K_PDE) lp[1] = lsum0;
+      else if (item.kind == K_OBS) lp[0] = lsum0;
+      else {
+        lp[2] = lsum0;
+        lp[s_is_time ? 4 : 3] = lsum1;
+      }
+    }
+  }   // items
+}
+
+// ----------------------------------------------- reduction + Adam ---
+// grad[k][j] = sum over the work items of net k (fixed order); per-block
+// partial squared norms for clipping.
+__global__ void k_reduce_grad(const float* __restrict__ part, const int* __restrict__ slot_begin,
+                              float* __restrict__ grad, float* __restrict__ norm_part, int npp, int n_params) {
+  __shared__ float red[NT / 32];
+  const int k = blockIdx.y;
+  const int j = blockIdx.x * NT + threadIdx.x;
+  float gsum = 0.f;
+  if (j < n_params) {
+    const int s0 = slot_begin[k], s1 = slot_begin[k + 1];
+    for (int s = s0; s < s1; ++s) gsum += part[(size_t)s * npp + j];
+    grad[(size_t)k * npp + j] = gsum;
+  }
+  const float tot = block_sum(gsum * gsum, red);
+  if (threadIdx.x == 0) norm_part[(size_t)k * gridDim.x + blockIdx.x] = tot;
+}
+
+// Per-net clip coefficient min(1, clip / (||g|| + 1e-6)), fixed-order sum.
+__global__ void k_clip_coef(const float* __restrict__ norm_part, int nblk, float clip, float* __restrict__ coef) {
+  __shared__ float red[NT / 32];
+  const int k = blockIdx.x;
+  float s = 0.f;
+  for (int i = threadIdx.x; i < nblk; i += NT) s += norm_part[(size_t)k * nblk + i];
+  const float tot = block_sum(s, red);
+  if (threadIdx.x == 0) {
+    const float c = clip / (sqrtf(tot) + 1e-6f);
+    coef[k] = c < 1.f ? c : 1.f;
+  }
+}
+
+struct AdamArgs {
+  double lr, beta1, beta2, eps;
+  int use_clip;
+};
+
+// Adam (PyTorch's rule) on every parameter of every net; rewrites the
+// transposed copies of the hidden weights used by the forward pass.
+__global__ void k_adam(const Shape sh, AdamArgs ar, float* __restrict__ theta, float* __restrict__ thetaT,
+                       float* __restrict__ m, float* __restrict__ v, const float* __restrict__ grad,
+                       const float* __restrict__ coef, const long long* __restrict__ step, int n_params) {
+  __shared__ float s_c[4];
+  if (threadIdx.x == 0) {
+    const double t = (double)(*step + 1);
+    const double bc1 = 1.0 - pow(ar.beta1, t);
+    const double bc2 = 1.0 - pow(ar.beta2, t);
+    s_c[0] = (float)(ar.lr / bc1);
+    s_c[1] = (float)(1.0 / sqrt(bc2));
+  }
+  __syncthreads();
+  const int k = blockIdx.y;
+  const int j = blockIdx.x * NT + threadIdx.x;
+  if (j >= n_params) return;
+  const size_t idx = (size_t)k * sh.npp + j;
+  float gj = grad[idx];
+  if (ar.use_clip) gj *= coef[k];
+  const float b1 = (float)ar.beta1, b2 = (float)ar.beta2;
+  const float mj = fmaf(b1, m[idx], (1.f - b1) * gj);
+  const float vj = fmaf(b2, v[idx], (1.f - b2) * gj * gj);
+  m[idx] = mj;
+  v[idx] = vj;
+  const float denom = sqrtf(vj) * s_c[1] + (float)ar.eps;
+  const float th = theta[idx] - s_c[0] * (mj / denom);
+  theta[idx] = th;
+  const int W = sh.W;
+  for (int l = 1; l < sh.L; ++l) {
+    if (j >= sh.woff[l] && j < sh.boff[l]) {
+      const int r = j - sh.woff[l], i = r / W, c = r % W;
+      thetaT[(size_t)k * sh.nTp + (size_t)(l - 1) * W * W + (size_t)c * W + i] = th;
+    }
+  }
+}
+
+// Rebuild the transposed hidden weights from theta (after set_state/init).
+__global__ void k_transpose(const Shape sh, const float* __restrict__ theta, float* __restrict__ thetaT) {
+  const int k = blockIdx.y;
+  const int W = sh.W;
+  const int e = blockIdx.x * NT + threadIdx.x;
+  if (e >= (sh.L - 1) * W * W) return;
+  const int l = 1 + e / (W * W), r = e % (W * W), i = r / W, c = r % W;
+  thetaT[(size_t)k * sh.nTp + (size_t)(l - 1) * W * W + (size_t)c * W + i] = theta[(size_t)k * sh.npp + sh.woff[l] + r];
+}
+
+// Loss record per net: fixed-order sum of the item partials, 1/N factors,
+// weighted total (Eq. (16)); non-finite values raise ERR_NONFINITE.
+__global__ void k_loss_record(const Shape sh, const double* __restrict__ loss_part, const int* __restrict__ slot_begin,
+                              const NetInfo* __restrict__ nets, int n_nets, float* __restrict__ rec, int* err,
+                              long long* step, int bump) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k == 0 && bump) *step += 1;
+  if (k >= n_nets) return;
+  double s[5] = {0, 0, 0, 0, 0};
+  for (int i = slot_begin[k]; i < slot_begin[k + 1]; ++i)
+    for (int q = 0; q < 5; ++q) s[q] += loss_part[(size_t)i * 5 + q];
+  const NetInfo ni = nets[k];
+  const double lo = s[0] * ni.inv_nobs, lp = s[1] * ni.inv_npde, lu = s[2] * ni.inv_ngh,
+               ls = s[3] * ni.inv_ngh, lt = s[4] * ni.inv_ngh;
+  const double tot = sh.lam_obs * lo + sh.lam_pde * lp + sh.lam_gh_u * lu + ni.lam_space * ls + sh.lam_time * lt;
+  const double v[6] = {lo, lp, lu, ls, lt, tot};
+  for (int q = 0; q < 6; ++q) {
+    rec[k * 6 + q] = (float)v[q];
+    if (!isfinite(v[q])) atomicExch(err + ERR_NONFINITE, 1);
+  }
+}
+
+// ----------------------------------------------------------- routing ---
+struct Route {
+  float lo[4], hi[4], inv_h[4];
+  int splits[4], stride[4];
+  int din, n_nets;
+};
+
+// Cell of every query point (float32 rule of the C ABI) and per-net counts.
+__global__ void k_route(const Route rt, const float* __restrict__ pts, long long n, int* __restrict__ net_of,
+                        int* __restrict__ counts, int* err) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int net = 0;
+  bool ok = true;
+  for (int a = 0; a < rt.din; ++a) {
+    const float x = pts[i * rt.din + a];
+    if (!(x >= rt.lo[a] && x <= rt.hi[a])) { ok = false; break; }
+    const float q = __fmul_rn(__fsub_rn(x, rt.lo[a]), rt.inv_h[a]);
+    int c = (int)floorf(q);
+    c = c < 0 ? 0 : (c > rt.splits[a] - 1 ? rt.splits[a] - 1 : c);
+    net += c * rt.stride[a];
+  }
+  if (!ok) {
+    net_of[i] = -1;
+    atomicExch(err + ERR_DOMAIN, 1);
+    return;
+  }
+  net_of[i] = net;
+  atomicAdd(counts + net, 1);
+}
+
+// Single block: segment offsets per net and the query work items (chunks of
+// `chunk` points); cursor[] starts at the offsets for the scatter.
+__global__ void k_route_plan(const int* __restrict__ counts, int n_nets, int chunk, int* __restrict__ offsets,
+                             int* __restrict__ cursor, Item* __restrict__ items, int* __restrict__ n_items) {
+  if (threadIdx.x != 0) return;
+  int off = 0, ni = 0;
+  for (int k = 0; k < n_nets; ++k) {
+    offsets[k] = off;
+    cursor[k] = off;
+    const int c = counts[k];
+    for (int s = 0; s < c; s += chunk) {
+      Item it;
+      it.kind = K_QUERY; it.net = k; it.begin = off + s; it.count = min(chunk, c - s);
+      it.slot = 0; it.face = 0; it.side = 0; it.pad = 0;
+      items[ni++] = it;
+    }
+    off += c;
+  }
+  *n_items = ni;
+}
+
+__global__ void k_route_scatter(const int* __restrict__ net_of, long long n, int* __restrict__ cursor,
+                                int* __restrict__ perm) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int k = net_of[i];
+  if (k < 0) return;
+  perm[atomicAdd(cursor + k, 1)] = (int)i;
+}
+
+// --------------------------------------------------- initialisation ---
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+// Xavier-normal weights (std sqrt(2/(fan_in+fan_out))), zero biases; normal
+// deviates by Box-Muller from a SplitMix64 counter stream keyed by
+// (seed, net, parameter index).
+__global__ void k_init(const Shape sh, uint64_t seed, float* __restrict__ theta, int n_params) {
+  const int k = blockIdx.y;
+  const int j = blockIdx.x * NT + threadIdx.x;
+  if (j >= n_params) return;
+  float val = 0.f;
+  for (int l = 0; l <= sh.L; ++l) {
+    const int fo = (l == sh.L) ? sh.dout : sh.W;
+    const int fi = (l == 0) ? sh.din : sh.W;
+    if (j >= sh.woff[l] && j < sh.boff[l]) {
+      const uint64_t key = splitmix64(seed ^ splitmix64(((uint64_t)k << 32) | (uint64_t)j));
+      const uint64_t r2 = splitmix64(key);
+      const double u1 = ((key >> 11) + 1.0) * (1.0 / 9007199254740993.0);
+      const double u2 = (r2 >> 11) * (1.0 / 9007199254740992.0);
+      const double nrm = sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+      val = (float)(nrm * sqrt(2.0 / (fi + fo)));
+    }
+  }
+  theta[(size_t)k * sh.npp + j] = val;
+}
+
+}  // namespace dk
