@@ -810,6 +810,8 @@ struct AdamArgs {
   double lr, beta1, beta2, eps;
   int use_clip;
 };
+// (1 - beta) factors are formed in double on the host and rounded once:
+// 1.f - 0.999f would carry a 1.3e-5 relative error into the second moment.
 
 // Adam (PyTorch's rule) on every parameter of every net; rewrites the
 // transposed copies of the hidden weights used by the forward pass.
@@ -832,8 +834,9 @@ __global__ void k_adam(const Shape sh, AdamArgs ar, float* __restrict__ theta, f
   float gj = grad[idx];
   if (ar.use_clip) gj *= coef[k];
   const float b1 = (float)ar.beta1, b2 = (float)ar.beta2;
-  const float mj = fmaf(b1, m[idx], (1.f - b1) * gj);
-  const float vj = fmaf(b2, v[idx], (1.f - b2) * gj * gj);
+  const float omb1 = (float)(1.0 - ar.beta1), omb2 = (float)(1.0 - ar.beta2);
+  const float mj = fmaf(b1, m[idx], omb1 * gj);
+  const float vj = fmaf(b2, v[idx], omb2 * gj * gj);
   m[idx] = mj;
   v[idx] = vj;
   const float denom = sqrtf(vj) * s_c[1] + (float)ar.eps;

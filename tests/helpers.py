@@ -57,3 +57,34 @@ def random_points_around(cfg, k, n, seed=0, pad=0.2):
     rng = np.random.default_rng(seed)
     span = hi - lo
     return lo - pad * span + (1 + 2 * pad) * span * rng.uniform(size=(n, lo.size))
+
+
+def residual_term_scale(Y, cfg):
+    """Per point and equation, the sum of magnitudes of the terms of the
+    residual, from jets Y [n][d_out][C] (channels: value, d/dx_q, Laplacian)."""
+    ds, unst, nu = cfg["d_space"], cfg["unsteady"], cfg["nu"]
+    C = Y.shape[2]
+    s = np.zeros((len(Y), ds + 1))
+    for j in range(ds):
+        s[:, j] = np.abs(Y[:, ds, 1 + j]) + nu * np.abs(Y[:, j, C - 1])
+        if unst:
+            s[:, j] += np.abs(Y[:, j, 1 + ds])
+        for i in range(ds):
+            s[:, j] += np.abs(Y[:, i, 0] * Y[:, j, 1 + i])
+    s[:, ds] = sum(np.abs(Y[:, i, 1 + i]) for i in range(ds))
+    return s
+
+
+def residual_error(gpu_r, ref_r, scale):
+    """L2 error of residuals relative to the L2 norm of their term magnitudes."""
+    return np.linalg.norm((np.asarray(gpu_r, np.float64) - ref_r).ravel()) / np.linalg.norm(scale.ravel())
+
+
+def query_jets(ora, th, pts, nets):
+    """Oracle jets [n][d_out][C] at routed query points."""
+    npar = ora.n_params
+    out = np.zeros((len(pts), ora.d_out, ora.C))
+    for k in np.unique(nets):
+        sel = nets == k
+        out[sel] = ora.forward(int(k), th[k * npar:(k + 1) * npar], pts[sel].astype(np.float64))
+    return out

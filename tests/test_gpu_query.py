@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 from paper_2602_15883_b300 import synth
-from tests.helpers import rel_l2
+from tests.helpers import query_jets, rel_l2, residual_error, residual_term_scale
 from tests.test_gpu_parity import _gpu, small_case
 
 pytestmark = pytest.mark.gpu
@@ -33,10 +33,16 @@ def test_query_matches_oracle(name, want_res):
     pts = synth.query_points(cfg, 3001, seed=4)
     out = d.query(torch.from_numpy(pts).cuda(), want_residual=want_res).cpu().numpy()
     ora = oracle.Oracle(cfg, pb)
-    ref, nets, st = ora.query(np.asarray(pb.theta0, np.float64), pts, want_res=want_res)
+    th = np.asarray(pb.theta0, np.float64)
+    ref, nets, st = ora.query(th, pts, want_res=want_res)
     assert st == 0
-    for c in range(ref.shape[1]):
+    do = ora.d_out
+    for c in range(do):
         assert rel_l2(out[:, c], ref[:, c]) <= 1e-5, (c, rel_l2(out[:, c], ref[:, c]))
+    if want_res:
+        scale = residual_term_scale(query_jets(ora, th, pts, nets), cfg)
+        err = residual_error(out[:, do:], ref[:, do:], scale)
+        assert err <= 1e-5, err
 
 
 def test_anchor_identity_and_p_ref():
@@ -90,9 +96,12 @@ def test_boundary_points_route_like_oracle():
         pts[sel, a] = rng.choice(edges, sel.sum())
     out = d.query(torch.from_numpy(pts).cuda(), want_residual=True).cpu().numpy()
     ora = oracle.Oracle(cfg, pb)
-    ref, nets, st = ora.query(np.asarray(pb.theta0, np.float64), pts, want_res=True)
+    th = np.asarray(pb.theta0, np.float64)
+    ref, nets, st = ora.query(th, pts, want_res=True)
     assert st == 0
-    assert rel_l2(out, ref) <= 1e-5
+    assert rel_l2(out[:, :4], ref[:, :4]) <= 1e-5
+    scale = residual_term_scale(query_jets(ora, th, pts, nets), cfg)
+    assert residual_error(out[:, 4:], ref[:, 4:], scale) <= 1e-5
 
 
 def test_batch_invariance_alone_vs_mixed():
