@@ -173,6 +173,29 @@ int dpinn_get_grad(dpinn_t* h, float* host_out);
  * (INVALID_ARG); its row is left untouched. */
 int dpinn_query(dpinn_t* h, const float* dev_pts, int64_t n, int want_residual,
                 float* dev_out, dpinn_stream_t stream);
+/* Same as dpinn_query, for callers that must not allocate device memory
+ * while serving: a latency-bound loop that cannot afford the device-wide
+ * synchronisation a cudaMalloc implies, or code whose device memory is owned
+ * by another framework's allocator.  dpinn_query grows handle-owned scratch
+ * with cudaMalloc when a request is larger than any before it; this variant
+ * calls no cudaMalloc, cudaFree or allocating library routine.  Its scratch
+ * is one fixed array in device memory (about 2.4 MB) that every GPU loading
+ * this library holds until the process exits.  (The paper has no
+ * counterpart: this is a serving convenience.)
+ *   - n <= 262144 points per call and at most 4096 nets, else INVALID_ARG
+ *     with a message; pts/out are device pointers owned by the caller.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device made current); make that first call
+ *     before any stream capture.
+ *   - All calls share the one array and leave their contents in it; each
+ *     call clears what must start at zero.  Calls that overlap on the GPU
+ *     (different streams, or several handles on one device) race on it:
+ *     issue them on one stream or serialise them.
+ *   - Errors of points outside the domain are reported by
+ *     dpinn_query_status, as for dpinn_query. */
+int dpinn_query_static(dpinn_t* h, const float* dev_pts, int64_t n, int want_residual,
+                       float* dev_out, dpinn_stream_t stream);
+
 /* Synchronise `stream` and report (then clear) out-of-domain errors. */
 int dpinn_query_status(dpinn_t* h, dpinn_stream_t stream);
 

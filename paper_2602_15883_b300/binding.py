@@ -26,7 +26,7 @@ EXPORTS = (
     "dpinn_config_default", "dpinn_create", "dpinn_destroy", "dpinn_last_error", "dpinn_get_layout",
     "dpinn_net_info", "dpinn_face_info", "dpinn_set_points", "dpinn_step", "dpinn_eval_grad", "dpinn_loss",
     "dpinn_get_grad", "dpinn_query", "dpinn_query_status", "dpinn_get_state", "dpinn_set_state",
-    "dpinn_apply_grad", "dpinn_launches_per_step", "dpinn_step_timed",
+    "dpinn_apply_grad", "dpinn_launches_per_step", "dpinn_step_timed", "dpinn_query_static",
 )
 
 
@@ -88,6 +88,7 @@ def load_library(path: str = LIB_PATH):
         "dpinn_apply_grad": ([vp, vp], i32),
         "dpinn_launches_per_step": ([vp], i32),
         "dpinn_step_timed": ([vp, vp, vp, i32, vp, vp], i32),
+        "dpinn_query_static": ([vp, vp, i64, i32, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -817,6 +818,108 @@ int dpinn_query(dpinn_t* h, const float* pts, int64_t n, int want_residual, floa
   const size_t smem = want_residual ? h->ks.smem_jet : h->ks.smem_val;
   const int grid = (int)std::min<size_t>(max_items, (size_t)h->n_sms * occupancy(fn, smem));
   CK(h, launch_pinn(fn, grid, smem, h->shape, b, h->q_items.p, h->q_nitems.p, s));
+  return DPINN_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// Scratch of dpinn_query_static: one fixed-size array in device memory,
+// reserved on every GPU that loads this library until the process exits.
+// Layout (byte offsets, each part 256-byte aligned): the net of each point,
+// the points ordered by net, per-net counts / segment starts / scatter
+// cursors, the work-item count, the work items.
+constexpr int64_t QS_MAX_POINTS = 262144;
+constexpr int QS_MAX_NETS = 4096;
+constexpr int QS_MAX_ITEMS = (int)(QS_MAX_POINTS / 64) + QS_MAX_NETS + 1;   // chunks are >= 64 points
+constexpr size_t QS_OFF_NET = 0;
+constexpr size_t QS_OFF_PERM = QS_OFF_NET + QS_MAX_POINTS * sizeof(int);
+constexpr size_t QS_OFF_COUNTS = QS_OFF_PERM + QS_MAX_POINTS * sizeof(int);
+constexpr size_t QS_OFF_OFFSETS = QS_OFF_COUNTS + QS_MAX_NETS * sizeof(int);
+constexpr size_t QS_OFF_CURSOR = QS_OFF_OFFSETS + QS_MAX_NETS * sizeof(int);
+constexpr size_t QS_OFF_NITEMS = QS_OFF_CURSOR + QS_MAX_NETS * sizeof(int);
+constexpr size_t QS_OFF_ITEMS = QS_OFF_NITEMS + 256;
+constexpr size_t QS_BYTES = QS_OFF_ITEMS + (size_t)QS_MAX_ITEMS * sizeof(dk::Item);
+
+static __device__ __align__(256) unsigned char g_query_scratch[QS_BYTES];
+
+// Device address of g_query_scratch per device ordinal, looked up once per
+// device (the symbol's host-side name is not a device address).
+std::mutex g_qs_mu;
+void* g_qs_addr[256] = {nullptr};
+
+int query_scratch_address(dpinn* h, void** out) {
+  std::lock_guard<std::mutex> lock(g_qs_mu);
+  if (h->dev < 0 || h->dev >= 256) return fail(h, DPINN_ERR_INVALID_ARG, "device ordinal out of range");
+  if (!g_qs_addr[h->dev]) {
+    int cur = 0;
+    CK(h, cudaGetDevice(&cur));
+    if (cur != h->dev) CK(h, cudaSetDevice(h->dev));
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_query_scratch);
+    if (cur != h->dev) cudaSetDevice(cur);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGetSymbolAddress(g_query_scratch)");
+    g_qs_addr[h->dev] = p;
+  }
+  *out = g_qs_addr[h->dev];
+  return DPINN_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int dpinn_query_static(dpinn_t* h, const float* pts, int64_t n, int want_residual, float* out,
+                       dpinn_stream_t stream) {
+  if (!h) return DPINN_ERR_INVALID_ARG;
+  if (n < 0 || n > QS_MAX_POINTS)
+    return fail(h, DPINN_ERR_INVALID_ARG, "dpinn_query_static serves at most 262144 points per call");
+  if (h->n_nets > QS_MAX_NETS)
+    return fail(h, DPINN_ERR_INVALID_ARG, "dpinn_query_static serves ensembles of at most 4096 nets");
+  if (n == 0) return DPINN_OK;
+  if (!pts || !out) return fail(h, DPINN_ERR_INVALID_ARG, "null pointer");
+  void* base = nullptr;
+  int rc = query_scratch_address(h, &base);
+  if (rc) return rc;
+  char* sb = static_cast<char*>(base);
+  int* net_of = reinterpret_cast<int*>(sb + QS_OFF_NET);
+  int* perm = reinterpret_cast<int*>(sb + QS_OFF_PERM);
+  int* counts = reinterpret_cast<int*>(sb + QS_OFF_COUNTS);
+  int* offsets = reinterpret_cast<int*>(sb + QS_OFF_OFFSETS);
+  int* cursor = reinterpret_cast<int*>(sb + QS_OFF_CURSOR);
+  int* nitems = reinterpret_cast<int*>(sb + QS_OFF_NITEMS);
+  dk::Item* items = reinterpret_cast<dk::Item*>(sb + QS_OFF_ITEMS);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int P = want_residual ? h->ks.P_jet : h->ks.P_val;
+  const int chunk = 4 * P;   // >= 64, so at most QS_MAX_ITEMS items
+  const size_t max_items = (size_t)(n / chunk) + h->n_nets + 1;
+  dk::Route rt{};
+  for (int a = 0; a < h->din; ++a) {
+    rt.lo[a] = (float)h->cfg.lo[a];
+    rt.hi[a] = (float)h->cfg.hi[a];
+    rt.inv_h[a] = (float)((double)h->cfg.splits[a] / (h->cfg.hi[a] - h->cfg.lo[a]));
+    rt.splits[a] = h->cfg.splits[a];
+    rt.stride[a] = h->stride[a];
+  }
+  rt.din = h->din;
+  rt.n_nets = h->n_nets;
+  // the array keeps the previous call's contents: clear the counters
+  CK(h, cudaMemsetAsync(counts, 0, h->n_nets * sizeof(int), s));
+  CK(h, cudaMemsetAsync(nitems, 0, 2 * sizeof(int), s));
+  const int nb = (int)((n + 255) / 256);
+  dk::k_route<<<nb, 256, 0, s>>>(rt, pts, n, net_of, counts, h->err_d.p);
+  dk::k_route_plan<<<1, 32, 0, s>>>(counts, h->n_nets, chunk, offsets, cursor, items, nitems);
+  dk::k_route_scatter<<<nb, 256, 0, s>>>(net_of, n, cursor, perm);
+  CK(h, cudaGetLastError());
+  dk::Bufs b = make_bufs(h);
+  b.counter = nitems + 1;
+  b.q_pts = pts;
+  b.q_perm = perm;
+  b.q_out = out;
+  b.q_w = h->dout + (want_residual ? h->ds + 1 : 0);
+  const void* fn = want_residual ? h->ks.query_jet : h->ks.query_val;
+  const size_t smem = want_residual ? h->ks.smem_jet : h->ks.smem_val;
+  const int grid = (int)std::min<size_t>(max_items, (size_t)h->n_sms * occupancy(fn, smem));
+  CK(h, launch_pinn(fn, grid, smem, h->shape, b, items, nitems, s));
   return DPINN_OK;
 }
 
