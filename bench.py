@@ -58,41 +58,63 @@ class Clocks:
     def __init__(self, gpu):
         self.gpu = gpu
         self.p = None
+        self.rows = []
+        self.window = None
 
-    def __enter__(self):
+    def start(self):
+        """Start sampling (every 100 ms); give nvidia-smi a second to come up."""
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
-                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True, bufsize=1)
         except OSError:
             self.p = None
-        return self
+            return
+        import threading
+        self._stamped = []
 
-    def __exit__(self, *a):
-        self.rows = []
+        def reader():
+            for line in self.p.stdout:
+                self._stamped.append((time.time(), line))
+        self._t = threading.Thread(target=reader, daemon=True)
+        self._t.start()
+        time.sleep(1.0)
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
+
+    def stop(self):
         if self.p is None:
             return
+        time.sleep(0.3)
         self.p.terminate()
         try:
-            out, _ = self.p.communicate(timeout=5)
+            self.p.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.p.kill()
-            out, _ = self.p.communicate()
-        for line in out.strip().splitlines():
+        self._t.join(timeout=2)
+        t0, t1 = self.window or (0, 1e30)
+        stamped = [(t, l) for t, l in self._stamped]
+        inside = [l for t, l in stamped if t0 - 0.15 <= t <= t1 + 0.15]
+        if not inside and stamped:   # region shorter than the sampling period
+            mid = 0.5 * (t0 + t1)
+            inside = [min(stamped, key=lambda x: abs(x[0] - mid))[1]]
+        for line in inside:
             f = [x.strip() for x in line.split(",")]
             if len(f) >= 9:
                 self.rows.append(f)
 
     def summary(self):
-        if not getattr(self, "rows", None):
+        if not self.rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
-        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        num = lambda x: x.replace(".", "", 1).isdigit()
+        sm = [float(r[1]) for r in self.rows if num(r[1])]
+        mx = [float(r[2]) for r in self.rows if num(r[2])]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        pw = [float(r[3]) for r in self.rows if num(r[3])]
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows),
-                "power_w_max": max(float(r[3]) for r in self.rows) if self.rows else None}
+                "reasons": reasons, "samples": len(self.rows), "power_w_max": max(pw) if pw else None}
 
 
 def peaks():
@@ -216,16 +238,19 @@ def main():
     # ---- device-timed region
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clk = Clocks(local)
+    clk.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    with Clocks(local) as clk:
-        for i in range(args.steps):
-            flush.fill_(float(i))
-            starts[i].record(stream)
-            d.step(1, stream)
-            ends[i].record(stream)
-        torch.cuda.synchronize()
+    w0 = time.time()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        d.step(1, stream)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    clk.mark(w0, time.time())
     if dist:
         dist.barrier()
     ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
@@ -247,6 +272,7 @@ def main():
             kt.setdefault(k, []).append(v)
     kms = {k: float(np.mean(v)) for k, v in kt.items()}
     jet_ms = kms.get("train_jet", float("nan"))
+    clk.stop()
     clocks = clk.summary()
     pk, pk_kind = peaks()
     sm_mhz = float(pk.get("sm_max_mhz", 2032.0))

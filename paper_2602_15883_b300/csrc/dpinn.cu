@@ -47,8 +47,8 @@ KernelSet make_set(int L) {
   k.smem_val = dk::smem_floats<W, 1, DOUT>(L) * sizeof(float);
   k.P_jet = dk::Tile<W, CJ>::P;
   k.P_val = dk::Tile<W, 1>::P;
-  k.stash_jet = (long long)(L > 1 ? L - 1 : 0) * dk::Tile<W, CJ>::NQ * dk::NT * 4;
-  k.stash_val = (long long)(L > 1 ? L - 1 : 0) * dk::Tile<W, 1>::NQ * dk::NT * 4;
+  k.stash_jet = (long long)L * dk::Tile<W, CJ>::NQ * dk::NT * 4;
+  k.stash_val = (long long)L * dk::Tile<W, 1>::NQ * dk::NT * 4;
   return k;
 }
 

@@ -22,9 +22,10 @@
 //
 // Shared memory holds two activation buffers [W][RS] (RS = P*C padded so that
 // rows fall on distinct banks), one weight matrix staged by a TMA bulk copy
-// (cp.async.bulk + mbarrier), and small per-net tensors.  Pre-activation jets
-// of every hidden layer are stashed per thread (coalesced) in a per-CTA
-// global scratch and re-read in the reverse pass.
+// (cp.async.bulk + mbarrier), and small per-net tensors.  For every layer the
+// jets (tanh value, first derivatives and Laplacian of the pre-activation)
+// are stashed per thread (coalesced) in a per-CTA global scratch and re-read
+// in the reverse pass, which therefore evaluates no tanh.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -83,23 +84,43 @@ struct Bufs {
 };
 
 // ------------------------------------------------------------ tiling ---
+// Register tiles.  Shared memory delivers 128 B per clock per SM whatever
+// the broadcast, against 128 FFMA per clock, so a thread tile needs >= 4 FMA
+// per float it loads: TM neurons x (TP points x C channels) gives
+// TM*NCOL / (TM + NCOL).  W = 64 uses 8 neurons per thread; W = 128 is held
+// to 4 by the shared-memory capacity of its activation buffers.
 template <int W, int C>
 struct Tile {
-  static constexpr int TM = 4;                    // neurons per thread
+  static constexpr int TM = (W == 64) ? 8 : 4;    // neurons per thread
   static constexpr int NG = W / TM;               // neuron groups
   static constexpr int PG = NT / NG;              // point groups
   static constexpr int TP = (W == 128) ? (C == 1 ? 8 : (C == 4 ? 4 : 2))
-                          : (W == 64) ? (C == 6 ? 2 : 4)
+                          : (W == 64) ? (C == 1 ? 4 : (C == 6 ? 1 : 2))
                           : 2;                    // points per thread
   static constexpr int P = PG * TP;               // points per tile
   static constexpr int NCOL = TP * C;             // columns per thread
   static constexpr int PC = P * C;
-  static constexpr int RS = ((PC + 27) / 32) * 32 + 4;   // row stride, = 4 mod 32
   static constexpr int VEC = (NCOL % 4 == 0) ? 4 : ((NCOL % 2 == 0) ? 2 : 1);
-  static constexpr int DI = W / 16;               // weight-gradient tile (DI x DI)
+  // Activation rows: row(i) = i*RS + SK*((i/TM) % SKM).  RS = 4 (mod 32) keeps
+  // the strided rows of the weight-gradient loads on distinct banks; the skew
+  // SK per neuron group separates the rows that the lanes of one
+  // shared-memory phase store (8 rows apart when TM = 8).  Chosen with a
+  // wavefront model of every access pattern of the kernel.
+  static constexpr int RS0 = ((PC + 27) / 32) * 32 + 4;
+  static constexpr int SK = (W == 64) ? (C == 1 ? 16 : (C == 4 ? 4 : 8)) : 0;
+  static constexpr int SKM = (W == 64) ? ((C == 1 || C == 4) ? 2 : 4) : 1;
+  static constexpr int RS = (RS0 >= PC + SK * (SKM - 1)) ? RS0 : RS0 + 32 * ((PC + SK * (SKM - 1) - RS0 + 31) / 32);
+  __host__ __device__ static constexpr int row(int i) { return i * RS + SK * ((i / TM) % SKM); }
   static constexpr int NQ = TM * NCOL / 4;        // stashed float4 per thread per layer
+  // weight-gradient contraction dW[i][k] = sum_pc Zb[i][pc] A[k][pc]:
+  // D x D outputs per thread, K (pc) split over KS consecutive lanes
+  static constexpr int D = (W >= 64) ? 8 : 4;
+  static constexpr int NTI = W / D;               // tiles per matrix dimension
+  static constexpr int KS = NT / (NTI * NTI);     // K-split lanes per tile
   static_assert(NG >= 8 && PG >= 4 && PG * NG == NT, "tile");
-  static_assert(PC % 4 == 0, "tile columns");
+  static_assert(PC % 4 == 0 && TM % 4 == 0 && RS % 4 == 0 && SK % VEC == 0, "tile columns");
+  static_assert(RS >= PC + SK * (SKM - 1), "row skew exceeds the row padding");
+  static_assert(KS >= 1 && KS <= 32 && NTI * NTI * KS == NT, "weight-gradient tile");
 };
 
 template <int W, int C, int DOUT>
@@ -166,27 +187,30 @@ __device__ __forceinline__ void mbar_wait(uint64_t* bar, uint32_t parity, int* e
 // ------------------------------------------------------ jet algebra ---
 // tanh jets per neuron: a = tanh(z), s1 = 1 - a^2, s2 = -2 a s1,
 // d_q a = s1 d_q z, lap a = s2 * sum_{spatial q} (d_q z)^2 + s1 * lap z.
+// Activation jet from the stashed form h = (a = tanh z, d_q z, lap z): the
+// tanh derivatives are polynomials in a, so no tanh is re-evaluated.
 template <int C, int DS, int DIN>
-__device__ __forceinline__ void act_fwd(const float* z, float* a) {
-  const float t = tanhf(z[0]);
+__device__ __forceinline__ void act_from_stash(const float* h, float* a) {
+  const float t = h[0];
   a[0] = t;
   if constexpr (C > 1) {
     const float s1 = 1.f - t * t;
     const float s2 = -2.f * t * s1;
     float S = 0.f;
 #pragma unroll
-    for (int q = 0; q < DS; ++q) S = fmaf(z[1 + q], z[1 + q], S);
+    for (int q = 0; q < DS; ++q) S = fmaf(h[1 + q], h[1 + q], S);
 #pragma unroll
-    for (int q = 0; q < DIN; ++q) a[1 + q] = s1 * z[1 + q];
-    a[C - 1] = fmaf(s2, S, s1 * z[C - 1]);
+    for (int q = 0; q < DIN; ++q) a[1 + q] = s1 * h[1 + q];
+    a[C - 1] = fmaf(s2, S, s1 * h[C - 1]);
   }
 }
 
-// Adjoint of act_fwd: from the activation-jet adjoints ab to the
-// pre-activation-jet adjoints zb (s3 = d s2 / dz = -2 s1 (1 - 3 a^2)).
+// Adjoint of the activation: from the activation-jet adjoints ab to the
+// pre-activation-jet adjoints zb, given the stashed form h = (a, d_q z,
+// lap z) (s3 = d s2 / dz = -2 s1 (1 - 3 a^2)).
 template <int C, int DS, int DIN>
 __device__ __forceinline__ void act_bwd(const float* z, const float* ab, float* zb) {
-  const float t = tanhf(z[0]);
+  const float t = z[0];
   const float s1 = 1.f - t * t;
   if constexpr (C == 1) {
     zb[0] = ab[0] * s1;
@@ -245,23 +269,21 @@ __device__ __forceinline__ void sts_vec(float* p, const float* x) {
   }
 }
 
-// acc[m][j] += sum_k Ws[k][n0 + m] * Xs[k][col0 + j],  m < 4, j < NCOL.
-// Ws rows have stride ws, Xs rows stride xs (both multiples of 4 floats).
-template <int NCOL, int VEC>
-__device__ __forceinline__ void contract(float (&acc)[4][NCOL], const float* __restrict__ Ws, int ws, int n0,
-                                         const float* __restrict__ Xs, int xs, int col0, int K) {
+// acc[m][j] += sum_k Ws[k][n0 + m] * Xs[k][col0 + j],  m < TM, j < NCOL.
+// Ws rows have stride ws, row k of Xs starts at rowx(k) (multiples of 4).
+template <int TM, int NCOL, int VEC, class RowX>
+__device__ __forceinline__ void contract(float (&acc)[TM][NCOL], const float* __restrict__ Ws, int ws, int n0,
+                                         const float* __restrict__ Xs, RowX rowx, int col0, int K) {
 #pragma unroll 2
   for (int k = 0; k < K; ++k) {
-    const float4 w = *reinterpret_cast<const float4*>(Ws + k * ws + n0);
+    float w[TM];
+    lds_vec<TM, 4>(w, Ws + k * ws + n0);
     float x[NCOL];
-    lds_vec<NCOL, VEC>(x, Xs + k * xs + col0);
+    lds_vec<NCOL, VEC>(x, Xs + rowx(k) + col0);
 #pragma unroll
-    for (int j = 0; j < NCOL; ++j) {
-      acc[0][j] = fmaf(w.x, x[j], acc[0][j]);
-      acc[1][j] = fmaf(w.y, x[j], acc[1][j]);
-      acc[2][j] = fmaf(w.z, x[j], acc[2][j]);
-      acc[3][j] = fmaf(w.w, x[j], acc[3][j]);
-    }
+    for (int m = 0; m < TM; ++m)
+#pragma unroll
+      for (int j = 0; j < NCOL; ++j) acc[m][j] = fmaf(w[m], x[j], acc[m][j]);
   }
 }
 
@@ -294,7 +316,7 @@ __global__ void __launch_bounds__(NT, 1)
   constexpr int DOUT = DS + 1;
   using T = Tile<W, C>;
   constexpr int P = T::P, RS = T::RS, TP = T::TP, NCOL = T::NCOL, VEC = T::VEC, PC = T::PC;
-  constexpr int TM = 4;
+  constexpr int TM = T::TM;
   constexpr bool TRAIN = (MODE == M_TRAIN);
 
   extern __shared__ float4 sm4[];
@@ -316,11 +338,15 @@ __global__ void __launch_bounds__(NT, 1)
   __shared__ int s_other_master, s_is_time;
 
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int ng = (warp % (T::NG / 8)) * 8 + (lane & 7);
-  const int pg = (warp / (T::NG / 8)) * 4 + (lane >> 3);
+  // A quarter-warp (8 lanes) spans 2 neuron groups x 4 point groups, so the
+  // 16-byte stores of a thread tile's rows (4 rows apart = 16 banks apart)
+  // and columns land in 8 distinct bank groups.
+  const int ng = (warp % (T::NG / 8)) * 8 + (lane >> 2);
+  const int pg = (warp / (T::NG / 8)) * 4 + (lane & 3);
   const int n0 = ng * TM, p0 = pg * TP, col0 = p0 * C;
   const int L = sh.L;
   const int n_items = *n_items_ptr;
+  const auto ROW = [](int i) { return T::row(i); };
 
   if (t == 0) mbar_init(&mbar, 1);
   __syncthreads();
@@ -332,13 +358,13 @@ __global__ void __launch_bounds__(NT, 1)
     const float* zf = &z[0][0];
 #pragma unroll
     for (int q = 0; q < T::NQ; ++q)
-      stash[((size_t)(l - 1) * T::NQ + q) * NT + t] = make_float4(zf[4 * q], zf[4 * q + 1], zf[4 * q + 2], zf[4 * q + 3]);
+      stash[((size_t)l * T::NQ + q) * NT + t] = make_float4(zf[4 * q], zf[4 * q + 1], zf[4 * q + 2], zf[4 * q + 3]);
   };
   auto stash_ld = [&](int l, float (&z)[TM][NCOL]) {
     float* zf = &z[0][0];
 #pragma unroll
     for (int q = 0; q < T::NQ; ++q) {
-      const float4 v = stash[((size_t)(l - 1) * T::NQ + q) * NT + t];
+      const float4 v = stash[((size_t)l * T::NQ + q) * NT + t];
       zf[4 * q] = v.x; zf[4 * q + 1] = v.y; zf[4 * q + 2] = v.z; zf[4 * q + 3] = v.w;
     }
   };
@@ -363,14 +389,21 @@ __global__ void __launch_bounds__(NT, 1)
       }
     }
   };
-  // activations of the thread tile into an smem buffer
-  auto act_store = [&](float* buf, const float (&z)[TM][NCOL]) {
+  // z -> stashed form in place: the value channel becomes a = tanh(z)
+  auto to_stash_form = [&](float (&z)[TM][NCOL]) {
+#pragma unroll
+    for (int m = 0; m < TM; ++m)
+#pragma unroll
+      for (int pp = 0; pp < TP; ++pp) z[m][pp * C] = tanhf(z[m][pp * C]);
+  };
+  // activations of the thread tile (from the stashed form) into smem
+  auto act_store = [&](float* buf, const float (&h)[TM][NCOL]) {
 #pragma unroll
     for (int m = 0; m < TM; ++m) {
       float a[NCOL];
 #pragma unroll
-      for (int pp = 0; pp < TP; ++pp) act_fwd<C, DS, DIN>(&z[m][pp * C], &a[pp * C]);
-      sts_vec<NCOL, VEC>(buf + (n0 + m) * RS + col0, a);
+      for (int pp = 0; pp < TP; ++pp) act_from_stash<C, DS, DIN>(&h[m][pp * C], &a[pp * C]);
+      sts_vec<NCOL, VEC>(buf + ROW(n0 + m) + col0, a);
     }
   };
 
@@ -438,6 +471,8 @@ __global__ void __launch_bounds__(NT, 1)
         {
           float z[TM][NCOL];
           layer0(z);
+          to_stash_form(z);
+          if (TRAIN) stash_st(0, z);
           act_store(bufA, z);
         }
         cur = bufA;
@@ -451,7 +486,7 @@ __global__ void __launch_bounds__(NT, 1)
           for (int m = 0; m < TM; ++m)
 #pragma unroll
             for (int j = 0; j < NCOL; ++j) z[m][j] = 0.f;
-          contract<NCOL, VEC>(z, wbuf, W, n0, cur, RS, col0, W);
+          contract<TM, NCOL, VEC>(z, wbuf, W, n0, cur, ROW, col0, W);
 #pragma unroll
           for (int m = 0; m < TM; ++m)
 #pragma unroll
@@ -461,6 +496,7 @@ __global__ void __launch_bounds__(NT, 1)
             if (l + 1 < L) bulk_load(wbuf, thT + (size_t)l * W * W, W * W * 4, &mbar);
             else bulk_load(wbuf, th + sh.woff[L], DOUT * W * 4, &mbar);
           }
+          to_stash_form(z);
           if (TRAIN) stash_st(l, z);
           act_store(oth, z);
           float* tmp = cur; cur = oth; oth = tmp;
@@ -481,7 +517,7 @@ __global__ void __launch_bounds__(NT, 1)
             for (int k = lk; k < W; k += KS) {
               const float w = wbuf[j * W + k];
 #pragma unroll
-              for (int c = 0; c < C; ++c) acc[c] = fmaf(w, cur[k * RS + p * C + c], acc[c]);
+              for (int c = 0; c < C; ++c) acc[c] = fmaf(w, cur[ROW(k) + p * C + c], acc[c]);
             }
 #pragma unroll
             for (int o = KS / 2; o > 0; o >>= 1)
@@ -650,7 +686,7 @@ __global__ void __launch_bounds__(NT, 1)
       for (int e = t; e < DOUT * W; e += NT) {
         const int j = e / W, k = e % W;
         float s = 0.f;
-        for (int pc = 0; pc < PC; ++pc) s = fmaf(ybsm[j * RS + pc], cur[k * RS + pc], s);
+        for (int pc = 0; pc < PC; ++pc) s = fmaf(ybsm[j * RS + pc], cur[ROW(k) + pc], s);
         grad_rmw(g + sh.woff[L] + e, s, first);
       }
       if (t < DOUT) {
@@ -666,45 +702,53 @@ __global__ void __launch_bounds__(NT, 1)
         for (int m = 0; m < TM; ++m)
 #pragma unroll
           for (int j = 0; j < NCOL; ++j) a[m][j] = 0.f;
-        contract<NCOL, VEC>(a, wbuf, W, n0, ybsm, RS, col0, DOUT);
+        contract<TM, NCOL, VEC>(a, wbuf, W, n0, ybsm, ROW, col0, DOUT);
         __syncthreads();
         if (t == 0 && L >= 2) bulk_load(wbuf, th + sh.woff[L - 1], W * W * 4, &mbar);
         float z[TM][NCOL];
-        if (L - 1 >= 1) stash_ld(L - 1, z); else layer0(z);
+        stash_ld(L - 1, z);
 #pragma unroll
         for (int m = 0; m < TM; ++m) {
           float zz[NCOL];
 #pragma unroll
           for (int pp = 0; pp < TP; ++pp) act_bwd<C, DS, DIN>(&z[m][pp * C], &a[m][pp * C], &zz[pp * C]);
-          sts_vec<NCOL, VEC>(zb + (n0 + m) * RS + col0, zz);
+          sts_vec<NCOL, VEC>(zb + ROW(n0 + m) + col0, zz);
         }
       }
       for (int l = L - 1; l >= 1; --l) {
         __syncthreads();
         {   // A_{l-1} into ab
           float z[TM][NCOL];
-          if (l - 1 >= 1) stash_ld(l - 1, z); else layer0(z);
+          stash_ld(l - 1, z);
           act_store(ab, z);
         }
         __syncthreads();
         {   // dW_l[i][k] += sum_pc Zb_l[i][pc] A_{l-1}[k][pc]
-          constexpr int DI = T::DI;
-          const int kg = t % 16, ig = t / 16;
-          float acc[DI][DI];
+          // Tile (ig, kg) owns rows ig + NTI a and columns kg + NTI c; its KS
+          // lanes take interleaved float4 chunks of pc and are summed by
+          // shuffles in a fixed order.  With KS > 1 the chunk offset moves
+          // the bank group, so kg is permuted to keep a quarter-warp's
+          // rows 4 groups apart.
+          constexpr int D = T::D, NTI = T::NTI, KS = T::KS;
+          const int ks = t % KS, tile = t / KS;
+          const int kq = tile % NTI;
+          const int kg = (KS > 1 && NTI == 8) ? ((kq & 1) * 4 + (kq >> 1)) : kq;
+          const int ig = tile / NTI;
+          float acc[D][D];
 #pragma unroll
-          for (int a = 0; a < DI; ++a)
+          for (int a = 0; a < D; ++a)
 #pragma unroll
-            for (int c = 0; c < DI; ++c) acc[a][c] = 0.f;
-          for (int pc = 0; pc < PC; pc += 4) {
-            float4 zv[DI], av[DI];
+            for (int c = 0; c < D; ++c) acc[a][c] = 0.f;
+          for (int pc = 4 * ks; pc < PC; pc += 4 * KS) {
+            float4 zv[D], av[D];
 #pragma unroll
-            for (int a = 0; a < DI; ++a) zv[a] = *reinterpret_cast<const float4*>(zb + (ig + 16 * a) * RS + pc);
+            for (int a = 0; a < D; ++a) zv[a] = *reinterpret_cast<const float4*>(zb + ROW(ig + NTI * a) + pc);
 #pragma unroll
-            for (int c = 0; c < DI; ++c) av[c] = *reinterpret_cast<const float4*>(ab + (kg + 16 * c) * RS + pc);
+            for (int c = 0; c < D; ++c) av[c] = *reinterpret_cast<const float4*>(ab + ROW(kg + NTI * c) + pc);
 #pragma unroll
-            for (int a = 0; a < DI; ++a)
+            for (int a = 0; a < D; ++a)
 #pragma unroll
-              for (int c = 0; c < DI; ++c) {
+              for (int c = 0; c < D; ++c) {
                 float s = acc[a][c];
                 s = fmaf(zv[a].x, av[c].x, s);
                 s = fmaf(zv[a].y, av[c].y, s);
@@ -713,13 +757,23 @@ __global__ void __launch_bounds__(NT, 1)
                 acc[a][c] = s;
               }
           }
+          if constexpr (KS > 1) {
 #pragma unroll
-          for (int a = 0; a < DI; ++a)
+            for (int o = KS / 2; o > 0; o >>= 1)
 #pragma unroll
-            for (int c = 0; c < DI; ++c) grad_rmw(g + sh.woff[l] + (ig + 16 * a) * W + kg + 16 * c, acc[a][c], first);
+              for (int a = 0; a < D; ++a)
+#pragma unroll
+                for (int c = 0; c < D; ++c) acc[a][c] += __shfl_xor_sync(0xffffffffu, acc[a][c], o);
+          }
+          if (ks == 0) {
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+              for (int c = 0; c < D; ++c) grad_rmw(g + sh.woff[l] + (ig + NTI * a) * W + kg + NTI * c, acc[a][c], first);
+          }
           for (int e = t; e < W; e += NT) {
             float s = 0.f;
-            for (int p = 0; p < P; ++p) s += zb[e * RS + p * C];
+            for (int p = 0; p < P; ++p) s += zb[ROW(e) + p * C];
             grad_rmw(g + sh.boff[l] + e, s, first);
           }
         }
@@ -731,17 +785,17 @@ __global__ void __launch_bounds__(NT, 1)
         for (int m = 0; m < TM; ++m)
 #pragma unroll
           for (int j = 0; j < NCOL; ++j) a[m][j] = 0.f;
-        contract<NCOL, VEC>(a, wbuf, W, n0, zb, RS, col0, W);
+        contract<TM, NCOL, VEC>(a, wbuf, W, n0, zb, ROW, col0, W);
         __syncthreads();
         if (t == 0 && l - 1 >= 1) bulk_load(wbuf, th + sh.woff[l - 1], W * W * 4, &mbar);
         float z[TM][NCOL];
-        if (l - 1 >= 1) stash_ld(l - 1, z); else layer0(z);
+        stash_ld(l - 1, z);
 #pragma unroll
         for (int m = 0; m < TM; ++m) {
           float zz[NCOL];
 #pragma unroll
           for (int pp = 0; pp < TP; ++pp) act_bwd<C, DS, DIN>(&z[m][pp * C], &a[m][pp * C], &zz[pp * C]);
-          sts_vec<NCOL, VEC>(zb + (n0 + m) * RS + col0, zz);
+          sts_vec<NCOL, VEC>(zb + ROW(n0 + m) + col0, zz);
         }
       }
       __syncthreads();
@@ -750,14 +804,14 @@ __global__ void __launch_bounds__(NT, 1)
         const int i = e / DIN, q = e % DIN;
         float s = 0.f;
         for (int p = 0; p < P; ++p) {
-          s = fmaf(zb[i * RS + p * C], xh[p * 4 + q], s);
-          if constexpr (JETS) s = fmaf(s_scale[q], zb[i * RS + p * C + 1 + q], s);
+          s = fmaf(zb[ROW(i) + p * C], xh[p * 4 + q], s);
+          if constexpr (JETS) s = fmaf(s_scale[q], zb[ROW(i) + p * C + 1 + q], s);
         }
         grad_rmw(g + sh.woff[0] + e, s, first);
       }
       for (int e = t; e < W; e += NT) {
         float s = 0.f;
-        for (int p = 0; p < P; ++p) s += zb[e * RS + p * C];
+        for (int p = 0; p < P; ++p) s += zb[ROW(e) + p * C];
         grad_rmw(g + sh.boff[0] + e, s, first);
       }
       __syncthreads();

@@ -58,6 +58,9 @@ def small_case(name):
     elif name == "unsteady3d_w32":
         cfg = synth.config("beltrami32", width=32, depth=5, splits=[1, 2, 1, 2], anchor=[0.2, -0.3, 0.4])
         res, obs, face = (260, 64), (70, 30), (33, 17)
+    elif name == "unsteady3d_w64":
+        cfg = synth.config("beltrami32", width=64, depth=4, splits=[2, 1, 1, 2], anchor=[0.4, -0.3, 0.1])
+        res, obs, face = (150, 50), (40, 12), (30, 9)
     elif name == "unsteady2d_w128_deep":
         cfg = synth.config("tgv", width=128, depth=3, splits=[1, 2, 3, 1], anchor=[3.0, 1.0, 0.0])
         res, obs, face = (90, 30), (20, 8), (20, 8)
@@ -77,7 +80,7 @@ def small_case(name):
 
 
 CASES = ["kovasznay", "tgv", "beltrami32", "beltrami128", "steady3d_w64", "unsteady3d_w32",
-         "unsteady2d_w128_deep"]
+         "unsteady3d_w64", "unsteady2d_w128_deep"]
 
 
 def compare_losses(gpu, ref, tol=LOSS_TOL):
