@@ -200,6 +200,34 @@ def plain_form_rate(cfg, pb, steps=2):
             "kind": "per-net eager PyTorch autograd double backward + torch.optim.Adam, FP32"}
 
 
+def serving_leg(seconds=5.0, rate=200.0, train_steps=20, seed=0):
+    """Continuous-batching serving of the trained 32-net Beltrami ensemble:
+    Poisson arrivals, log-uniform 1k-1M point clouds, 10 % with residuals,
+    8 GB in-flight memory cap; p50/p99 latency and points/s."""
+    from paper_2602_15883_b300.binding import Dpinn
+    from paper_2602_15883_b300.serve import Server, latency_summary, poisson_load
+    cfg = synth.config("beltrami32")
+    pb = synth.make_problem(cfg, seed=seed)
+    d = Dpinn(cfg)
+    d.set_problem(pb)
+    d.step(train_steps)
+    d.loss()
+    srv = Server(d, slots=4, mem_cap_bytes=8 << 30, max_batch_points=1 << 21).start()
+    try:
+        poisson_load(srv, cfg, rate_hz=20.0, duration_s=0.5, seed=seed + 1)     # warm-up
+        reqs = poisson_load(srv, cfg, rate_hz=rate, duration_s=seconds, seed=seed + 2)
+    finally:
+        srv.stop()
+    out = latency_summary(reqs)
+    out.update({"workload": "beltrami32 ensemble (32 nets of 8x128) after %d training steps" % train_steps,
+                "arrivals": f"Poisson {rate:g} req/s for {seconds:g} s", "points_per_request": "log-uniform 1e3..1e6",
+                "residual_fraction": 0.1, "mem_cap_gb": 8, "slots": 4,
+                "max_concurrent_batches": srv.max_concurrent,
+                "offered_points_per_s": sum(r.n for r in reqs) / seconds})
+    d.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -209,6 +237,8 @@ def main():
     ap.add_argument("--workload", default="tgv", choices=list(synth.CONFIGS))
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-baselines", action="store_true", help="skip the plain-form and CPU legs")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serving-seconds", type=float, default=5.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -324,6 +354,11 @@ def main():
             except Exception as ex:   # reported, not fatal
                 line["plain_form"] = {"error": str(ex)[:200]}
             line["cpu_baseline"] = cpu_baseline(cfg, pb)
+        if not args.no_serving and world == 1:
+            try:
+                line["serving"] = serving_leg(seconds=args.serving_seconds)
+            except Exception as ex:   # reported, not fatal
+                line["serving"] = {"error": str(ex)[:300]}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

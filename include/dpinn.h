@@ -153,6 +153,14 @@ int dpinn_step(dpinn_t* h, dpinn_stream_t stream, int n_steps);
  * current parameters; the gradient is readable with dpinn_get_grad. */
 int dpinn_eval_grad(dpinn_t* h, dpinn_stream_t stream);
 
+/* Losses only (no reverse pass, no update) at the current parameters, on
+ * `stream`; read them with dpinn_loss. */
+int dpinn_eval_loss(dpinn_t* h, dpinn_stream_t stream);
+
+/* Replace the parameters ([n_nets][n_params], host or device pointer)
+ * without touching the Adam moments or the step count.  Synchronises. */
+int dpinn_set_params(dpinn_t* h, const float* params);
+
 /* Synchronise with the handle's work and copy the loss record of the most
  * recent step (evaluated at its pre-update parameters) to host_out
  * [n_nets][6].  Errors: NONFINITE (a loss is NaN/Inf; host_out still
@@ -160,7 +168,8 @@ int dpinn_eval_grad(dpinn_t* h, dpinn_stream_t stream);
 int dpinn_loss(dpinn_t* h, float* host_out);
 
 /* Gradient of the most recent step or dpinn_eval_grad (before clipping),
- * host_out [n_nets][n_params] in the parameter-block order.  Synchronises. */
+ * out [n_nets][n_params] in the parameter-block order (host or device
+ * pointer).  Synchronises. */
 int dpinn_get_grad(dpinn_t* h, float* host_out);
 
 /* Query the resident ensemble: route each point to its cell, evaluate the
@@ -173,6 +182,22 @@ int dpinn_get_grad(dpinn_t* h, float* host_out);
  * (INVALID_ARG); its row is left untouched. */
 int dpinn_query(dpinn_t* h, const float* dev_pts, int64_t n, int want_residual,
                 float* dev_out, dpinn_stream_t stream);
+/* Query contexts: dpinn_query shares one scratch per handle, so two of its
+ * calls must not overlap on the GPU.  A context owns its own routing scratch
+ * for up to max_points points per call (allocated once, here) and its own
+ * error words, so queries through different contexts may run concurrently
+ * on different streams (the serving loop keeps one per in-flight batch).
+ * dpinn_qctx_query: as dpinn_query (device pointers, asynchronous on
+ * `stream`); n > max_points is INVALID_ARG.  dpinn_qctx_status: synchronise
+ * `stream`, report (then clear) the context's out-of-domain error.  A
+ * context must be destroyed before its handle. */
+typedef struct dpinn_qctx dpinn_qctx_t;
+int dpinn_qctx_create(dpinn_t* h, int64_t max_points, dpinn_qctx_t** out);
+void dpinn_qctx_destroy(dpinn_qctx_t* q);
+int dpinn_qctx_query(dpinn_qctx_t* q, const float* dev_pts, int64_t n, int want_residual,
+                     float* dev_out, dpinn_stream_t stream);
+int dpinn_qctx_status(dpinn_qctx_t* q, dpinn_stream_t stream);
+
 /* Same as dpinn_query, for callers that must not allocate device memory
  * while serving: a latency-bound loop that cannot afford the device-wide
  * synchronisation a cudaMalloc implies, or code whose device memory is owned
@@ -208,6 +233,18 @@ int dpinn_set_state(dpinn_t* h, const float* params, const float* m, const float
 /* Apply one optimiser update with a given gradient (host [n_nets][n_params]);
  * the same kernels as the step's update. */
 int dpinn_apply_grad(dpinn_t* h, const float* host_grad);
+
+/* Schedule of the grouped kernels: points per work item of the jet (residual)
+ * and value (observation / face) kernels, in tiles of their tile size
+ * (0 = automatic: about 8 items per SM, at most 64 tiles), and the order in
+ * which the persistent CTAs take items (0 = longest first, 1 = net order).
+ * Rebuilds the work lists and recaptures the step; results do not depend on
+ * the schedule beyond float rounding of the gradient sums (each schedule is
+ * itself deterministic).  Used by the autotuner. */
+int dpinn_set_schedule(dpinn_t* h, int jet_tiles, int val_tiles, int order);
+/* Current schedule and the tile sizes (points) of the jet and value kernels
+ * (tile_points[2]). */
+int dpinn_get_schedule(dpinn_t* h, int* jet_tiles, int* val_tiles, int* order, int* tile_points);
 
 /* Kernels launched by one dpinn_step (for accounting). */
 int dpinn_launches_per_step(dpinn_t* h);

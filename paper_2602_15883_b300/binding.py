@@ -27,6 +27,8 @@ EXPORTS = (
     "dpinn_net_info", "dpinn_face_info", "dpinn_set_points", "dpinn_step", "dpinn_eval_grad", "dpinn_loss",
     "dpinn_get_grad", "dpinn_query", "dpinn_query_status", "dpinn_get_state", "dpinn_set_state",
     "dpinn_apply_grad", "dpinn_launches_per_step", "dpinn_step_timed", "dpinn_query_static",
+    "dpinn_eval_loss", "dpinn_set_params", "dpinn_set_schedule", "dpinn_get_schedule",
+    "dpinn_qctx_create", "dpinn_qctx_destroy", "dpinn_qctx_query", "dpinn_qctx_status",
 )
 
 
@@ -89,6 +91,14 @@ def load_library(path: str = LIB_PATH):
         "dpinn_launches_per_step": ([vp], i32),
         "dpinn_step_timed": ([vp, vp, vp, i32, vp, vp], i32),
         "dpinn_query_static": ([vp, vp, i64, i32, vp, vp], i32),
+        "dpinn_eval_loss": ([vp, vp], i32),
+        "dpinn_set_params": ([vp, vp], i32),
+        "dpinn_set_schedule": ([vp, i32, i32, i32], i32),
+        "dpinn_get_schedule": ([vp, vp, vp, vp, vp], i32),
+        "dpinn_qctx_create": ([vp, i64, vp], i32),
+        "dpinn_qctx_destroy": ([vp], None),
+        "dpinn_qctx_query": ([vp, vp, i64, i32, vp, vp], i32),
+        "dpinn_qctx_status": ([vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -223,6 +233,20 @@ class Dpinn:
     def eval_grad(self, stream=None):
         self._check(self.lib.dpinn_eval_grad(self.h, _stream(stream)))
 
+    def eval_loss(self, stream=None):
+        self._check(self.lib.dpinn_eval_loss(self.h, _stream(stream)))
+
+    def set_params(self, params):
+        """Replace the parameters (NumPy or torch, host or device) only."""
+        p, keep = _ptr(params)
+        self._check(self.lib.dpinn_set_params(self.h, p))
+
+    def grad_into(self, out):
+        """Copy the last gradient into a torch tensor / NumPy array (any device)."""
+        p, keep = _ptr(out)
+        self._check(self.lib.dpinn_get_grad(self.h, p))
+        return out
+
     def loss(self, check=True):
         out = np.zeros((self.n_nets, 6), np.float32)
         rc = self.lib.dpinn_loss(self.h, out.ctypes.data)
@@ -269,6 +293,16 @@ class Dpinn:
                                               C.addressof(names)))
         return {names[i].decode(): ms[i] for i in range(n.value)}
 
+    def set_schedule(self, jet_tiles=0, val_tiles=0, order=0):
+        self._check(self.lib.dpinn_set_schedule(self.h, int(jet_tiles), int(val_tiles), int(order)))
+
+    def get_schedule(self):
+        v = [C.c_int() for _ in range(3)]
+        tp = (C.c_int * 2)()
+        self._check(self.lib.dpinn_get_schedule(self.h, *[C.addressof(x) for x in v], C.addressof(tp)))
+        return {"jet_tiles": v[0].value, "val_tiles": v[1].value, "order": v[2].value,
+                "tile_points": (tp[0], tp[1])}
+
     @property
     def launches_per_step(self):
         return self.lib.dpinn_launches_per_step(self.h)
@@ -291,3 +325,36 @@ class Dpinn:
 
     def query_status(self, stream=None):
         return self.lib.dpinn_query_status(self.h, _stream(stream))
+
+
+class QueryContext:
+    """Routing scratch for up to ``max_points`` points per query, so that
+    queries through different contexts can be in flight on different streams."""
+
+    def __init__(self, d: Dpinn, max_points: int):
+        self.d = d
+        q = C.c_void_p()
+        d._check(d.lib.dpinn_qctx_create(d.h, int(max_points), C.addressof(q)))
+        self.q = q
+        self.max_points = int(max_points)
+
+    def query_into(self, pts, out, want_residual=False, stream=None):
+        p, kp = _ptr(pts)
+        o, ko = _ptr(out)
+        self.d._check(self.d.lib.dpinn_qctx_query(self.q, p, int(pts.shape[0]), int(bool(want_residual)), o,
+                                                  _stream(stream)))
+        return out
+
+    def status(self, stream=None):
+        return self.d.lib.dpinn_qctx_status(self.q, _stream(stream))
+
+    def close(self):
+        if getattr(self, "q", None):
+            self.d.lib.dpinn_qctx_destroy(self.q)
+            self.q = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

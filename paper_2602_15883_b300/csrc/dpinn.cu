@@ -131,8 +131,9 @@ struct dpinn {
   DevBuf<double> loss_part;
   float* loss_host = nullptr;
   bool plan_ok = false;
+  int sched_jet = 0, sched_val = 0, sched_order = 0;   // 0 = automatic / longest first
   cudaStream_t cap = nullptr;
-  cudaGraphExec_t g_step = nullptr, g_grad = nullptr;
+  cudaGraphExec_t g_step = nullptr, g_grad = nullptr, g_loss = nullptr;
   cudaEvent_t done = nullptr;
   int launches = 0;
   // query scratch
@@ -142,6 +143,7 @@ struct dpinn {
   ~dpinn() {
     if (g_step) cudaGraphExecDestroy(g_step);
     if (g_grad) cudaGraphExecDestroy(g_grad);
+    if (g_loss) cudaGraphExecDestroy(g_loss);
     if (done) cudaEventDestroy(done);
     if (cap) cudaStreamDestroy(cap);
     if (loss_host) cudaFreeHost(loss_host);
@@ -221,8 +223,12 @@ int build_plan(dpinn* h);
 // Enqueue one step's work on stream s.  With `ev` (an array of at least 8
 // events) an event is recorded before the first and after every kernel, and
 // the kernel names are reported in `names` (for per-kernel timing).
-cudaError_t enqueue_step(dpinn* h, bool with_adam, cudaStream_t s, int* n_launch, cudaEvent_t* ev = nullptr,
+// Step modes: the training step, gradients without the update, losses only.
+enum { RUN_STEP = 0, RUN_GRAD = 1, RUN_LOSS = 2 };
+
+cudaError_t enqueue_step(dpinn* h, int mode, cudaStream_t s, int* n_launch, cudaEvent_t* ev = nullptr,
                          const char** names = nullptr) {
+  const bool with_adam = (mode == RUN_STEP);
   int launches = 0;
   int ne = 0;
   auto mark = [&](const char* name) {
@@ -241,6 +247,7 @@ cudaError_t enqueue_step(dpinn* h, bool with_adam, cudaStream_t s, int* n_launch
     ++launches;
     mark("exchange");
   }
+  b.no_reverse = (mode == RUN_LOSS) ? 1 : 0;
   if (e == cudaSuccess && h->n_jet) {
     dk::Bufs bb = b;
     bb.counter = h->counters.p + 1;
@@ -258,7 +265,7 @@ cudaError_t enqueue_step(dpinn* h, bool with_adam, cudaStream_t s, int* n_launch
     mark("train_val");
   }
   const int nblk = (h->n_params + dk::NT - 1) / dk::NT;
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && mode != RUN_LOSS) {
     dk::k_reduce_grad<<<dim3(nblk, h->n_nets), dk::NT, 0, s>>>(h->grad_part.p, h->slot_begin_d.p, h->grad.p,
                                                                 h->norm_part.p, h->npp, h->n_params);
     e = cudaGetLastError();
@@ -290,7 +297,7 @@ cudaError_t enqueue_step(dpinn* h, bool with_adam, cudaStream_t s, int* n_launch
   return e;
 }
 
-int capture(dpinn* h, bool with_adam, cudaGraphExec_t* out) {
+int capture(dpinn* h, int mode, cudaGraphExec_t* out) {
   if (*out) {
     cudaGraphExecDestroy(*out);
     *out = nullptr;
@@ -298,7 +305,7 @@ int capture(dpinn* h, bool with_adam, cudaGraphExec_t* out) {
   cudaStream_t s = h->cap;
   CK(h, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   int launches = 0;
-  cudaError_t e = enqueue_step(h, with_adam, s, &launches);
+  cudaError_t e = enqueue_step(h, mode, s, &launches);
   cudaGraph_t g = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(s, &g);
   if (e != cudaSuccess) {
@@ -309,7 +316,7 @@ int capture(dpinn* h, bool with_adam, cudaGraphExec_t* out) {
   e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
-  if (with_adam) h->launches = launches;
+  if (mode == RUN_STEP) h->launches = launches;
   return DPINN_OK;
 }
 
@@ -326,13 +333,15 @@ int build_plan(dpinn* h) {
   const int64_t n_face_pts = face_off[nf];
 
   // chunk sizes: enough items for several waves, multiples of the tile
-  auto pick_chunk = [&](int64_t total, int P) {
+  // (or the schedule set with dpinn_set_schedule)
+  auto pick_chunk = [&](int64_t total, int P, int tiles) {
+    if (tiles > 0) return (int64_t)tiles * P;
     const int64_t target = std::max<int64_t>(1, total / (8LL * h->n_sms));
     int64_t c = ((target + P - 1) / P) * P;
     return std::min<int64_t>(std::max<int64_t>(c, P), 64LL * P);
   };
-  const int64_t cj = pick_chunk(res_off[nn], h->ks.P_jet);
-  const int64_t cv = pick_chunk(obs_off[nn] + 2 * n_face_pts, h->ks.P_val);
+  const int64_t cj = pick_chunk(res_off[nn], h->ks.P_jet, h->sched_jet);
+  const int64_t cv = pick_chunk(obs_off[nn] + 2 * n_face_pts, h->ks.P_val, h->sched_val);
 
   std::vector<dk::Item> ij, iv, ie;
   std::vector<int> slot_begin(nn + 1, 0);
@@ -380,9 +389,11 @@ int build_plan(dpinn* h) {
     }
   // longest chunks first (the scheduler hands items out in this order)
   auto by_count = [](const dk::Item& a, const dk::Item& b) { return a.count > b.count; };
-  std::stable_sort(ij.begin(), ij.end(), by_count);
-  std::stable_sort(iv.begin(), iv.end(), by_count);
-  std::stable_sort(ie.begin(), ie.end(), by_count);
+  if (h->sched_order == 0) {
+    std::stable_sort(ij.begin(), ij.end(), by_count);
+    std::stable_sort(iv.begin(), iv.end(), by_count);
+    std::stable_sort(ie.begin(), ie.end(), by_count);
+  }
   h->n_jet = (int)ij.size();
   h->n_val = (int)iv.size();
   h->n_eval = (int)ie.size();
@@ -412,9 +423,11 @@ int build_plan(dpinn* h) {
   CK(h, h->nbr_val.ensure((size_t)std::max<int64_t>(n_face_pts, 1) * 2 * h->dout));
   CK(h, h->nbr_anc.ensure((size_t)std::max<int64_t>(n_face_pts, 1) * 2));
   CK(h, cudaMemset(h->nbr_anc.p, 0, (size_t)std::max<int64_t>(n_face_pts, 1) * 2 * sizeof(float)));
-  int rc = capture(h, true, &h->g_step);
+  int rc = capture(h, RUN_STEP, &h->g_step);
   if (rc) return rc;
-  rc = capture(h, false, &h->g_grad);
+  rc = capture(h, RUN_GRAD, &h->g_grad);
+  if (rc) return rc;
+  rc = capture(h, RUN_LOSS, &h->g_loss);
   if (rc) return rc;
   h->plan_ok = true;
   return DPINN_OK;
@@ -452,7 +465,65 @@ int check_errors(dpinn* h) {
   return DPINN_OK;
 }
 
+// Device scratch of one query launch sequence (routing and work items).
+struct QueryScratch {
+  int *net_of, *perm, *counts, *offsets, *cursor, *nitems;
+  dk::Item* items;
+  int* err;   // error words the route and query kernels report to
+};
+
+// Route n points to their nets, order them by net, build the work items and
+// launch the grouped query kernel, all on stream s.
+int enqueue_query(dpinn* h, const QueryScratch& q, const float* pts, int64_t n, int want_residual, float* out,
+                  cudaStream_t s) {
+  const int P = want_residual ? h->ks.P_jet : h->ks.P_val;
+  const int chunk = 4 * P;
+  const size_t max_items = (size_t)(n / chunk) + h->n_nets + 1;
+  dk::Route rt{};
+  for (int a = 0; a < h->din; ++a) {
+    rt.lo[a] = (float)h->cfg.lo[a];
+    rt.hi[a] = (float)h->cfg.hi[a];
+    rt.inv_h[a] = (float)((double)h->cfg.splits[a] / (h->cfg.hi[a] - h->cfg.lo[a]));
+    rt.splits[a] = h->cfg.splits[a];
+    rt.stride[a] = h->stride[a];
+  }
+  rt.din = h->din;
+  rt.n_nets = h->n_nets;
+  CK(h, cudaMemsetAsync(q.counts, 0, h->n_nets * sizeof(int), s));
+  CK(h, cudaMemsetAsync(q.nitems, 0, 2 * sizeof(int), s));
+  const int nb = (int)((n + 255) / 256);
+  dk::k_route<<<nb, 256, 0, s>>>(rt, pts, n, q.net_of, q.counts, q.err);
+  dk::k_route_plan<<<1, 32, 0, s>>>(q.counts, h->n_nets, chunk, q.offsets, q.cursor, q.items, q.nitems);
+  dk::k_route_scatter<<<nb, 256, 0, s>>>(q.net_of, n, q.cursor, q.perm);
+  CK(h, cudaGetLastError());
+  dk::Bufs b = make_bufs(h);
+  b.counter = q.nitems + 1;
+  b.err = q.err;
+  b.q_pts = pts;
+  b.q_perm = q.perm;
+  b.q_out = out;
+  b.q_w = h->dout + (want_residual ? h->ds + 1 : 0);
+  const void* fn = want_residual ? h->ks.query_jet : h->ks.query_val;
+  const size_t smem = want_residual ? h->ks.smem_jet : h->ks.smem_val;
+  const int grid = (int)std::min<size_t>(max_items, (size_t)h->n_sms * occupancy(fn, smem));
+  CK(h, launch_pinn(fn, grid, smem, h->shape, b, q.items, q.nitems, s));
+  return DPINN_OK;
+}
+
 }  // namespace
+
+// Query context: its own scratch (sized once at creation) and error words, so
+// that queries on several streams can be in flight together.
+struct dpinn_qctx {
+  dpinn* h = nullptr;
+  int64_t cap = 0;
+  DevBuf<int> net_of, perm, counts, offsets, cursor, nitems, err;
+  DevBuf<dk::Item> items;
+  ~dpinn_qctx() {
+    for (auto* b : {&net_of, &perm, &counts, &offsets, &cursor, &nitems, &err}) b->free_();
+    items.free_();
+  }
+};
 
 // =================================================================== ABI ===
 extern "C" {
@@ -712,6 +783,48 @@ int dpinn_eval_grad(dpinn_t* h, dpinn_stream_t stream) {
   return DPINN_OK;
 }
 
+int dpinn_eval_loss(dpinn_t* h, dpinn_stream_t stream) {
+  if (!h) return DPINN_ERR_INVALID_ARG;
+  if (!h->plan_ok) {
+    int rc = build_plan(h);
+    if (rc) return rc;
+    if (!h->plan_ok) return fail(h, DPINN_ERR_STATE, "residual, observation and face points must be set first");
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(h, cudaGraphLaunch(h->g_loss, s));
+  CK(h, cudaEventRecord(h->done, s));
+  return DPINN_OK;
+}
+
+int dpinn_set_schedule(dpinn_t* h, int jet_tiles, int val_tiles, int order) {
+  if (!h) return DPINN_ERR_INVALID_ARG;
+  if (jet_tiles < 0 || jet_tiles > 4096 || val_tiles < 0 || val_tiles > 4096 || order < 0 || order > 1)
+    return fail(h, DPINN_ERR_INVALID_ARG, "bad schedule");
+  if (jet_tiles == h->sched_jet && val_tiles == h->sched_val && order == h->sched_order) return DPINN_OK;
+  CK(h, cudaDeviceSynchronize());
+  h->sched_jet = jet_tiles;
+  h->sched_val = val_tiles;
+  h->sched_order = order;
+  return build_plan(h);
+}
+
+int dpinn_get_schedule(dpinn_t* h, int* jet_tiles, int* val_tiles, int* order, int* tile_points) {
+  if (!h) return DPINN_ERR_INVALID_ARG;
+  if (jet_tiles) *jet_tiles = h->sched_jet;
+  if (val_tiles) *val_tiles = h->sched_val;
+  if (order) *order = h->sched_order;
+  if (tile_points) { tile_points[0] = h->ks.P_jet; tile_points[1] = h->ks.P_val; }
+  return DPINN_OK;
+}
+
+int dpinn_set_params(dpinn_t* h, const float* params) {
+  if (!h || !params) return DPINN_ERR_INVALID_ARG;
+  CK(h, cudaDeviceSynchronize());
+  int rc = copy_state_in(h, h->theta.p, params);
+  if (rc) return rc;
+  return refresh_transpose(h);
+}
+
 int dpinn_loss(dpinn_t* h, float* host_out) {
   if (!h || !host_out) return DPINN_ERR_INVALID_ARG;
   CK(h, cudaEventSynchronize(h->done));
@@ -779,10 +892,8 @@ int dpinn_query(dpinn_t* h, const float* pts, int64_t n, int want_residual, floa
   if (n < 0 || n > ((int64_t)1 << 30)) return fail(h, DPINN_ERR_INVALID_ARG, "bad point count");
   if (n == 0) return DPINN_OK;
   if (!pts || !out) return fail(h, DPINN_ERR_INVALID_ARG, "null pointer");
-  cudaStream_t s = (cudaStream_t)stream;
   const int P = want_residual ? h->ks.P_jet : h->ks.P_val;
-  const int chunk = 4 * P;
-  const size_t max_items = (size_t)(n / chunk) + h->n_nets + 1;
+  const size_t max_items = (size_t)(n / (4 * P)) + h->n_nets + 1;
   CK(h, h->q_net.ensure(n));
   CK(h, h->q_perm.ensure(n));
   CK(h, h->q_counts.ensure(h->n_nets));
@@ -790,35 +901,9 @@ int dpinn_query(dpinn_t* h, const float* pts, int64_t n, int want_residual, floa
   CK(h, h->q_cursor.ensure(h->n_nets));
   CK(h, h->q_nitems.ensure(2));
   CK(h, h->q_items.ensure(max_items));
-  dk::Route rt{};
-  for (int a = 0; a < h->din; ++a) {
-    rt.lo[a] = (float)h->cfg.lo[a];
-    rt.hi[a] = (float)h->cfg.hi[a];
-    rt.inv_h[a] = (float)((double)h->cfg.splits[a] / (h->cfg.hi[a] - h->cfg.lo[a]));
-    rt.splits[a] = h->cfg.splits[a];
-    rt.stride[a] = h->stride[a];
-  }
-  rt.din = h->din;
-  rt.n_nets = h->n_nets;
-  CK(h, cudaMemsetAsync(h->q_counts.p, 0, h->n_nets * sizeof(int), s));
-  CK(h, cudaMemsetAsync(h->q_nitems.p, 0, 2 * sizeof(int), s));
-  const int nb = (int)((n + 255) / 256);
-  dk::k_route<<<nb, 256, 0, s>>>(rt, pts, n, h->q_net.p, h->q_counts.p, h->err_d.p);
-  dk::k_route_plan<<<1, 32, 0, s>>>(h->q_counts.p, h->n_nets, chunk, h->q_off.p, h->q_cursor.p, h->q_items.p,
-                                     h->q_nitems.p);
-  dk::k_route_scatter<<<nb, 256, 0, s>>>(h->q_net.p, n, h->q_cursor.p, h->q_perm.p);
-  CK(h, cudaGetLastError());
-  dk::Bufs b = make_bufs(h);
-  b.counter = h->q_nitems.p + 1;
-  b.q_pts = pts;
-  b.q_perm = h->q_perm.p;
-  b.q_out = out;
-  b.q_w = h->dout + (want_residual ? h->ds + 1 : 0);
-  const void* fn = want_residual ? h->ks.query_jet : h->ks.query_val;
-  const size_t smem = want_residual ? h->ks.smem_jet : h->ks.smem_val;
-  const int grid = (int)std::min<size_t>(max_items, (size_t)h->n_sms * occupancy(fn, smem));
-  CK(h, launch_pinn(fn, grid, smem, h->shape, b, h->q_items.p, h->q_nitems.p, s));
-  return DPINN_OK;
+  QueryScratch qs{h->q_net.p, h->q_perm.p, h->q_counts.p, h->q_off.p, h->q_cursor.p, h->q_nitems.p,
+                  h->q_items.p, h->err_d.p};
+  return enqueue_query(h, qs, pts, n, want_residual, out, (cudaStream_t)stream);
 }
 
 }  // extern "C"
@@ -923,6 +1008,60 @@ int dpinn_query_static(dpinn_t* h, const float* pts, int64_t n, int want_residua
   return DPINN_OK;
 }
 
+int dpinn_qctx_create(dpinn_t* h, int64_t max_points, dpinn_qctx_t** out) {
+  if (!h || !out) return DPINN_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (max_points < 1 || max_points > ((int64_t)1 << 30)) return fail(h, DPINN_ERR_INVALID_ARG, "bad max_points");
+  std::unique_ptr<dpinn_qctx> q(new dpinn_qctx());
+  q->h = h;
+  q->cap = max_points;
+  const int Pmin = std::min(h->ks.P_jet, h->ks.P_val);
+  CK(h, q->net_of.ensure(max_points));
+  CK(h, q->perm.ensure(max_points));
+  CK(h, q->counts.ensure(h->n_nets));
+  CK(h, q->offsets.ensure(h->n_nets));
+  CK(h, q->cursor.ensure(h->n_nets));
+  CK(h, q->nitems.ensure(2));
+  CK(h, q->err.ensure(4));
+  CK(h, q->items.ensure((size_t)(max_points / (4 * Pmin)) + h->n_nets + 1));
+  CK(h, cudaMemset(q->err.p, 0, 4 * sizeof(int)));
+  *out = q.release();
+  return DPINN_OK;
+}
+
+void dpinn_qctx_destroy(dpinn_qctx_t* q) {
+  if (!q) return;
+  cudaSetDevice(q->h->dev);
+  cudaDeviceSynchronize();
+  delete q;
+}
+
+int dpinn_qctx_query(dpinn_qctx_t* q, const float* pts, int64_t n, int want_residual, float* out,
+                     dpinn_stream_t stream) {
+  if (!q) return DPINN_ERR_INVALID_ARG;
+  dpinn* h = q->h;
+  if (n < 0 || n > q->cap) return fail(h, DPINN_ERR_INVALID_ARG, "more points than the context was created for");
+  if (n == 0) return DPINN_OK;
+  if (!pts || !out) return fail(h, DPINN_ERR_INVALID_ARG, "null pointer");
+  QueryScratch qs{q->net_of.p, q->perm.p, q->counts.p, q->offsets.p, q->cursor.p, q->nitems.p, q->items.p,
+                  q->err.p};
+  return enqueue_query(h, qs, pts, n, want_residual, out, (cudaStream_t)stream);
+}
+
+int dpinn_qctx_status(dpinn_qctx_t* q, dpinn_stream_t stream) {
+  if (!q) return DPINN_ERR_INVALID_ARG;
+  dpinn* h = q->h;
+  CK(h, cudaStreamSynchronize((cudaStream_t)stream));
+  int e[3] = {0, 0, 0};
+  CK(h, cudaMemcpy(e, q->err.p, sizeof(e), cudaMemcpyDeviceToHost));
+  if (e[dk::ERR_TIMEOUT]) return fail(h, DPINN_ERR_TIMEOUT, "a device wait gave up");
+  if (e[dk::ERR_DOMAIN]) {
+    CK(h, cudaMemset(q->err.p + dk::ERR_DOMAIN, 0, sizeof(int)));
+    return fail(h, DPINN_ERR_INVALID_ARG, "query point outside the domain");
+  }
+  return DPINN_OK;
+}
+
 int dpinn_query_status(dpinn_t* h, dpinn_stream_t stream) {
   if (!h) return DPINN_ERR_INVALID_ARG;
   CK(h, cudaStreamSynchronize((cudaStream_t)stream));
@@ -951,7 +1090,7 @@ int dpinn_step_timed(dpinn_t* h, dpinn_stream_t stream, float* ms, int max_kerne
   for (auto& e : ev) CK(h, cudaEventCreate(&e));
   const char* nm[8] = {nullptr};
   int launches = 0;
-  cudaError_t e = enqueue_step(h, true, s, &launches, ev, nm);
+  cudaError_t e = enqueue_step(h, RUN_STEP, s, &launches, ev, nm);
   if (e == cudaSuccess) e = cudaEventRecord(h->done, s);
   if (e == cudaSuccess) e = cudaEventSynchronize(ev[launches]);
   const int n = std::min(launches, max_kernels);

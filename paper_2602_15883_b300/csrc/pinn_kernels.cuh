@@ -77,6 +77,7 @@ struct Bufs {
   long long stash_per_cta;
   int* counter;            // work counter (reset before each launch)
   int* err;                // [3] error words
+  int no_reverse;          // training modes: losses only, no reverse pass
   const float* q_pts;      // query points [n][din]
   const int* q_perm;       // query segment order -> point index
   float* q_out;            // query output rows
@@ -679,6 +680,7 @@ __global__ void __launch_bounds__(NT, 1)
         __syncthreads();
       }   // pass
       if constexpr (!TRAIN) continue;
+      if (b.no_reverse) continue;
 
       // ================= reverse pass =================
       float* const g = b.grad_part + (size_t)item.slot * sh.npp;

@@ -1,0 +1,271 @@
+"""Continuous-batching query server for a resident ensemble.
+
+Requests (point clouds of any size, asking for (u, v, [w], p) and optionally
+the Navier-Stokes residuals) arrive at any time.  A dispatcher thread keeps
+``slots`` batches in flight, each on its own CUDA stream with its own query
+context and pre-allocated buffers: whenever a slot is free it admits the
+oldest waiting requests that fit the slot and the in-flight memory cap,
+copies their points into one pinned staging buffer, and issues one
+host-to-device copy, one value launch (requests without residual), one
+residual launch, one device-to-host copy and an event.  Requests that arrive
+while other batches run are admitted as slots and memory free up, so the
+copies and kernels of different batches overlap on the device.  Each point
+is computed by the same kernel code whatever batch it lands in (no
+cross-point reduction), so a request's result does not depend on the mix.
+"""
+from __future__ import annotations
+
+import threading
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Request:
+    pts: np.ndarray
+    want_residual: bool
+    t_arrival: float = 0.0
+    t_done: float = 0.0
+    result: np.ndarray | None = None
+    error: str | None = None
+    rid: int = 0
+    done: threading.Event = field(default_factory=threading.Event)
+
+    @property
+    def n(self) -> int:
+        return int(self.pts.shape[0])
+
+    @property
+    def latency_ms(self) -> float:
+        return 1e3 * (self.t_done - self.t_arrival)
+
+
+def request_bytes(n: int, d_in: int, width: int) -> int:
+    """Device bytes a request holds while in flight: its points, its output
+    rows and the routing scratch (net index and order, two ints per point)."""
+    return n * 4 * (d_in + width + 2)
+
+
+def plan_batch(pending, max_points: int, budget_left: int, d_in: int, width_of):
+    """FIFO admission: the longest prefix of ``pending`` that fits both the
+    slot's point capacity and the remaining memory budget.  A request larger
+    than the slot is never admitted (it is rejected at submission)."""
+    take, pts, mem = [], 0, 0
+    for r in pending:
+        b = request_bytes(r.n, d_in, width_of(r))
+        if pts + r.n > max_points or mem + b > budget_left:
+            break
+        take.append(r)
+        pts += r.n
+        mem += b
+    return take, mem
+
+
+class Server:
+    def __init__(self, handle, slots: int = 4, mem_cap_bytes: int = 8 << 30, max_batch_points: int = 1 << 21):
+        import torch
+        from .binding import QueryContext
+        self.torch = torch
+        self.d = handle
+        self.d_in, self.d_out, self.ds = handle.d_in, handle.d_out, handle.d_space
+        self.w_val = self.d_out
+        self.w_res = self.d_out + self.ds + 1
+        self.max_points = int(max_batch_points)
+        self.mem_cap = int(mem_cap_bytes)
+        cfg = handle.cfg
+        self.lo = np.array([np.float32(cfg["lo"][a]) for a in range(self.d_in)], np.float32)
+        self.hi = np.array([np.float32(cfg["hi"][a]) for a in range(self.d_in)], np.float32)
+        self.slots = []
+        for _ in range(slots):
+            self.slots.append({
+                "stream": torch.cuda.Stream(),
+                "qctx": QueryContext(handle, self.max_points),
+                "pts_h": torch.empty((self.max_points, self.d_in), dtype=torch.float32).pin_memory(),
+                "pts_d": torch.empty((self.max_points, self.d_in), dtype=torch.float32, device="cuda"),
+                "val_d": torch.empty((self.max_points, self.w_val), dtype=torch.float32, device="cuda"),
+                "res_d": torch.empty((self.max_points, self.w_res), dtype=torch.float32, device="cuda"),
+                "val_h": torch.empty((self.max_points, self.w_val), dtype=torch.float32).pin_memory(),
+                "res_h": torch.empty((self.max_points, self.w_res), dtype=torch.float32).pin_memory(),
+                "busy": None,
+            })
+        self.pending = deque()
+        self.lock = threading.Condition()
+        self.in_flight_bytes = 0
+        self.max_in_flight_bytes = 0
+        self.max_concurrent = 0
+        self.completed = []
+        self._next_id = 0
+        self._stop = False
+        self._thread = None
+
+    # -- client side ------------------------------------------------------
+    def submit(self, pts: np.ndarray, want_residual: bool = False) -> Request:
+        pts = np.ascontiguousarray(pts, np.float32).reshape(-1, self.d_in)
+        r = Request(pts=pts, want_residual=bool(want_residual), t_arrival=time.perf_counter())
+        with self.lock:
+            r.rid = self._next_id
+            self._next_id += 1
+        if r.n > self.max_points:
+            r.error = f"request of {r.n} points exceeds the batch capacity {self.max_points}"
+        elif r.n and not np.all((pts >= self.lo) & (pts <= self.hi)):
+            r.error = "query point outside the domain"
+        if r.error or r.n == 0:
+            r.result = np.zeros((0, self._width(r)), np.float32) if not r.error else None
+            r.t_done = time.perf_counter()
+            r.done.set()
+            return r
+        with self.lock:
+            self.pending.append(r)
+            self.lock.notify()
+        return r
+
+    def _width(self, r):
+        return self.w_res if r.want_residual else self.w_val
+
+    # -- dispatcher ----------------------------------------------------------
+    def start(self):
+        self._stop = False
+        self._thread = threading.Thread(target=self._run, daemon=True)
+        self._thread.start()
+        return self
+
+    def stop(self, drain: bool = True):
+        if drain:
+            while True:
+                with self.lock:
+                    if not self.pending and all(s["busy"] is None for s in self.slots):
+                        break
+                time.sleep(0.001)
+        self._stop = True
+        with self.lock:
+            self.lock.notify()
+        if self._thread:
+            self._thread.join()
+        for s in self.slots:
+            s["qctx"].close()
+
+    def _run(self):
+        torch = self.torch
+        torch.cuda.set_device(self.d.cfg.get("device", 0))
+        while not self._stop:
+            progressed = self._complete()
+            with self.lock:
+                free = [s for s in self.slots if s["busy"] is None]
+                batches = []
+                for s in free:
+                    take, mem = plan_batch(self.pending, self.max_points, self.mem_cap - self.in_flight_bytes,
+                                           self.d_in, self._width)
+                    if not take:
+                        break
+                    for _ in take:
+                        self.pending.popleft()
+                    self.in_flight_bytes += mem
+                    self.max_in_flight_bytes = max(self.max_in_flight_bytes, self.in_flight_bytes)
+                    batches.append((s, take, mem))
+                if not batches and not progressed and all(s["busy"] is None for s in self.slots):
+                    self.lock.wait(timeout=0.002)
+            for s, take, mem in batches:
+                self._launch(s, take, mem)
+            busy = sum(1 for s in self.slots if s["busy"] is not None)
+            self.max_concurrent = max(self.max_concurrent, busy)
+            if not batches and not progressed:
+                time.sleep(0.0002)
+
+    def _launch(self, s, take, mem):
+        torch = self.torch
+        vals = [r for r in take if not r.want_residual]
+        ress = [r for r in take if r.want_residual]
+        order = vals + ress
+        nv = sum(r.n for r in vals)
+        nr = sum(r.n for r in ress)
+        ph = s["pts_h"].numpy()
+        off = 0
+        for r in order:
+            ph[off:off + r.n] = r.pts
+            off += r.n
+        stream = s["stream"]
+        with torch.cuda.stream(stream):
+            s["pts_d"][:off].copy_(s["pts_h"][:off], non_blocking=True)
+            if nv:
+                s["qctx"].query_into(s["pts_d"][:nv], s["val_d"][:nv], False, stream)
+                s["val_h"][:nv].copy_(s["val_d"][:nv], non_blocking=True)
+            if nr:
+                s["qctx"].query_into(s["pts_d"][nv:off], s["res_d"][:nr], True, stream)
+                s["res_h"][:nr].copy_(s["res_d"][:nr], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        s["busy"] = (ev, vals, ress, mem)
+
+    def _complete(self):
+        done_any = False
+        for s in self.slots:
+            if s["busy"] is None:
+                continue
+            ev, vals, ress, mem = s["busy"]
+            if not ev.query():
+                continue
+            st = s["qctx"].status(s["stream"])
+            t = time.perf_counter()
+            vh, rh = s["val_h"].numpy(), s["res_h"].numpy()
+            off = 0
+            for r in vals:
+                r.result = vh[off:off + r.n].copy()
+                off += r.n
+            off = 0
+            for r in ress:
+                r.result = rh[off:off + r.n].copy()
+                off += r.n
+            for r in vals + ress:
+                if st != 0:
+                    r.error = f"query failed with status {st}"
+                r.t_done = t
+                r.done.set()
+            with self.lock:
+                self.in_flight_bytes -= mem
+                self.completed.extend(vals + ress)
+                s["busy"] = None
+            done_any = True
+        return done_any
+
+
+def poisson_load(server: Server, cfg: dict, rate_hz: float, duration_s: float, seed: int = 0,
+                 n_min: int = 1000, n_max: int = 1_000_000, residual_fraction: float = 0.1, pool=None):
+    """Open-loop Poisson arrivals; each request a uniform space-time point cloud
+    of log-uniform size (a slice of a pre-generated uniform pool, so that
+    producing a request costs nothing), a fraction asking for residuals.
+    Returns the requests once all are done."""
+    from . import synth
+    rng = np.random.default_rng(seed)
+    if pool is None:
+        pool = synth.query_points(cfg, 2 * n_max, seed=seed + 7)
+    sched = []
+    t = 0.0
+    while True:
+        t += rng.exponential(1.0 / rate_hz)
+        if t > duration_s:
+            break
+        n = int(np.exp(rng.uniform(np.log(n_min), np.log(n_max))))
+        off = int(rng.integers(0, len(pool) - n + 1))
+        sched.append((t, off, n, bool(rng.random() < residual_fraction)))
+    t0 = time.perf_counter()
+    reqs = []
+    for (ta, off, n, want) in sched:
+        while time.perf_counter() - t0 < ta:
+            time.sleep(max(0.0, min(0.0005, ta - (time.perf_counter() - t0))))
+        reqs.append(server.submit(pool[off:off + n], want))
+    for r in reqs:
+        r.done.wait()
+    return reqs
+
+
+def latency_summary(reqs):
+    ok = [r for r in reqs if r.error is None]
+    lat = np.array([r.latency_ms for r in ok]) if ok else np.zeros(1)
+    pts = sum(r.n for r in ok)
+    span = (max(r.t_done for r in ok) - min(r.t_arrival for r in ok)) if ok else 1.0
+    return {"requests": len(reqs), "errors": len(reqs) - len(ok), "points": pts,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "points_per_s": pts / span if span > 0 else 0.0}

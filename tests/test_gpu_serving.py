@@ -1,0 +1,94 @@
+"""Continuous batching: results are the same alone and in a Poisson mix,
+admission respects the memory cap, batches overlap, bad requests fail alone."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_15883_b300 import synth
+from tests.helpers import rel_l2
+from tests.test_gpu_parity import _gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _server(slots=3, mem_cap=1 << 30, max_batch=1 << 18):
+    Dpinn = _gpu()
+    from paper_2602_15883_b300.serve import Server
+    cfg = synth.config("beltrami32")
+    pb = synth.make_problem(cfg, seed=0, res_counts=[64] * 32, obs_counts=[16] * 32, face_counts=[8] * 72,
+                            bias_std=0.1)
+    d = Dpinn(cfg)
+    d.set_problem(pb)
+    return cfg, pb, d, Server(d, slots=slots, mem_cap_bytes=mem_cap, max_batch_points=max_batch).start()
+
+
+def test_alone_equals_in_the_mix_and_matches_oracle():
+    from paper_2602_15883_b300.serve import latency_summary, poisson_load
+    cfg, pb, d, srv = _server()
+    try:
+        probe_v = synth.query_points(cfg, 3000, seed=11)
+        probe_r = synth.query_points(cfg, 2000, seed=12)
+        a_v = srv.submit(probe_v, False)
+        a_r = srv.submit(probe_r, True)
+        a_v.done.wait(); a_r.done.wait()
+        # the same requests in the middle of a Poisson stream of others
+        import threading
+        box = {}
+        t = threading.Thread(target=lambda: box.setdefault(
+            "reqs", poisson_load(srv, cfg, rate_hz=400, duration_s=0.6, seed=3, n_min=500, n_max=60000,
+                                 residual_fraction=0.3)))
+        t.start()
+        import time
+        time.sleep(0.25)
+        b_v = srv.submit(probe_v, False)
+        b_r = srv.submit(probe_r, True)
+        t.join()
+        b_v.done.wait(); b_r.done.wait()
+        mix = box["reqs"]
+        assert len(mix) > 100 and all(r.error is None for r in mix)
+        np.testing.assert_array_equal(a_v.result, b_v.result)
+        np.testing.assert_array_equal(a_r.result, b_r.result)
+        summ = latency_summary(mix)
+        assert summ["p99_ms"] >= summ["p50_ms"] > 0
+        assert srv.max_concurrent >= 2
+        # against the regular query and the oracle
+        import torch
+        ref_v = d.query(torch.from_numpy(probe_v).cuda()).cpu().numpy()
+        np.testing.assert_array_equal(a_v.result, ref_v)
+        ora = oracle.Oracle(cfg, pb)
+        o_v, _, st = ora.query(np.asarray(pb.theta0, np.float64), probe_v)
+        assert st == 0 and rel_l2(a_v.result, o_v) <= 1e-5
+    finally:
+        srv.stop()
+
+
+def test_memory_cap_is_respected_and_everything_completes():
+    from paper_2602_15883_b300.serve import request_bytes
+    cap = request_bytes(40000, 4, 8) + 1
+    cfg, pb, d, srv = _server(slots=4, mem_cap=cap)
+    try:
+        reqs = [srv.submit(synth.query_points(cfg, n, seed=n), bool(n % 3 == 0)) for n in
+                [30000, 39000, 1000, 25000, 12000, 40000, 5000]]
+        for r in reqs:
+            r.done.wait()
+        assert all(r.error is None and r.result.shape[0] == r.n for r in reqs)
+        assert 0 < srv.max_in_flight_bytes <= cap
+    finally:
+        srv.stop()
+
+
+def test_bad_requests_fail_alone():
+    cfg, pb, d, srv = _server()
+    try:
+        bad = synth.query_points(cfg, 100, seed=1)
+        bad[5, 0] = 3.0
+        r_bad = srv.submit(bad)
+        big = srv.submit(np.zeros(((1 << 18) + 1, 4), np.float32))
+        good = srv.submit(synth.query_points(cfg, 100, seed=2))
+        for r in (r_bad, big, good):
+            r.done.wait()
+        assert r_bad.error and "outside" in r_bad.error
+        assert big.error and "capacity" in big.error
+        assert good.error is None and good.result.shape == (100, 4)
+    finally:
+        srv.stop()
