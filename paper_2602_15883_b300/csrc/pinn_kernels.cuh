@@ -281,10 +281,24 @@ __device__ __forceinline__ void contract(float (&acc)[TM][NCOL], const float* __
     lds_vec<TM, 4>(w, Ws + k * ws + n0);
     float x[NCOL];
     lds_vec<NCOL, VEC>(x, Xs + rowx(k) + col0);
+    if constexpr (NCOL % 2 == 0) {
+      // packed dual FP32 FMA (sm_100+): two columns per instruction
 #pragma unroll
-    for (int m = 0; m < TM; ++m)
+      for (int m = 0; m < TM; ++m) {
+        const float2 wm = make_float2(w[m], w[m]);
 #pragma unroll
-      for (int j = 0; j < NCOL; ++j) acc[m][j] = fmaf(w[m], x[j], acc[m][j]);
+        for (int j = 0; j < NCOL; j += 2) {
+          float2 r = __ffma2_rn(wm, make_float2(x[j], x[j + 1]), make_float2(acc[m][j], acc[m][j + 1]));
+          acc[m][j] = r.x;
+          acc[m][j + 1] = r.y;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < TM; ++m)
+#pragma unroll
+        for (int j = 0; j < NCOL; ++j) acc[m][j] = fmaf(w[m], x[j], acc[m][j]);
+    }
   }
 }
 
@@ -736,11 +750,13 @@ __global__ void __launch_bounds__(NT, 1)
           const int kq = tile % NTI;
           const int kg = (KS > 1 && NTI == 8) ? ((kq & 1) * 4 + (kq >> 1)) : kq;
           const int ig = tile / NTI;
-          float acc[D][D];
+          // packed dual FMA: lane .x sums the even, .y the odd pc of a chunk,
+          // so both operands are register pairs of the float4 loads
+          float2 acc2[D][D];
 #pragma unroll
           for (int a = 0; a < D; ++a)
 #pragma unroll
-            for (int c = 0; c < D; ++c) acc[a][c] = 0.f;
+            for (int c = 0; c < D; ++c) acc2[a][c] = make_float2(0.f, 0.f);
           for (int pc = 4 * ks; pc < PC; pc += 4 * KS) {
             float4 zv[D], av[D];
 #pragma unroll
@@ -751,14 +767,17 @@ __global__ void __launch_bounds__(NT, 1)
             for (int a = 0; a < D; ++a)
 #pragma unroll
               for (int c = 0; c < D; ++c) {
-                float s = acc[a][c];
-                s = fmaf(zv[a].x, av[c].x, s);
-                s = fmaf(zv[a].y, av[c].y, s);
-                s = fmaf(zv[a].z, av[c].z, s);
-                s = fmaf(zv[a].w, av[c].w, s);
-                acc[a][c] = s;
+                float2 s = acc2[a][c];
+                s = __ffma2_rn(make_float2(zv[a].x, zv[a].y), make_float2(av[c].x, av[c].y), s);
+                s = __ffma2_rn(make_float2(zv[a].z, zv[a].w), make_float2(av[c].z, av[c].w), s);
+                acc2[a][c] = s;
               }
           }
+          float acc[D][D];
+#pragma unroll
+          for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int c = 0; c < D; ++c) acc[a][c] = acc2[a][c].x + acc2[a][c].y;
           if constexpr (KS > 1) {
 #pragma unroll
             for (int o = KS / 2; o > 0; o >>= 1)
