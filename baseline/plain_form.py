@@ -73,6 +73,12 @@ class PlainForm:
         self.w = torch.tensor(cfg["comp_w"][: self.ds], dtype=dtype, device=self.dev)
         self.opt = torch.optim.Adam([p for ps in self.params for p in ps], lr=cfg["lr"],
                                     betas=(cfg["beta1"], cfg["beta2"]), eps=cfg["eps"])
+        iv = int(cfg.get("lr_decay_interval", 0))
+        self.sched = (torch.optim.lr_scheduler.StepLR(self.opt, step_size=iv, gamma=cfg.get("lr_decay_factor", 1.0))
+                      if iv > 0 else None)
+        self.comm_interval = int(cfg.get("comm_interval", 1))
+        self.t = 0
+        self.msgs = None
 
     def _cell(self, a, x):
         import numpy as np
@@ -154,7 +160,10 @@ class PlainForm:
         return torch.stack([lobs, lpde, lgu, lsp, ltm, total])
 
     def losses_and_grads(self):
-        msgs = self.exchange()
+        # Algorithm 1: messages refreshed every I_comm iterations, reused between
+        if self.msgs is None or self.t % self.comm_interval == 0:
+            self.msgs = self.exchange()
+        msgs = self.msgs
         recs = []
         for k in range(self.nn):
             for p in self.params[k]:
@@ -171,6 +180,9 @@ class PlainForm:
             for k in range(self.nn):
                 torch.nn.utils.clip_grad_norm_(self.params[k], clip)
         self.opt.step()
+        if self.sched is not None:
+            self.sched.step()
+        self.t += 1
         return rec
 
     def flat(self, grads=False):

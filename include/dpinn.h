@@ -105,6 +105,15 @@ typedef struct dpinn_config {
   uint64_t seed;          /* Xavier-normal initialisation seed */
   int precision;          /* DPINN_PREC_FP32 */
   int device;             /* CUDA device ordinal */
+  /* Step decay of the learning rate (Table B1 "LR factor & interval"): the
+   * update of step t (t = 1, 2, ...) uses lr * factor^floor((t-1)/interval);
+   * interval 0 = constant lr. */
+  double lr_decay_factor;
+  int lr_decay_interval;
+  /* Communication interval I_comm of Algorithm 1: the neighbour messages
+   * are recomputed before step t (t = 0, 1, ... counted before the update)
+   * when t mod I_comm == 0 and reused (stale) otherwise.  1 = every step. */
+  int comm_interval;
 } dpinn_config;
 
 typedef struct dpinn_layout {
@@ -112,7 +121,8 @@ typedef struct dpinn_layout {
   int n_masters;
 } dpinn_layout;
 
-/* Fill *cfg with defaults (Adam 1e-3 / 0.9 / 0.999 / 1e-8, unit weights). */
+/* Fill *cfg with defaults (Adam 1e-3 / 0.9 / 0.999 / 1e-8, unit weights,
+ * constant lr, I_comm = 1). */
 int dpinn_config_default(dpinn_config* cfg);
 
 /* Validate cfg, build the decomposition (cells, faces, masters), allocate

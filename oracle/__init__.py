@@ -37,6 +37,7 @@ class Config(C.Structure):
         ("comp_w", C.c_double * 3),
         ("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
         ("clip", C.c_double),
+        ("lr_decay_factor", C.c_double), ("lr_decay_interval", C.c_int), ("comm_interval", C.c_int),
     ]
 
 
@@ -72,6 +73,7 @@ def lib():
             "ora_adam": [vp] * 6,
             "ora_step": [vp] * 7,
             "ora_query": [vp, vp, vp, i64, i32, vp, vp],
+            "ora_step_cached": [vp] * 9,
         }
         for name, args in sig.items():
             fn = getattr(_lib, name)
@@ -104,6 +106,9 @@ def make_config(cfg: dict) -> Config:
     c.lam_obs, c.lam_pde, c.lam_gh_u = cfg["lambda_obs"], cfg["lambda_pde"], cfg["lambda_gh_u"]
     c.lam_gh_p_space, c.lam_gh_p_time = cfg["lambda_gh_p_space"], cfg["lambda_gh_p_time"]
     c.lr, c.beta1, c.beta2, c.eps, c.clip = cfg["lr"], cfg["beta1"], cfg["beta2"], cfg["eps"], cfg["clip_norm"]
+    c.lr_decay_factor = float(cfg.get("lr_decay_factor", 1.0))
+    c.lr_decay_interval = int(cfg.get("lr_decay_interval", 0))
+    c.comm_interval = int(cfg.get("comm_interval", 1))
     return c
 
 
@@ -230,6 +235,20 @@ class Oracle:
         tt = C.c_int64(int(t))
         loss = np.zeros((self.n_nets, 6))
         lib().ora_step(C.addressof(self.c), C.addressof(self.pc), _p(th), _p(m), _p(v), C.addressof(tt), _p(loss))
+        return th, m, v, tt.value, loss
+
+    def step_cached(self, th, m, v, t, cache):
+        """One iteration with the communication interval; ``cache`` is a dict
+        holding the messages between calls (created on first use)."""
+        th, m, v = (np.array(a, np.float64) for a in (th, m, v))
+        n = int(np.sum(self._keep[6]))
+        if "val" not in cache:
+            cache["val"] = np.zeros((max(n, 1), 2, self.d_out))
+            cache["anc"] = np.zeros((max(n, 1), 2))
+        tt = C.c_int64(int(t))
+        loss = np.zeros((self.n_nets, 6))
+        lib().ora_step_cached(C.addressof(self.c), C.addressof(self.pc), _p(th), _p(m), _p(v), C.addressof(tt),
+                              _p(loss), _p(cache["val"]), _p(cache["anc"]))
         return th, m, v, tt.value, loss
 
     def query(self, th, pts, want_res=False):

@@ -61,6 +61,9 @@ struct ora_config {
   double lam_obs, lam_pde, lam_gh_u, lam_gh_p_space, lam_gh_p_time;
   double comp_w[3];
   double lr, beta1, beta2, eps, clip;
+  double lr_decay_factor;   // update t uses lr * factor^floor((t-1)/interval)
+  int lr_decay_interval;    // 0: constant learning rate
+  int comm_interval;        // Algorithm 1: messages refreshed when t mod I_comm == 0
 };
 
 struct ora_problem {
@@ -576,11 +579,13 @@ void adam(const Geo& g, double* th, double* m, double* v, int64_t t, const doubl
     }
   double bc1 = 1.0 - std::pow(c.beta1, (double)t);
   double bc2 = 1.0 - std::pow(c.beta2, (double)t);
+  double lr = c.lr;
+  if (c.lr_decay_interval > 0) lr *= std::pow(c.lr_decay_factor, (double)((t - 1) / c.lr_decay_interval));
   for (size_t j = 0; j < gr.size(); ++j) {
     m[j] = c.beta1 * m[j] + (1.0 - c.beta1) * gr[j];
     v[j] = c.beta2 * v[j] + (1.0 - c.beta2) * gr[j] * gr[j];
     double mh = m[j] / bc1, vh = v[j] / bc2;
-    th[j] -= c.lr * mh / (std::sqrt(vh) + c.eps);
+    th[j] -= lr * mh / (std::sqrt(vh) + c.eps);
   }
 }
 
@@ -748,6 +753,33 @@ int ora_step(const ora_config* c, const ora_problem* p, double* th, double* m, d
   Geo g(*c);
   std::vector<double> grad((size_t)g.n_nets * g.n_params);
   ora_grad(c, p, th, grad.data(), loss);
+  *t += 1;
+  adam(g, th, m, v, *t, grad.data());
+  return 0;
+}
+
+// One iteration of Algorithm 1 with a communication interval: the neighbour
+// messages are recomputed into (val, anc) when t mod I_comm == 0 (t = steps
+// taken so far) and the cached ones are used otherwise; then losses,
+// gradients and the optimiser step.  val [n_face_pts][2][d_out],
+// anc [n_face_pts][2] persist between calls.
+int ora_step_cached(const ora_config* c, const ora_problem* p, double* th, double* m, double* v, int64_t* t,
+                    double* loss, double* val, double* anc) {
+  Geo g(*c);
+  Prob pb(g, *p);
+  Nbr nb;
+  const int64_t nf = pb.face_off.back();
+  if (c->comm_interval <= 1 || (*t % c->comm_interval) == 0) {
+    nb = exchange(pb, th);
+    std::copy(nb.val.begin(), nb.val.end(), val);
+    std::copy(nb.anc.begin(), nb.anc.end(), anc);
+  } else {
+    nb.val.assign(val, val + (size_t)nf * 2 * g.dout);
+    nb.anc.assign(anc, anc + (size_t)nf * 2);
+  }
+  std::vector<double> grad((size_t)g.n_nets * g.n_params);
+  for (int k = 0; k < g.n_nets; ++k)
+    net_grad(pb, nb, k, th + (size_t)k * g.n_params, grad.data() + (size_t)k * g.n_params, loss ? loss + k * 6 : nullptr);
   *t += 1;
   adam(g, th, m, v, *t, grad.data());
   return 0;

@@ -9,6 +9,11 @@ the two calls - and scales each net's gradient by the incoming gradient of
 its loss.  Nothing is differentiated by autograd itself: the Jacobian
 product is the library's adjoint.
 
+As in Algorithm 1, the neighbour messages a net's ghost terms compare
+against are constants of its gradient: d L_{k,m} / d theta_{k,m} only, so
+the Jacobian of the vector of losses is block-diagonal and the backward of
+``sum(losses)`` is not the total derivative through the messages.
+
 ``EnsembleModule`` holds the flat parameter tensor (canonical per-net block
 order of ``include/dpinn.h``) so that any torch optimiser can drive it.
 """

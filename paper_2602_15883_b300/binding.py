@@ -50,6 +50,7 @@ class Config(C.Structure):
         ("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
         ("clip_norm", C.c_double),
         ("seed", C.c_uint64), ("precision", C.c_int), ("device", C.c_int),
+        ("lr_decay_factor", C.c_double), ("lr_decay_interval", C.c_int), ("comm_interval", C.c_int),
     ]
 
 
@@ -129,6 +130,9 @@ def make_config(cfg: dict) -> Config:
     c.seed = int(cfg.get("seed", 0))
     c.precision = int(cfg.get("precision", 0))
     c.device = int(cfg.get("device", 0))
+    c.lr_decay_factor = float(cfg.get("lr_decay_factor", 1.0))
+    c.lr_decay_interval = int(cfg.get("lr_decay_interval", 0))
+    c.comm_interval = int(cfg.get("comm_interval", 1))
     return c
 
 

@@ -197,6 +197,8 @@ dk::Bufs make_bufs(dpinn* h) {
   b.stash_per_cta = 0;
   b.counter = h->counters.p;
   b.err = h->err_d.p;
+  b.step = h->step_d.p;
+  b.comm_interval = h->cfg.comm_interval;
   return b;
 }
 
@@ -278,7 +280,8 @@ cudaError_t enqueue_step(dpinn* h, int mode, cudaStream_t s, int* n_launch, cuda
       ++launches;
       mark("clip");
     }
-    dk::AdamArgs ar{h->cfg.lr, h->cfg.beta1, h->cfg.beta2, h->cfg.eps, h->cfg.clip_norm > 0 ? 1 : 0};
+    dk::AdamArgs ar{h->cfg.lr, h->cfg.beta1, h->cfg.beta2, h->cfg.eps, h->cfg.clip_norm > 0 ? 1 : 0,
+                   h->cfg.lr_decay_factor, h->cfg.lr_decay_interval};
     dk::k_adam<<<dim3(nblk, h->n_nets), dk::NT, 0, s>>>(h->shape, ar, h->theta.p, h->thetaT.p, h->m.p, h->v.p,
                                                          h->grad.p, h->coef.p, h->step_d.p, h->n_params);
     e = cudaGetLastError();
@@ -539,6 +542,9 @@ int dpinn_config_default(dpinn_config* c) {
   c->lambda_obs = c->lambda_pde = c->lambda_gh_u = c->lambda_gh_p_space = c->lambda_gh_p_time = 1.0;
   c->comp_w[0] = c->comp_w[1] = c->comp_w[2] = 1.0;
   c->lr = 1e-3; c->beta1 = 0.9; c->beta2 = 0.999; c->eps = 1e-8;
+  c->lr_decay_factor = 1.0;
+  c->lr_decay_interval = 0;
+  c->comm_interval = 1;
   return DPINN_OK;
 }
 
@@ -555,6 +561,9 @@ int dpinn_create(const dpinn_config* cfg, dpinn_t** out) {
   if (c.activation != DPINN_ACT_TANH) return fail(nullptr, DPINN_ERR_INVALID_ARG, "only tanh is supported");
   if (c.precision != DPINN_PREC_FP32) return fail(nullptr, DPINN_ERR_INVALID_ARG, "only FP32 is supported");
   if (!(c.nu >= 0)) return fail(nullptr, DPINN_ERR_INVALID_ARG, "nu must be >= 0");
+  if (c.comm_interval < 1) return fail(nullptr, DPINN_ERR_INVALID_ARG, "comm_interval must be >= 1");
+  if (c.lr_decay_interval < 0 || !(c.lr_decay_factor > 0))
+    return fail(nullptr, DPINN_ERR_INVALID_ARG, "bad learning-rate decay");
   const int din = c.d_space + c.unsteady;
   int64_t nn = 1;
   for (int a = 0; a < din; ++a) {
@@ -877,7 +886,8 @@ int dpinn_apply_grad(dpinn_t* h, const float* host_grad) {
                                                         h->n_params);
   if (h->cfg.clip_norm > 0)
     dk::k_clip_coef<<<h->n_nets, dk::NT>>>(h->norm_part.p, nblk, (float)h->cfg.clip_norm, h->coef.p);
-  dk::AdamArgs ar{h->cfg.lr, h->cfg.beta1, h->cfg.beta2, h->cfg.eps, h->cfg.clip_norm > 0 ? 1 : 0};
+  dk::AdamArgs ar{h->cfg.lr, h->cfg.beta1, h->cfg.beta2, h->cfg.eps, h->cfg.clip_norm > 0 ? 1 : 0,
+                   h->cfg.lr_decay_factor, h->cfg.lr_decay_interval};
   dk::k_adam<<<dim3(nblk, h->n_nets), dk::NT>>>(h->shape, ar, h->theta.p, h->thetaT.p, h->m.p, h->v.p, h->grad.p,
                                                  h->coef.p, h->step_d.p, h->n_params);
   dk::k_loss_record<<<1, 32>>>(h->shape, h->loss_part.p, h->slot_begin_d.p, h->nets_d.p, 0, h->loss_rec.p,

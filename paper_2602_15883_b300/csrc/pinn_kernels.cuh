@@ -78,6 +78,8 @@ struct Bufs {
   int* counter;            // work counter (reset before each launch)
   int* err;                // [3] error words
   int no_reverse;          // training modes: losses only, no reverse pass
+  const long long* step;   // exchange: steps taken so far
+  int comm_interval;       // exchange only when *step % comm_interval == 0
   const float* q_pts;      // query points [n][din]
   const int* q_perm;       // query segment order -> point index
   float* q_out;            // query output rows
@@ -361,6 +363,9 @@ __global__ void __launch_bounds__(NT, 1)
   const int n0 = ng * TM, p0 = pg * TP, col0 = p0 * C;
   const int L = sh.L;
   const int n_items = *n_items_ptr;
+  // Algorithm 1: the messages are refreshed every I_comm iterations and the
+  // cached (stale) ones are used in between.
+  if (MODE == M_EVAL && b.comm_interval > 1 && (*b.step % b.comm_interval) != 0) return;
   const auto ROW = [](int i) { return T::row(i); };
 
   if (t == 0) mbar_init(&mbar, 1);
@@ -884,6 +889,8 @@ __global__ void k_clip_coef(const float* __restrict__ norm_part, int nblk, float
 struct AdamArgs {
   double lr, beta1, beta2, eps;
   int use_clip;
+  double decay_factor;   // lr * decay_factor^floor((t-1)/decay_interval)
+  int decay_interval;    // 0: constant lr
 };
 // (1 - beta) factors are formed in double on the host and rounded once:
 // 1.f - 0.999f would carry a 1.3e-5 relative error into the second moment.
@@ -898,7 +905,9 @@ __global__ void k_adam(const Shape sh, AdamArgs ar, float* __restrict__ theta, f
     const double t = (double)(*step + 1);
     const double bc1 = 1.0 - pow(ar.beta1, t);
     const double bc2 = 1.0 - pow(ar.beta2, t);
-    s_c[0] = (float)(ar.lr / bc1);
+    double lr = ar.lr;
+    if (ar.decay_interval > 0) lr *= pow(ar.decay_factor, (double)((*step) / ar.decay_interval));
+    s_c[0] = (float)(lr / bc1);
     s_c[1] = (float)(1.0 / sqrt(bc2));
   }
   __syncthreads();

@@ -51,7 +51,7 @@ def _base(**kw):
         p_ref=0.0, lambda_obs=10.0, lambda_pde=4.0, lambda_gh_u=1.0,
         lambda_gh_p_space=1.0, lambda_gh_p_time=1.0, comp_w=[1.0, 1.0, 1.0],
         lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, clip_norm=0.0, seed=0,
-        precision=0, device=0,
+        precision=0, device=0, lr_decay_factor=1.0, lr_decay_interval=0, comm_interval=1,
         # workload (not part of the library config)
         flow="kovasznay", res_dist=("const", 1000), n_obs=200, noise=0.01,
         n_face=0,
@@ -100,7 +100,8 @@ LIB_KEYS = (
     "d_space", "unsteady", "lo", "hi", "splits", "depth", "width", "activation",
     "nu", "anchor", "p_ref", "lambda_obs", "lambda_pde", "lambda_gh_u",
     "lambda_gh_p_space", "lambda_gh_p_time", "comp_w", "lr", "beta1", "beta2",
-    "eps", "clip_norm", "seed", "precision", "device",
+    "eps", "clip_norm", "seed", "precision", "device", "lr_decay_factor", "lr_decay_interval",
+    "comm_interval",
 )
 
 

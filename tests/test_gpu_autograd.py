@@ -65,25 +65,40 @@ def test_backward_matches_torch_double_backward_fp64():
 
 
 def test_backward_matches_finite_differences_of_gpu_losses():
-    torch, cfg, pb, d, mod = _setup("beltrami128")
-    out = mod()
-    (g,) = torch.autograd.grad(out.sum(), mod.theta)
-    g = g.cpu().numpy()
-    theta = mod.theta.detach().clone()
-    idx = np.argsort(-np.abs(g))[:6]
+    """The gradient of net A's loss with the neighbour messages held constant
+    (the method's gradient) against central differences of the GPU losses.
+    The messages are frozen with a long communication interval: one step
+    caches them at theta_0, then the parameters are reset to theta_0."""
+    Dpinn = _gpu()
+    import torch
     from paper_2602_15883_b300.autograd import ensemble_loss
+    cfg, pb = small_case("beltrami128")
+    cfg = dict(cfg, comm_interval=1000)
+    d = Dpinn(cfg)
+    d.set_problem(pb)
+    d.step(1)                          # t = 1: messages of theta_0 stay cached
+    theta = torch.from_numpy(np.asarray(pb.theta0, np.float32)).cuda()
+    d.set_params(theta)
+    d.eval_grad()
+    g = d.grad()
+    npar = d.n_params
 
-    def central(j, h):
-        tp, tm = theta.clone(), theta.clone()
-        tp[j] += h
-        tm[j] -= h
-        return (ensemble_loss(tp, d).sum() - ensemble_loss(tm, d).sum()).item() / (2 * h)
+    def own_loss(th, k):
+        return ensemble_loss(th, d)[k].item()
 
-    for j in idx:
-        h = 2e-3 * max(1.0, abs(float(theta[j])))
-        # Richardson extrapolation removes the O(h^2) truncation term
-        fd = (4.0 * central(j, h / 2) - central(j, h)) / 3.0
-        assert abs(fd - g[j]) <= 1e-2 * abs(g[j]), (j, fd, g[j])
+    for k in (0, d.n_nets - 1):
+        gk = g[k]
+        for j in np.argsort(-np.abs(gk))[:3]:
+            h = 2e-3 * max(1.0, abs(float(theta[k * npar + j])))
+
+            def central(hh):
+                tp, tm = theta.clone(), theta.clone()
+                tp[k * npar + j] += hh
+                tm[k * npar + j] -= hh
+                return (own_loss(tp, k) - own_loss(tm, k)) / (2 * hh)
+            # Richardson extrapolation removes the O(h^2) truncation term
+            fd = (4.0 * central(h / 2) - central(h)) / 3.0
+            assert abs(fd - gk[j]) <= 1e-2 * abs(gk[j]), (k, j, fd, gk[j])
 
 
 def test_torch_adam_drives_the_module_like_the_library_step():

@@ -257,3 +257,25 @@ def test_redelivering_points_keeps_plan():
     for k in range(ora.n_nets):
         assert rel_l2(g2[k], og[k]) <= GRAD_TOL
     assert not np.array_equal(g1, g2)
+
+
+@pytest.mark.parametrize("interval", [1, 3])
+def test_comm_interval_and_lr_decay_trajectory(interval):
+    """Algorithm 1 with I_comm > 1 (stale messages between refreshes) and a
+    step decay of the learning rate, 6 steps against the oracle."""
+    Dpinn = _gpu()
+    cfg, pb = small_case("tgv")
+    cfg = dict(cfg, comm_interval=interval, lr=3e-3, lr_decay_factor=0.5, lr_decay_interval=2)
+    d = Dpinn(cfg)
+    d.set_problem(pb)
+    ora = oracle.Oracle(cfg, pb)
+    th = np.asarray(pb.theta0, np.float64)
+    m, v, t, cache = np.zeros_like(th), np.zeros_like(th), 0, {}
+    for s in range(6):
+        d.step(1)
+        loss = d.loss()
+        th, m, v, t, oloss = ora.step_cached(th, m, v, t, cache)
+        compare_losses(loss, oloss, tol=1e-4)
+    gth, _, _, gt = d.get_state()
+    assert gt == 6
+    assert rel_l2(gth, th) < 1e-4
