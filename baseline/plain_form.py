@@ -95,7 +95,7 @@ class PlainForm:
         for l in range(nl):
             h = torch.nn.functional.linear(h, ps[2 * l], ps[2 * l + 1])
             if l < nl - 1:
-                h = torch.tanh(h)
+                h = torch.sin(h) if self.cfg.get("activation", 0) == 1 else torch.tanh(h)
         return h
 
     def residual(self, k, x):

@@ -82,7 +82,9 @@ enum {
 };
 
 enum { DPINN_POINTS_RESIDUAL = 0, DPINN_POINTS_OBS = 1, DPINN_POINTS_FACE = 2 };
-enum { DPINN_ACT_TANH = 0 };
+/* Hidden-layer activation: tanh, or sin (the paper's cylinder cases,
+ * Table B1). */
+enum { DPINN_ACT_TANH = 0, DPINN_ACT_SIN = 1 };
 enum { DPINN_PREC_FP32 = 0 };
 
 typedef struct dpinn_config {
@@ -92,7 +94,7 @@ typedef struct dpinn_config {
   int splits[4];          /* cells per input axis */
   int depth;              /* hidden layers L (2..16) */
   int width;              /* neurons per hidden layer: 32, 64 or 128 */
-  int activation;         /* DPINN_ACT_TANH */
+  int activation;         /* DPINN_ACT_TANH or DPINN_ACT_SIN */
   double nu;              /* kinematic viscosity = 1/Re */
   double anchor_x[3];     /* x_anc (spatial) */
   double p_ref;           /* pressure value assigned to x_anc in queries */

@@ -38,6 +38,7 @@ class Config(C.Structure):
         ("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
         ("clip", C.c_double),
         ("lr_decay_factor", C.c_double), ("lr_decay_interval", C.c_int), ("comm_interval", C.c_int),
+        ("activation", C.c_int),
     ]
 
 
@@ -109,6 +110,7 @@ def make_config(cfg: dict) -> Config:
     c.lr_decay_factor = float(cfg.get("lr_decay_factor", 1.0))
     c.lr_decay_interval = int(cfg.get("lr_decay_interval", 0))
     c.comm_interval = int(cfg.get("comm_interval", 1))
+    c.activation = int(cfg.get("activation", 0))
     return c
 
 

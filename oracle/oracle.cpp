@@ -64,6 +64,7 @@ struct ora_config {
   double lr_decay_factor;   // update t uses lr * factor^floor((t-1)/interval)
   int lr_decay_interval;    // 0: constant learning rate
   int comm_interval;        // Algorithm 1: messages refreshed when t mod I_comm == 0
+  int activation;           // 0 tanh, 1 sin
 };
 
 struct ora_problem {
@@ -166,21 +167,25 @@ struct Geo {
 // derivatives along each input (space then time), channel LAP = spatial
 // Laplacian.  With jets == false only channel 0 is carried (plain value).
 //
-// tanh derivatives with a = tanh(z):  s1 = 1 - a^2,  s2 = -2 a s1,
-// s3 = -2 s1 (1 - 3 a^2).
+// Activation derivatives s1, s2, s3 of sigma: tanh (a = tanh z,
+// s1 = 1 - a^2, s2 = -2 a s1, s3 = -2 s1 (1 - 3 a^2)) or sin (s1 = cos z,
+// s2 = -sin z, s3 = -cos z; the cylinder cases of Table B1).
 // Chain rule per neuron:  d_q a = s1 d_q z;
 //   lap a = s2 * sum_{spatial q} (d_q z)^2 + s1 * lap z.
 
 template <class T>
 void activate(const Geo& g, int nc, const T* Z, T* A) {
+  const bool sn = g.cfg.activation == 1;
   for (int k = 0; k < g.W; ++k) {
     const T* z = Z + (size_t)k * nc;
     T* a_ = A + (size_t)k * nc;
-    T a = std::tanh(z[0]);
+    // sigma and its first two derivatives: tanh (s1 = 1 - a^2, s2 = -2 a s1)
+    // or sin (s1 = cos z, s2 = -sin z)
+    T a = sn ? std::sin(z[0]) : std::tanh(z[0]);
     a_[0] = a;
     if (nc == 1) continue;
-    T s1 = 1.0 - a * a;
-    T s2 = -2.0 * a * s1;
+    T s1 = sn ? std::cos(z[0]) : T(1.0 - a * a);
+    T s2 = sn ? T(-a) : T(-2.0 * a * s1);
     T S = 0.0;
     for (int q = 0; q < g.ds; ++q) S += z[1 + q] * z[1 + q];
     for (int q = 0; q < g.din; ++q) a_[1 + q] = s1 * z[1 + q];
@@ -263,11 +268,19 @@ void residual_adjoint(const Geo& g, const double* Y, const double* rb, double* Y
 // Adjoint of `activate` for one neuron: from the adjoints Ab of the
 // activation jet to the adjoints Zb of the pre-activation jet.
 void activate_adjoint(const Geo& g, int nc, const double* z, const double* Ab, double* Zb) {
-  double a = std::tanh(z[0]);
-  double s1 = 1.0 - a * a;
+  // s1, s2, s3: first three derivatives of sigma at z
+  double s1, s2, s3;
+  if (g.cfg.activation == 1) {
+    s1 = std::cos(z[0]);
+    s2 = -std::sin(z[0]);
+    s3 = -s1;
+  } else {
+    double a = std::tanh(z[0]);
+    s1 = 1.0 - a * a;
+    s2 = -2.0 * a * s1;
+    s3 = -2.0 * s1 * (1.0 - 3.0 * a * a);
+  }
   if (nc == 1) { Zb[0] = Ab[0] * s1; return; }
-  double s2 = -2.0 * a * s1;
-  double s3 = -2.0 * s1 * (1.0 - 3.0 * a * a);
   double S = 0.0;
   for (int q = 0; q < g.ds; ++q) S += z[1 + q] * z[1 + q];
   Zb[g.LAP] = Ab[g.LAP] * s1;

@@ -1,31 +1,62 @@
-"""Build libdpinn.so in-tree with nvcc for sm_103a (B300)."""
+"""Build libdpinn.so in-tree with nvcc for sm_103a (B300).
+
+The grouped-kernel instantiations are split over one translation unit per
+width and activation; they compile in parallel and are linked with the host
+runtime into one shared library.
+"""
 from __future__ import annotations
 
+import glob
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
 SO = os.path.join(HERE, "libdpinn.so")
-SRC = [os.path.join(HERE, "csrc", "dpinn.cu")]
-DEPS = SRC + [os.path.join(HERE, "csrc", "pinn_kernels.cuh"),
-              os.path.join(os.path.dirname(HERE), "include", "dpinn.h")]
+OBJ = os.path.join(HERE, "_build")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
-         "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr"]
+         "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+
+
+def sources():
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+
+
+def deps():
+    return sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
+        [os.path.join(os.path.dirname(HERE), "include", "dpinn.h")]
 
 
 def stale() -> bool:
     if not os.path.exists(SO):
         return True
     t = os.path.getmtime(SO)
-    return any(os.path.getmtime(p) > t for p in DEPS)
+    return any(os.path.getmtime(p) > t for p in deps())
+
+
+def _compile(src, verbose):
+    obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
+    cmd = [NVCC] + FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-c", "-o", obj, src]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    return src, obj, r.returncode, r.stdout + r.stderr
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    if force or stale():
-        cmd = [NVCC] + FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-o", SO] + SRC
-        subprocess.check_call(cmd)
+    if not (force or stale()):
+        return SO
+    os.makedirs(OBJ, exist_ok=True)
+    with ThreadPoolExecutor(max_workers=max(1, min(len(sources()), os.cpu_count() or 1))) as ex:
+        results = list(ex.map(lambda s: _compile(s, verbose), sources()))
+    for src, obj, rc, log in results:
+        if verbose or rc:
+            sys.stderr.write(log)
+        if rc:
+            raise RuntimeError(f"nvcc failed on {src}")
+    subprocess.check_call([NVCC, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", SO]
+                          + [o for _, o, _, _ in results])
     return SO
 
 

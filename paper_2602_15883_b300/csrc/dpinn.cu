@@ -19,52 +19,18 @@
 #include <vector>
 
 #include "../../include/dpinn.h"
-#include "pinn_kernels.cuh"
+#include "kernel_set.h"
+#include "pinn_aux.cuh"
 
 namespace {
 
-struct KernelSet {
-  const void* train_jet = nullptr;
-  const void* train_val = nullptr;
-  const void* eval_val = nullptr;
-  const void* query_val = nullptr;
-  const void* query_jet = nullptr;
-  size_t smem_jet = 0, smem_val = 0;
-  int P_jet = 0, P_val = 0;
-  long long stash_jet = 0, stash_val = 0;   // floats per CTA
-};
+using dk::KernelSet;
 
-template <int W, int DS, int UNST>
-KernelSet make_set(int L) {
-  constexpr int DIN = DS + UNST, CJ = DIN + 2, DOUT = DS + 1;
-  KernelSet k;
-  k.train_jet = (const void*)dk::k_pinn<W, DS, UNST, true, dk::M_TRAIN>;
-  k.train_val = (const void*)dk::k_pinn<W, DS, UNST, false, dk::M_TRAIN>;
-  k.eval_val = (const void*)dk::k_pinn<W, DS, UNST, false, dk::M_EVAL>;
-  k.query_val = (const void*)dk::k_pinn<W, DS, UNST, false, dk::M_QUERY>;
-  k.query_jet = (const void*)dk::k_pinn<W, DS, UNST, true, dk::M_QUERY>;
-  k.smem_jet = dk::smem_floats<W, CJ, DOUT>(L) * sizeof(float);
-  k.smem_val = dk::smem_floats<W, 1, DOUT>(L) * sizeof(float);
-  k.P_jet = dk::Tile<W, CJ>::P;
-  k.P_val = dk::Tile<W, 1>::P;
-  k.stash_jet = (long long)L * dk::Tile<W, CJ>::NQ * dk::NT * 4;
-  k.stash_val = (long long)L * dk::Tile<W, 1>::NQ * dk::NT * 4;
-  return k;
-}
-
-template <int W>
-bool pick_ds(int ds, int unst, int L, KernelSet* k) {
-  if (ds == 2 && unst == 0) { *k = make_set<W, 2, 0>(L); return true; }
-  if (ds == 2 && unst == 1) { *k = make_set<W, 2, 1>(L); return true; }
-  if (ds == 3 && unst == 0) { *k = make_set<W, 3, 0>(L); return true; }
-  if (ds == 3 && unst == 1) { *k = make_set<W, 3, 1>(L); return true; }
-  return false;
-}
-
-bool pick_kernels(int W, int ds, int unst, int L, KernelSet* k) {
-  if (W == 32) return pick_ds<32>(ds, unst, L, k);
-  if (W == 64) return pick_ds<64>(ds, unst, L, k);
-  if (W == 128) return pick_ds<128>(ds, unst, L, k);
+bool pick_kernels(int W, int ds, int unst, int L, int act, KernelSet* k) {
+  const bool sn = (act == DPINN_ACT_SIN);
+  if (W == 32) return sn ? dk::kernels_w32_sin(ds, unst, L, k) : dk::kernels_w32_tanh(ds, unst, L, k);
+  if (W == 64) return sn ? dk::kernels_w64_sin(ds, unst, L, k) : dk::kernels_w64_tanh(ds, unst, L, k);
+  if (W == 128) return sn ? dk::kernels_w128_sin(ds, unst, L, k) : dk::kernels_w128_tanh(ds, unst, L, k);
   return false;
 }
 
@@ -558,7 +524,8 @@ int dpinn_create(const dpinn_config* cfg, dpinn_t** out) {
   if (c.unsteady != 0 && c.unsteady != 1) return fail(nullptr, DPINN_ERR_INVALID_ARG, "unsteady must be 0 or 1");
   if (c.width != 32 && c.width != 64 && c.width != 128) return fail(nullptr, DPINN_ERR_INVALID_ARG, "width must be 32, 64 or 128");
   if (c.depth < 1 || c.depth > dk::MAXL) return fail(nullptr, DPINN_ERR_INVALID_ARG, "depth must be in [1, 16]");
-  if (c.activation != DPINN_ACT_TANH) return fail(nullptr, DPINN_ERR_INVALID_ARG, "only tanh is supported");
+  if (c.activation != DPINN_ACT_TANH && c.activation != DPINN_ACT_SIN)
+    return fail(nullptr, DPINN_ERR_INVALID_ARG, "activation must be tanh or sin");
   if (c.precision != DPINN_PREC_FP32) return fail(nullptr, DPINN_ERR_INVALID_ARG, "only FP32 is supported");
   if (!(c.nu >= 0)) return fail(nullptr, DPINN_ERR_INVALID_ARG, "nu must be >= 0");
   if (c.comm_interval < 1) return fail(nullptr, DPINN_ERR_INVALID_ARG, "comm_interval must be >= 1");
@@ -580,7 +547,8 @@ int dpinn_create(const dpinn_config* cfg, dpinn_t** out) {
   h->ds = c.d_space; h->unst = c.unsteady; h->din = din; h->dout = c.d_space + 1;
   h->W = c.width; h->L = c.depth;
   h->n_nets = (int)nn;
-  if (!pick_kernels(h->W, h->ds, h->unst, h->L, &h->ks)) return fail(nullptr, DPINN_ERR_INVALID_ARG, "unsupported shape");
+  if (!pick_kernels(h->W, h->ds, h->unst, h->L, c.activation, &h->ks))
+    return fail(nullptr, DPINN_ERR_INVALID_ARG, "unsupported shape");
   // decomposition
   int s = 1;
   for (int a = 0; a < din; ++a) { h->stride.push_back(s); s *= c.splits[a]; }
@@ -629,6 +597,7 @@ int dpinn_create(const dpinn_config* cfg, dpinn_t** out) {
   h->npp = ((off + 63) / 64) * 64;
   h->nTp = std::max(1, (h->L - 1) * h->W * h->W);
   sh.npp = h->npp; sh.nTp = h->nTp;
+  sh.act = (c.activation == DPINN_ACT_SIN) ? dk::ACT_SIN : dk::ACT_TANH;
   sh.nu = (float)c.nu; sh.p_ref = (float)c.p_ref;
   for (int a = 0; a < 3; ++a) { sh.anchor[a] = (float)c.anchor_x[a]; sh.comp_w[a] = (float)c.comp_w[a]; }
   sh.lam_obs = (float)c.lambda_obs; sh.lam_pde = (float)c.lambda_pde; sh.lam_gh_u = (float)c.lambda_gh_u;

@@ -1,0 +1,28 @@
+// Kernel sets of the grouped kernel k_pinn: one translation unit per width
+// and activation instantiates them (kernels_w*_*.cu), so that the many
+// instantiations compile in parallel.
+#pragma once
+#include <cstddef>
+
+namespace dk {
+
+struct KernelSet {
+  const void* train_jet = nullptr;
+  const void* train_val = nullptr;
+  const void* eval_val = nullptr;
+  const void* query_val = nullptr;
+  const void* query_jet = nullptr;
+  size_t smem_jet = 0, smem_val = 0;
+  int P_jet = 0, P_val = 0;
+  long long stash_jet = 0, stash_val = 0;   // floats per CTA
+};
+
+// Fill *k for (d_space, unsteady, depth); false if the shape is unsupported.
+bool kernels_w32_tanh(int ds, int unst, int L, KernelSet* k);
+bool kernels_w64_tanh(int ds, int unst, int L, KernelSet* k);
+bool kernels_w128_tanh(int ds, int unst, int L, KernelSet* k);
+bool kernels_w32_sin(int ds, int unst, int L, KernelSet* k);
+bool kernels_w64_sin(int ds, int unst, int L, KernelSet* k);
+bool kernels_w128_sin(int ds, int unst, int L, KernelSet* k);
+
+}  // namespace dk

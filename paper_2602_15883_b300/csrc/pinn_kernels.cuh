@@ -44,6 +44,7 @@ struct Shape {
   int npp;                     // padded per-net parameter stride (floats)
   int nTp;                     // per-net stride of the transposed hidden weights
   int woff[MAXL + 1], boff[MAXL + 1];
+  int act;                     // ACT_TANH or ACT_SIN
   float nu, p_ref;
   float anchor[3];
   float lam_obs, lam_pde, lam_gh_u, lam_time;
@@ -188,52 +189,87 @@ __device__ __forceinline__ void mbar_wait(uint64_t* bar, uint32_t parity, int* e
 }
 
 // ------------------------------------------------------ jet algebra ---
-// tanh jets per neuron: a = tanh(z), s1 = 1 - a^2, s2 = -2 a s1,
-// d_q a = s1 d_q z, lap a = s2 * sum_{spatial q} (d_q z)^2 + s1 * lap z.
-// Activation jet from the stashed form h = (a = tanh z, d_q z, lap z): the
-// tanh derivatives are polynomials in a, so no tanh is re-evaluated.
-template <int C, int DS, int DIN>
+// Activation jets per neuron, a = sigma(z) with s1, s2, s3 the first three
+// derivatives of sigma:  d_q a = s1 d_q z,  lap a = s2 * sum_{spatial q}
+// (d_q z)^2 + s1 * lap z.
+//   tanh: s1 = 1 - a^2, s2 = -2 a s1, s3 = -2 s1 (1 - 3 a^2), all
+//         polynomials in a, so the stash keeps a = tanh z in the value
+//         channel and the reverse pass evaluates no tanh;
+//   sin:  s1 = cos z, s2 = -sin z, s3 = -cos z; cos z is not a function of
+//         sin z, so the stash keeps z itself.
+enum { ACT_TANH = 0, ACT_SIN = 1 };
+
+struct ActD {
+  float a, s1, s2, s3;
+};
+
+// derivatives from the stashed value channel h0 (a for tanh, z for sin)
+template <int ACT>
+__device__ __forceinline__ ActD act_derivs(float h0) {
+  ActD d;
+  if constexpr (ACT == ACT_SIN) {
+    float sn, cs;
+    sincosf(h0, &sn, &cs);
+    d.a = sn; d.s1 = cs; d.s2 = -sn; d.s3 = -cs;
+  } else {
+    d.a = h0;
+    d.s1 = 1.f - h0 * h0;
+    d.s2 = -2.f * h0 * d.s1;
+    d.s3 = -2.f * d.s1 * (1.f - 3.f * h0 * h0);
+  }
+  return d;
+}
+
+// value channel of the stashed form from the pre-activation
+template <int ACT>
+__device__ __forceinline__ float stash_value(float z) {
+  if constexpr (ACT == ACT_SIN) return z;
+  else return tanhf(z);
+}
+
+// Activation jet from the stashed form h = (h0, d_q z, lap z).
+template <int C, int DS, int DIN, int ACT>
 __device__ __forceinline__ void act_from_stash(const float* h, float* a) {
-  const float t = h[0];
-  a[0] = t;
-  if constexpr (C > 1) {
-    const float s1 = 1.f - t * t;
-    const float s2 = -2.f * t * s1;
+  if constexpr (C == 1) {
+    if constexpr (ACT == ACT_SIN) a[0] = sinf(h[0]);
+    else a[0] = h[0];
+  } else {
+    const ActD d = act_derivs<ACT>(h[0]);
+    a[0] = d.a;
     float S = 0.f;
 #pragma unroll
     for (int q = 0; q < DS; ++q) S = fmaf(h[1 + q], h[1 + q], S);
 #pragma unroll
-    for (int q = 0; q < DIN; ++q) a[1 + q] = s1 * h[1 + q];
-    a[C - 1] = fmaf(s2, S, s1 * h[C - 1]);
+    for (int q = 0; q < DIN; ++q) a[1 + q] = d.s1 * h[1 + q];
+    a[C - 1] = fmaf(d.s2, S, d.s1 * h[C - 1]);
   }
 }
 
 // Adjoint of the activation: from the activation-jet adjoints ab to the
-// pre-activation-jet adjoints zb, given the stashed form h = (a, d_q z,
-// lap z) (s3 = d s2 / dz = -2 s1 (1 - 3 a^2)).
-template <int C, int DS, int DIN>
+// pre-activation-jet adjoints zb, given the stashed form h.
+template <int C, int DS, int DIN, int ACT>
 __device__ __forceinline__ void act_bwd(const float* z, const float* ab, float* zb) {
-  const float t = z[0];
-  const float s1 = 1.f - t * t;
   if constexpr (C == 1) {
+    float s1;
+    if constexpr (ACT == ACT_SIN) s1 = cosf(z[0]);
+    else s1 = 1.f - z[0] * z[0];
     zb[0] = ab[0] * s1;
   } else {
-    const float s2 = -2.f * t * s1;
-    const float s3 = -2.f * s1 * (1.f - 3.f * t * t);
+    const ActD d = act_derivs<ACT>(z[0]);
     const float al = ab[C - 1];
     float S = 0.f;
 #pragma unroll
     for (int q = 0; q < DS; ++q) S = fmaf(z[1 + q], z[1 + q], S);
-    float v = fmaf(ab[0], s1, al * fmaf(s3, S, s2 * z[C - 1]));
+    float v = fmaf(ab[0], d.s1, al * fmaf(d.s3, S, d.s2 * z[C - 1]));
 #pragma unroll
     for (int q = 0; q < DIN; ++q) {
-      float g = ab[1 + q] * s1;
-      if (q < DS) g = fmaf(2.f * al * s2, z[1 + q], g);
+      float g = ab[1 + q] * d.s1;
+      if (q < DS) g = fmaf(2.f * al * d.s2, z[1 + q], g);
       zb[1 + q] = g;
-      v = fmaf(ab[1 + q] * s2, z[1 + q], v);
+      v = fmaf(ab[1 + q] * d.s2, z[1 + q], v);
     }
     zb[0] = v;
-    zb[C - 1] = al * s1;
+    zb[C - 1] = al * d.s1;
   }
 }
 
@@ -325,7 +361,7 @@ __device__ __forceinline__ void grad_rmw(float* g, float v, bool first) {
 }
 
 // ------------------------------------------------------ the kernel ---
-template <int W, int DS, int UNST, bool JETS, int MODE>
+template <int W, int DS, int UNST, bool JETS, int MODE, int ACT>
 __global__ void __launch_bounds__(NT, 1)
     k_pinn(const Shape sh, const Bufs b, const Item* __restrict__ items, const int* __restrict__ n_items_ptr) {
   constexpr int DIN = DS + UNST;
@@ -409,12 +445,12 @@ __global__ void __launch_bounds__(NT, 1)
       }
     }
   };
-  // z -> stashed form in place: the value channel becomes a = tanh(z)
+  // z -> stashed form in place (value channel: tanh z, or z for sin)
   auto to_stash_form = [&](float (&z)[TM][NCOL]) {
 #pragma unroll
     for (int m = 0; m < TM; ++m)
 #pragma unroll
-      for (int pp = 0; pp < TP; ++pp) z[m][pp * C] = tanhf(z[m][pp * C]);
+      for (int pp = 0; pp < TP; ++pp) z[m][pp * C] = stash_value<ACT>(z[m][pp * C]);
   };
   // activations of the thread tile (from the stashed form) into smem
   auto act_store = [&](float* buf, const float (&h)[TM][NCOL]) {
@@ -422,7 +458,7 @@ __global__ void __launch_bounds__(NT, 1)
     for (int m = 0; m < TM; ++m) {
       float a[NCOL];
 #pragma unroll
-      for (int pp = 0; pp < TP; ++pp) act_from_stash<C, DS, DIN>(&h[m][pp * C], &a[pp * C]);
+      for (int pp = 0; pp < TP; ++pp) act_from_stash<C, DS, DIN, ACT>(&h[m][pp * C], &a[pp * C]);
       sts_vec<NCOL, VEC>(buf + ROW(n0 + m) + col0, a);
     }
   };
@@ -732,7 +768,7 @@ __global__ void __launch_bounds__(NT, 1)
         for (int m = 0; m < TM; ++m) {
           float zz[NCOL];
 #pragma unroll
-          for (int pp = 0; pp < TP; ++pp) act_bwd<C, DS, DIN>(&z[m][pp * C], &a[m][pp * C], &zz[pp * C]);
+          for (int pp = 0; pp < TP; ++pp) act_bwd<C, DS, DIN, ACT>(&z[m][pp * C], &a[m][pp * C], &zz[pp * C]);
           sts_vec<NCOL, VEC>(zb + ROW(n0 + m) + col0, zz);
         }
       }
@@ -820,7 +856,7 @@ __global__ void __launch_bounds__(NT, 1)
         for (int m = 0; m < TM; ++m) {
           float zz[NCOL];
 #pragma unroll
-          for (int pp = 0; pp < TP; ++pp) act_bwd<C, DS, DIN>(&z[m][pp * C], &a[m][pp * C], &zz[pp * C]);
+          for (int pp = 0; pp < TP; ++pp) act_bwd<C, DS, DIN, ACT>(&z[m][pp * C], &a[m][pp * C], &zz[pp * C]);
           sts_vec<NCOL, VEC>(zb + ROW(n0 + m) + col0, zz);
         }
       }
@@ -853,210 +889,6 @@ __global__ void __launch_bounds__(NT, 1)
       }
     }
   }   // items
-}
-
-// ----------------------------------------------- reduction + Adam ---
-// grad[k][j] = sum over the work items of net k (fixed order); per-block
-// partial squared norms for clipping.
-__global__ void k_reduce_grad(const float* __restrict__ part, const int* __restrict__ slot_begin,
-                              float* __restrict__ grad, float* __restrict__ norm_part, int npp, int n_params) {
-  __shared__ float red[NT / 32];
-  const int k = blockIdx.y;
-  const int j = blockIdx.x * NT + threadIdx.x;
-  float gsum = 0.f;
-  if (j < n_params) {
-    const int s0 = slot_begin[k], s1 = slot_begin[k + 1];
-    for (int s = s0; s < s1; ++s) gsum += part[(size_t)s * npp + j];
-    grad[(size_t)k * npp + j] = gsum;
-  }
-  const float tot = block_sum(gsum * gsum, red);
-  if (threadIdx.x == 0) norm_part[(size_t)k * gridDim.x + blockIdx.x] = tot;
-}
-
-// Per-net clip coefficient min(1, clip / (||g|| + 1e-6)), fixed-order sum.
-__global__ void k_clip_coef(const float* __restrict__ norm_part, int nblk, float clip, float* __restrict__ coef) {
-  __shared__ float red[NT / 32];
-  const int k = blockIdx.x;
-  float s = 0.f;
-  for (int i = threadIdx.x; i < nblk; i += NT) s += norm_part[(size_t)k * nblk + i];
-  const float tot = block_sum(s, red);
-  if (threadIdx.x == 0) {
-    const float c = clip / (sqrtf(tot) + 1e-6f);
-    coef[k] = c < 1.f ? c : 1.f;
-  }
-}
-
-struct AdamArgs {
-  double lr, beta1, beta2, eps;
-  int use_clip;
-  double decay_factor;   // lr * decay_factor^floor((t-1)/decay_interval)
-  int decay_interval;    // 0: constant lr
-};
-// (1 - beta) factors are formed in double on the host and rounded once:
-// 1.f - 0.999f would carry a 1.3e-5 relative error into the second moment.
-
-// Adam (PyTorch's rule) on every parameter of every net; rewrites the
-// transposed copies of the hidden weights used by the forward pass.
-__global__ void k_adam(const Shape sh, AdamArgs ar, float* __restrict__ theta, float* __restrict__ thetaT,
-                       float* __restrict__ m, float* __restrict__ v, const float* __restrict__ grad,
-                       const float* __restrict__ coef, const long long* __restrict__ step, int n_params) {
-  __shared__ float s_c[4];
-  if (threadIdx.x == 0) {
-    const double t = (double)(*step + 1);
-    const double bc1 = 1.0 - pow(ar.beta1, t);
-    const double bc2 = 1.0 - pow(ar.beta2, t);
-    double lr = ar.lr;
-    if (ar.decay_interval > 0) lr *= pow(ar.decay_factor, (double)((*step) / ar.decay_interval));
-    s_c[0] = (float)(lr / bc1);
-    s_c[1] = (float)(1.0 / sqrt(bc2));
-  }
-  __syncthreads();
-  const int k = blockIdx.y;
-  const int j = blockIdx.x * NT + threadIdx.x;
-  if (j >= n_params) return;
-  const size_t idx = (size_t)k * sh.npp + j;
-  float gj = grad[idx];
-  if (ar.use_clip) gj *= coef[k];
-  const float b1 = (float)ar.beta1, b2 = (float)ar.beta2;
-  const float omb1 = (float)(1.0 - ar.beta1), omb2 = (float)(1.0 - ar.beta2);
-  const float mj = fmaf(b1, m[idx], omb1 * gj);
-  const float vj = fmaf(b2, v[idx], omb2 * gj * gj);
-  m[idx] = mj;
-  v[idx] = vj;
-  const float denom = sqrtf(vj) * s_c[1] + (float)ar.eps;
-  const float th = theta[idx] - s_c[0] * (mj / denom);
-  theta[idx] = th;
-  const int W = sh.W;
-  for (int l = 1; l < sh.L; ++l) {
-    if (j >= sh.woff[l] && j < sh.boff[l]) {
-      const int r = j - sh.woff[l], i = r / W, c = r % W;
-      thetaT[(size_t)k * sh.nTp + (size_t)(l - 1) * W * W + (size_t)c * W + i] = th;
-    }
-  }
-}
-
-// Rebuild the transposed hidden weights from theta (after set_state/init).
-__global__ void k_transpose(const Shape sh, const float* __restrict__ theta, float* __restrict__ thetaT) {
-  const int k = blockIdx.y;
-  const int W = sh.W;
-  const int e = blockIdx.x * NT + threadIdx.x;
-  if (e >= (sh.L - 1) * W * W) return;
-  const int l = 1 + e / (W * W), r = e % (W * W), i = r / W, c = r % W;
-  thetaT[(size_t)k * sh.nTp + (size_t)(l - 1) * W * W + (size_t)c * W + i] = theta[(size_t)k * sh.npp + sh.woff[l] + r];
-}
-
-// Loss record per net: fixed-order sum of the item partials, 1/N factors,
-// weighted total (Eq. (16)); non-finite values raise ERR_NONFINITE.
-__global__ void k_loss_record(const Shape sh, const double* __restrict__ loss_part, const int* __restrict__ slot_begin,
-                              const NetInfo* __restrict__ nets, int n_nets, float* __restrict__ rec, int* err,
-                              long long* step, int bump) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k == 0 && bump) *step += 1;
-  if (k >= n_nets) return;
-  double s[5] = {0, 0, 0, 0, 0};
-  for (int i = slot_begin[k]; i < slot_begin[k + 1]; ++i)
-    for (int q = 0; q < 5; ++q) s[q] += loss_part[(size_t)i * 5 + q];
-  const NetInfo ni = nets[k];
-  const double lo = s[0] * ni.inv_nobs, lp = s[1] * ni.inv_npde, lu = s[2] * ni.inv_ngh,
-               ls = s[3] * ni.inv_ngh, lt = s[4] * ni.inv_ngh;
-  const double tot = sh.lam_obs * lo + sh.lam_pde * lp + sh.lam_gh_u * lu + ni.lam_space * ls + sh.lam_time * lt;
-  const double v[6] = {lo, lp, lu, ls, lt, tot};
-  for (int q = 0; q < 6; ++q) {
-    rec[k * 6 + q] = (float)v[q];
-    if (!isfinite(v[q])) atomicExch(err + ERR_NONFINITE, 1);
-  }
-}
-
-// ----------------------------------------------------------- routing ---
-struct Route {
-  float lo[4], hi[4], inv_h[4];
-  int splits[4], stride[4];
-  int din, n_nets;
-};
-
-// Cell of every query point (float32 rule of the C ABI) and per-net counts.
-__global__ void k_route(const Route rt, const float* __restrict__ pts, long long n, int* __restrict__ net_of,
-                        int* __restrict__ counts, int* err) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int net = 0;
-  bool ok = true;
-  for (int a = 0; a < rt.din; ++a) {
-    const float x = pts[i * rt.din + a];
-    if (!(x >= rt.lo[a] && x <= rt.hi[a])) { ok = false; break; }
-    const float q = __fmul_rn(__fsub_rn(x, rt.lo[a]), rt.inv_h[a]);
-    int c = (int)floorf(q);
-    c = c < 0 ? 0 : (c > rt.splits[a] - 1 ? rt.splits[a] - 1 : c);
-    net += c * rt.stride[a];
-  }
-  if (!ok) {
-    net_of[i] = -1;
-    atomicExch(err + ERR_DOMAIN, 1);
-    return;
-  }
-  net_of[i] = net;
-  atomicAdd(counts + net, 1);
-}
-
-// Single block: segment offsets per net and the query work items (chunks of
-// `chunk` points); cursor[] starts at the offsets for the scatter.
-__global__ void k_route_plan(const int* __restrict__ counts, int n_nets, int chunk, int* __restrict__ offsets,
-                             int* __restrict__ cursor, Item* __restrict__ items, int* __restrict__ n_items) {
-  if (threadIdx.x != 0) return;
-  int off = 0, ni = 0;
-  for (int k = 0; k < n_nets; ++k) {
-    offsets[k] = off;
-    cursor[k] = off;
-    const int c = counts[k];
-    for (int s = 0; s < c; s += chunk) {
-      Item it;
-      it.kind = K_QUERY; it.net = k; it.begin = off + s; it.count = min(chunk, c - s);
-      it.slot = 0; it.face = 0; it.side = 0; it.pad = 0;
-      items[ni++] = it;
-    }
-    off += c;
-  }
-  *n_items = ni;
-}
-
-__global__ void k_route_scatter(const int* __restrict__ net_of, long long n, int* __restrict__ cursor,
-                                int* __restrict__ perm) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int k = net_of[i];
-  if (k < 0) return;
-  perm[atomicAdd(cursor + k, 1)] = (int)i;
-}
-
-// --------------------------------------------------- initialisation ---
-__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
-  x += 0x9E3779B97F4A7C15ull;
-  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
-  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
-  return x ^ (x >> 31);
-}
-
-// Xavier-normal weights (std sqrt(2/(fan_in+fan_out))), zero biases; normal
-// deviates by Box-Muller from a SplitMix64 counter stream keyed by
-// (seed, net, parameter index).
-__global__ void k_init(const Shape sh, uint64_t seed, float* __restrict__ theta, int n_params) {
-  const int k = blockIdx.y;
-  const int j = blockIdx.x * NT + threadIdx.x;
-  if (j >= n_params) return;
-  float val = 0.f;
-  for (int l = 0; l <= sh.L; ++l) {
-    const int fo = (l == sh.L) ? sh.dout : sh.W;
-    const int fi = (l == 0) ? sh.din : sh.W;
-    if (j >= sh.woff[l] && j < sh.boff[l]) {
-      const uint64_t key = splitmix64(seed ^ splitmix64(((uint64_t)k << 32) | (uint64_t)j));
-      const uint64_t r2 = splitmix64(key);
-      const double u1 = ((key >> 11) + 1.0) * (1.0 / 9007199254740993.0);
-      const double u2 = (r2 >> 11) * (1.0 / 9007199254740992.0);
-      const double nrm = sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
-      val = (float)(nrm * sqrt(2.0 / (fi + fo)));
-    }
-  }
-  theta[(size_t)k * sh.npp + j] = val;
 }
 
 }  // namespace dk

@@ -61,6 +61,12 @@ def small_case(name):
     elif name == "unsteady3d_w64":
         cfg = synth.config("beltrami32", width=64, depth=4, splits=[2, 1, 1, 2], anchor=[0.4, -0.3, 0.1])
         res, obs, face = (150, 50), (40, 12), (30, 9)
+    elif name == "tgv_sin":
+        cfg = synth.config("tgv", splits=[2, 2, 2, 1], activation=1)
+        res, obs, face = (300, 70), (60, 20), (45, 12)
+    elif name == "beltrami_sin":
+        cfg = synth.config("beltrami32", splits=[2, 1, 1, 2], activation=1)
+        res, obs, face = (150, 40), (40, 12), (30, 9)
     elif name == "unsteady2d_w128_deep":
         cfg = synth.config("tgv", width=128, depth=3, splits=[1, 2, 3, 1], anchor=[3.0, 1.0, 0.0])
         res, obs, face = (90, 30), (20, 8), (20, 8)
@@ -80,7 +86,7 @@ def small_case(name):
 
 
 CASES = ["kovasznay", "tgv", "beltrami32", "beltrami128", "steady3d_w64", "unsteady3d_w32",
-         "unsteady3d_w64", "unsteady2d_w128_deep"]
+         "unsteady3d_w64", "unsteady2d_w128_deep", "tgv_sin", "beltrami_sin"]
 
 
 def compare_losses(gpu, ref, tol=LOSS_TOL):
@@ -112,7 +118,7 @@ def test_losses_and_gradients_match_oracle(name):
         assert g[0, -1] == 0.0 and og[0, -1] == 0.0
 
 
-@pytest.mark.parametrize("name", ["kovasznay", "tgv", "beltrami32"])
+@pytest.mark.parametrize("name", ["kovasznay", "tgv", "beltrami32", "beltrami_sin"])
 def test_one_step_matches_oracle(name):
     Dpinn = _gpu()
     cfg, pb = small_case(name)
