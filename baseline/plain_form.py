@@ -71,6 +71,21 @@ class PlainForm:
             self.net_faces[a].append((f, 0))
             self.net_faces[b].append((f, 1))
         self.w = torch.tensor(cfg["comp_w"][: self.ds], dtype=dtype, device=self.dev)
+        # volumetric ghost layers: per net, its ghost points grouped by owner
+        self.ghost = None
+        if getattr(problem, "ghost_counts", None) is not None:
+            go = np.concatenate([[0], np.cumsum(problem.ghost_counts)])
+            owners = synth.owner_net(cfg, problem.ghost_pts)
+            self.ghost = []
+            for k in range(self.nn):
+                own = owners[go[k]:go[k + 1]]
+                pts = problem.ghost_pts[go[k]:go[k + 1]]
+                groups = []
+                for B in sorted(set(own.tolist())):
+                    same_space = all(synth.cell_of_net(cfg, k)[a] == synth.cell_of_net(cfg, B)[a]
+                                     for a in range(self.ds))
+                    groups.append((B, t(pts[own == B]).to(dtype), bool(self.unst and same_space)))
+                self.ghost.append(groups)
         self.opt = torch.optim.Adam([p for ps in self.params for p in ps], lr=cfg["lr"],
                                     betas=(cfg["beta1"], cfg["beta2"]), eps=cfg["eps"])
         iv = int(cfg.get("lr_decay_interval", 0))
@@ -115,9 +130,23 @@ class PlainForm:
         r.append(sum(grads[i][:, i] for i in range(ds)))
         return torch.stack(r, 1)
 
+    def _message(self, k, x):
+        """Net k's velocity and (anchor-normalised if k is a master) pressure at x."""
+        y = self.net(k, x)
+        P = y[:, self.ds]
+        if self.master[k]:
+            import numpy as np
+            xa = x.clone()
+            xa[:, : self.ds] = torch.tensor(np.float32(self.cfg["anchor"][: self.ds]), dtype=self.dt, device=self.dev)
+            P = P - self.net(k, xa)[:, self.ds]
+        return y[:, : self.ds], P
+
     def exchange(self):
         """Neighbour messages at the current parameters (detached)."""
         import numpy as np
+        if self.ghost is not None:
+            with torch.no_grad():
+                return [[(B, x, tm, self._message(B, x)) for (B, x, tm) in groups] for groups in self.ghost]
         msgs = []
         with torch.no_grad():
             for f, (a, b, ax) in enumerate(self.faces):
@@ -143,8 +172,19 @@ class PlainForm:
         if len(self.obs[k]):
             e = self.net(k, self.obs[k])[:, : self.ds] - self.obsv[k]
             lobs = (self.w * e * e).sum(1).mean()
+        if self.ghost is not None:
+            ngh = sum(len(x) for (_, x, _) in self.ghost[k])
+            for (B, x, tm, (U, P)) in msgs[k]:
+                y = self.net(k, x)
+                e = y[:, : self.ds] - U
+                lgu = lgu + (self.w * e * e).sum() / ngh
+                ep = ((y[:, self.ds] - P) ** 2).sum() / ngh
+                if tm:
+                    ltm = ltm + ep
+                else:
+                    lsp = lsp + ep
         ngh = sum(len(self.fpts[f]) for f, _ in self.net_faces[k])
-        for f, side in self.net_faces[k]:
+        for f, side in (self.net_faces[k] if self.ghost is None else []):
             U, P = msgs[f][1 - side]
             y = self.net(k, self.fpts[f])
             e = y[:, : self.ds] - U

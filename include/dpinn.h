@@ -81,7 +81,7 @@ enum {
   DPINN_ERR_STATE = -7
 };
 
-enum { DPINN_POINTS_RESIDUAL = 0, DPINN_POINTS_OBS = 1, DPINN_POINTS_FACE = 2 };
+enum { DPINN_POINTS_RESIDUAL = 0, DPINN_POINTS_OBS = 1, DPINN_POINTS_FACE = 2, DPINN_POINTS_GHOST = 3 };
 /* Hidden-layer activation: tanh, or sin (the paper's cylinder cases,
  * Table B1). */
 enum { DPINN_ACT_TANH = 0, DPINN_ACT_SIN = 1 };
@@ -149,6 +149,17 @@ int dpinn_face_info(dpinn_t* h, int face, int* net_lo, int* net_hi, int* axis, i
  *                  counts[n_nets].
  *   kind FACE:     pts [n][d_in], counts[n_faces] (points of face 0 first;
  *                  each point must lie on its face).
+ *   kind GHOST:    pts [n][d_in], counts[n_nets]: the paper's volumetric
+ *                  ghost layers (Sec. 2.2, thickness delta > 0): net A's
+ *                  points lie in its cell grown by delta, outside the cell
+ *                  itself.  Each point is routed (float32 rule) to the net B
+ *                  whose cell holds it - corner regions reach diagonal
+ *                  neighbours - and A's ghost terms compare against B's
+ *                  prediction there (anchor-normalised when B is a master).
+ *                  The pressure term is temporal when A and B share their
+ *                  spatial cell, spatial otherwise.  Replaces FACE points
+ *                  (delivering FACE points switches back).  A point inside
+ *                  A's own cell or outside the domain is INVALID_ARG.
  * pts/vals may be host or device pointers.  n_counts must equal n_nets (or
  * n_faces).  Counts may be 0.  Re-delivering the same counts only copies;
  * new counts rebuild the work lists and the captured step.  Errors:

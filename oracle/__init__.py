@@ -47,6 +47,7 @@ class ProblemC(C.Structure):
         ("res_pts", C.c_void_p), ("res_counts", C.c_void_p),
         ("obs_pts", C.c_void_p), ("obs_vals", C.c_void_p), ("obs_counts", C.c_void_p),
         ("face_pts", C.c_void_p), ("face_counts", C.c_void_p),
+        ("ghost_pts", C.c_void_p), ("ghost_counts", C.c_void_p),
     ]
 
 
@@ -146,8 +147,12 @@ class Oracle:
                 np.ascontiguousarray(pb.obs_pts, np.float32), np.ascontiguousarray(pb.obs_vals, np.float32),
                 np.ascontiguousarray(pb.obs_counts, np.int64), np.ascontiguousarray(pb.face_pts, np.float32),
                 np.ascontiguousarray(pb.face_counts, np.int64)]
+        gc = getattr(pb, "ghost_counts", None)
+        if gc is not None:
+            arrs += [np.ascontiguousarray(pb.ghost_pts, np.float32), np.ascontiguousarray(gc, np.int64)]
         self._keep = arrs
-        self.pc = ProblemC(*[a.ctypes.data for a in arrs])
+        ptrs = [a.ctypes.data for a in arrs] + ([None, None] if gc is None else [])
+        self.pc = ProblemC(*ptrs)
 
     # -- pieces ------------------------------------------------------------
     def forward(self, net, th_net, x, jets=True):

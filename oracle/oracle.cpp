@@ -72,6 +72,9 @@ struct ora_problem {
   const float* obs_pts;  const float* obs_vals;       // [n_obs][d_in], [n_obs][d_space]
   const int64_t* obs_counts;                          // [n_nets]
   const float* face_pts; const int64_t* face_counts;  // [n_face][d_in], [n_faces]
+  // Volumetric ghost layers (delta > 0): points of each net outside its own
+  // cell; when ghost_counts is set they replace the face points.
+  const float* ghost_pts; const int64_t* ghost_counts;  // [n_ghost][d_in], [n_nets]
 };
 
 
@@ -358,11 +361,18 @@ struct Prob {
     o = 0;
     for (int f = 0; f < g.n_faces; ++f) { face_off.push_back(o); o += p.face_counts ? p.face_counts[f] : 0; }
     face_off.push_back(o);
+    o = 0;
+    for (int k = 0; k < g.n_nets; ++k) { ghost_off.push_back(o); o += p.ghost_counts ? p.ghost_counts[k] : 0; }
+    ghost_off.push_back(o);
   }
+  bool ghost_mode() const { return p.ghost_counts != nullptr; }
+  void ghost_x(int64_t i, double* x) const { for (int q = 0; q < g.din; ++q) x[q] = p.ghost_pts[i * g.din + q]; }
+  std::vector<int64_t> ghost_off;
   void res_x(int64_t i, double* x) const { for (int q = 0; q < g.din; ++q) x[q] = p.res_pts[i * g.din + q]; }
   void obs_x(int64_t i, double* x) const { for (int q = 0; q < g.din; ++q) x[q] = p.obs_pts[i * g.din + q]; }
   void face_x(int64_t i, double* x) const { for (int q = 0; q < g.din; ++q) x[q] = p.face_pts[i * g.din + q]; }
   int64_t n_gh(int net) const {
+    if (ghost_mode()) return ghost_off[net + 1] - ghost_off[net];
     int64_t n = 0;
     for (auto& fs : g.net_faces[net]) n += face_off[fs.first + 1] - face_off[fs.first];
     return n;
@@ -374,7 +384,21 @@ struct Prob {
 // for a master side (0 otherwise).
 struct Nbr {
   std::vector<double> val, anc;
+  // ghost mode: per ghost point, the owner net and its (u, p) and anchor p
+  std::vector<int> owner;
+  std::vector<double> gval, ganc;
 };
+
+// Net whose cell holds x (float32 rule), -1 outside the domain.
+int route_fp32(const Geo& g, const double* x) {
+  int net = 0;
+  for (int a = 0; a < g.din; ++a) {
+    int k = cell_fp32(g.cfg, a, (float)x[a]);
+    if (k < 0) return -1;
+    net += k * g.stride[a];
+  }
+  return net;
+}
 
 // The anchor's coordinates are taken at float32 precision, the precision of
 // every point the method is given, so a query point placed on x_anc hits it
@@ -396,6 +420,32 @@ T value_p(const Geo& g, int net, const T* th, const double* x) {
 Nbr exchange(const Prob& pb, const double* th_all, const std::vector<char>* need = nullptr) {
   const Geo& g = pb.g;
   Nbr nb;
+  if (pb.ghost_mode()) {
+    // each ghost point of net A is evaluated by the net B whose cell holds it
+    const int64_t n = pb.ghost_off.back();
+    nb.owner.assign(n, -1);
+    nb.gval.assign((size_t)n * g.dout, 0.0);
+    nb.ganc.assign(n, 0.0);
+    std::vector<double> Zg((size_t)g.L * g.W), Yg(g.dout);
+    for (int A = 0; A < g.n_nets; ++A) {
+      if (need && !(*need)[A]) continue;
+      for (int64_t i = pb.ghost_off[A]; i < pb.ghost_off[A + 1]; ++i) {
+        double x[4], xa[4];
+        pb.ghost_x(i, x);
+        const int B = route_fp32(g, x);
+        nb.owner[i] = B;
+        if (B < 0) continue;
+        const double* th = th_all + (size_t)B * g.n_params;
+        forward(g, B, th, x, false, Zg.data(), Yg.data());
+        for (int j = 0; j < g.dout; ++j) nb.gval[(size_t)i * g.dout + j] = Yg[j];
+        if (g.master[B]) {
+          anchor_point(g, x, xa);
+          nb.ganc[i] = value_p(g, B, th, xa);
+        }
+      }
+    }
+    return nb;
+  }
   int64_t nf = pb.face_off.back();
   nb.val.assign((size_t)nf * 2 * g.dout, 0.0);
   nb.anc.assign((size_t)nf * 2, 0.0);
@@ -434,6 +484,20 @@ void ghost_target(const Prob& pb, const Nbr& nb, int f, int64_t i, int side, dou
 
 double lam_space(const Geo& g, int net) { return g.master[net] ? 0.0 : g.cfg.lam_gh_p_space; }
 
+// Volumetric ghost point i of net A: the owner B's velocity and (anchor-
+// normalised if B is a master) pressure; the pressure term is temporal when
+// A and B share their spatial cell (a purely temporal neighbour).
+void ghost_target_vol(const Prob& pb, const Nbr& nb, int A, int64_t i, double* U, double* P, bool* is_time) {
+  const Geo& g = pb.g;
+  const int B = nb.owner[i];
+  const double* v = &nb.gval[(size_t)i * g.dout];
+  for (int c = 0; c < g.ds; ++c) U[c] = v[c];
+  *P = v[g.ds] - (g.master[B] ? nb.ganc[i] : 0.0);
+  bool same_space = true;
+  for (int a = 0; a < g.ds; ++a) same_space = same_space && g.cell[A][a] == g.cell[B][a];
+  *is_time = g.unst && same_space;
+}
+
 // Loss terms of net A at parameters thA (T = double or complex for the
 // complex-step pins): out = {L_obs, L_PDE, L_gh_u, L_gh_p^space,
 // L_gh_p^time, L_total}.  Eq. (3), Eq. (5), Eqs. (13)-(14), Eq. (16).
@@ -463,6 +527,7 @@ void net_loss(const Prob& pb, const Nbr& nb, int A, const T* thA, T* out) {
   }
   int64_t ngh = pb.n_gh(A);
   for (auto& fs : g.net_faces[A]) {
+    if (pb.ghost_mode()) break;
     int f = fs.first, side = fs.second;
     for (int64_t i = pb.face_off[f]; i < pb.face_off[f + 1]; ++i) {
       double x[4], U[3], P;
@@ -477,6 +542,20 @@ void net_loss(const Prob& pb, const Nbr& nb, int A, const T* thA, T* out) {
       if (g.face_is_time(f)) ltm += ep * ep; else lsp += ep * ep;
     }
   }
+  if (pb.ghost_mode())
+    for (int64_t i = pb.ghost_off[A]; i < pb.ghost_off[A + 1]; ++i) {
+      double x[4], U[3], P;
+      bool tm;
+      pb.ghost_x(i, x);
+      ghost_target_vol(pb, nb, A, i, U, &P, &tm);
+      forward(g, A, thA, x, false, Zv.data(), Yv.data());
+      for (int c = 0; c < g.ds; ++c) {
+        T e = Yv[c] - U[c];
+        lgu += g.cfg.comp_w[c] * e * e;
+      }
+      T ep = Yv[g.ds] - P;
+      if (tm) ltm += ep * ep; else lsp += ep * ep;
+    }
   out[0] = nobs ? lobs / (double)nobs : T(0.0);
   out[1] = npde ? lpde / (double)npde : T(0.0);
   out[2] = ngh ? lgu / (double)ngh : T(0.0);
@@ -500,9 +579,13 @@ void net_grad(const Prob& pb, const Nbr& nb, int A, const double* thA, double* g
   std::vector<Item> items;
   for (int64_t i = pb.res_off[A]; i < pb.res_off[A + 1]; ++i) items.push_back({0, 0, 0, i});
   for (int64_t i = pb.obs_off[A]; i < pb.obs_off[A + 1]; ++i) items.push_back({1, 0, 0, i});
-  for (auto& fs : g.net_faces[A])
-    for (int64_t i = pb.face_off[fs.first]; i < pb.face_off[fs.first + 1]; ++i)
-      items.push_back({2, fs.first, fs.second, i});
+  if (pb.ghost_mode()) {
+    for (int64_t i = pb.ghost_off[A]; i < pb.ghost_off[A + 1]; ++i) items.push_back({3, 0, 0, i});
+  } else {
+    for (auto& fs : g.net_faces[A])
+      for (int64_t i = pb.face_off[fs.first]; i < pb.face_off[fs.first + 1]; ++i)
+        items.push_back({2, fs.first, fs.second, i});
+  }
   int T = std::max(1, g_threads);
   std::vector<std::vector<double>> gbuf(T, std::vector<double>(g.n_params, 0.0));
   std::vector<std::array<double, 5>> lbuf(T, {0, 0, 0, 0, 0});
@@ -535,9 +618,16 @@ void net_grad(const Prob& pb, const Nbr& nb, int A, const double* thA, double* g
         }
         backward(g, A, thA, x, false, Z.data(), Yb.data(), gbuf[t].data());
       } else {
-        pb.face_x(w.i, x);
         double U[3], P;
-        ghost_target(pb, nb, w.f, w.i, w.side, U, &P);
+        bool tm;
+        if (w.kind == 2) {
+          pb.face_x(w.i, x);
+          ghost_target(pb, nb, w.f, w.i, w.side, U, &P);
+          tm = g.face_is_time(w.f);
+        } else {
+          pb.ghost_x(w.i, x);
+          ghost_target_vol(pb, nb, A, w.i, U, &P, &tm);
+        }
         forward(g, A, thA, x, false, Z.data(), Y.data());
         for (int c = 0; c < g.ds; ++c) {
           double e_ = Y[c] - U[c];
@@ -545,7 +635,6 @@ void net_grad(const Prob& pb, const Nbr& nb, int A, const double* thA, double* g
           Yb[c] = 2.0 * g.cfg.lam_gh_u * g.cfg.comp_w[c] * e_ / (double)ngh;
         }
         double ep = Y[g.ds] - P;
-        bool tm = g.face_is_time(w.f);
         lbuf[t][tm ? 4 : 3] += ep * ep;
         double lam = tm ? g.cfg.lam_gh_p_time : lam_space(g, A);
         Yb[g.ds] = 2.0 * lam * ep / (double)ngh;

@@ -16,7 +16,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdpinn.so")
 
-POINTS_RESIDUAL, POINTS_OBS, POINTS_FACE = 0, 1, 2
+POINTS_RESIDUAL, POINTS_OBS, POINTS_FACE, POINTS_GHOST = 0, 1, 2, 3
 
 ERRORS = {
     -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NONFINITE", -5: "TIMEOUT", -6: "BUSY", -7: "STATE",
@@ -226,7 +226,10 @@ class Dpinn:
         self.set_points(POINTS_RESIDUAL, np.asarray(pb.res_pts, np.float32), pb.res_counts)
         self.set_points(POINTS_OBS, np.asarray(pb.obs_pts, np.float32), pb.obs_counts,
                         np.asarray(pb.obs_vals, np.float32))
-        self.set_points(POINTS_FACE, np.asarray(pb.face_pts, np.float32), pb.face_counts)
+        if getattr(pb, "ghost_counts", None) is not None:
+            self.set_points(POINTS_GHOST, np.asarray(pb.ghost_pts, np.float32), pb.ghost_counts)
+        else:
+            self.set_points(POINTS_FACE, np.asarray(pb.face_pts, np.float32), pb.face_counts)
         if set_params:
             self.set_state(params=pb.theta0, step=0, zero_moments=True)
 

@@ -89,6 +89,11 @@ struct dpinn {
   DevBuf<float> res_pts, obs_pts, obs_vals, face_pts;
   std::vector<int64_t> res_counts, obs_counts, face_counts;
   bool have[3] = {false, false, false};
+  // volumetric ghost layers: directed segments (own net, owner net, is_time)
+  // of the ghost points, grouped by own net then owner
+  bool ghost_mode = false;
+  std::vector<std::array<int, 3>> seg;
+  std::vector<int64_t> seg_counts;
   // plan
   DevBuf<dk::Item> items_eval, items_jet, items_val;
   int n_eval = 0, n_jet = 0, n_val = 0, n_slots = 0;
@@ -294,11 +299,26 @@ int build_plan(dpinn* h) {
   if (!(h->have[0] && h->have[1] && (h->have[2] || h->n_faces == 0)))
     return DPINN_OK;   // built when every point set is present
   if (!h->have[2]) h->face_counts.assign(h->n_faces, 0);
-  const int nn = h->n_nets, nf = h->n_faces;
+  const int nn = h->n_nets;
+  // Interfaces: the geometric faces (shared points, both sides train and
+  // both evaluate) or, with volumetric ghost layers, directed segments (the
+  // own net trains, the owner of the points evaluates).
+  const bool directed = h->ghost_mode;
+  std::vector<std::array<int, 3>> ifc;
+  if (directed) ifc = h->seg;
+  else
+    for (auto& f : h->faces) ifc.push_back({f[0], f[1], (h->unst && f[2] == h->ds) ? 1 : 0});
+  const std::vector<int64_t>& ifc_counts = directed ? h->seg_counts : h->face_counts;
+  const int nf = (int)ifc.size();
+  std::vector<std::vector<std::pair<int, int>>> trains(nn);   // (interface, side) per net
+  for (int f = 0; f < nf; ++f) {
+    trains[ifc[f][0]].push_back({f, 0});
+    if (!directed) trains[ifc[f][1]].push_back({f, 1});
+  }
   std::vector<int64_t> res_off(nn + 1, 0), obs_off(nn + 1, 0), face_off(nf + 1, 0);
   for (int k = 0; k < nn; ++k) res_off[k + 1] = res_off[k] + h->res_counts[k];
   for (int k = 0; k < nn; ++k) obs_off[k + 1] = obs_off[k] + h->obs_counts[k];
-  for (int f = 0; f < nf; ++f) face_off[f + 1] = face_off[f] + h->face_counts[f];
+  for (int f = 0; f < nf; ++f) face_off[f + 1] = face_off[f] + ifc_counts[f];
   const int64_t n_face_pts = face_off[nf];
 
   // chunk sizes: enough items for several waves, multiples of the tile
@@ -325,10 +345,10 @@ int build_plan(dpinn* h) {
       iv.push_back({dk::K_OBS, k, (int)b, (int)c, slot++, 0, 0, 0});
     });
     int64_t ngh = 0;
-    for (int f : h->net_faces[k]) {
-      const int side = (h->faces[f][0] == k) ? 0 : 1;
-      ngh += h->face_counts[f];
-      chunks(face_off[f], h->face_counts[f], cv, [&](int64_t b, int64_t c) {
+    for (auto& fs : trains[k]) {
+      const int f = fs.first, side = fs.second;
+      ngh += ifc_counts[f];
+      chunks(face_off[f], ifc_counts[f], cv, [&](int64_t b, int64_t c) {
         iv.push_back({dk::K_FACE, k, (int)b, (int)c, slot++, f, side, 0});
       });
     }
@@ -349,13 +369,20 @@ int build_plan(dpinn* h) {
   slot_begin[nn] = slot;
   h->n_slots = slot;
   for (int f = 0; f < nf; ++f)
-    for (int side = 0; side < 2; ++side) {
-      const int k = h->faces[f][side];
-      chunks(face_off[f], h->face_counts[f], cv, [&](int64_t b, int64_t c) {
+    for (int side = directed ? 1 : 0; side < 2; ++side) {
+      const int k = ifc[f][side];
+      chunks(face_off[f], ifc_counts[f], cv, [&](int64_t b, int64_t c) {
         ie.push_back({dk::K_EVAL, k, (int)b, (int)c, 0, f, side, 0});
         if (h->master[k]) ie.push_back({dk::K_EVAL_ANC, k, (int)b, (int)c, 0, f, side, 0});
       });
     }
+  {
+    std::vector<int> fi((size_t)std::max(nf, 1) * 3, 0);
+    for (int f = 0; f < nf; ++f)
+      for (int q = 0; q < 3; ++q) fi[(size_t)f * 3 + q] = ifc[f][q];
+    CK(h, h->face_info_d.ensure(fi.size()));
+    CK(h, cudaMemcpy(h->face_info_d.p, fi.data(), fi.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
   // longest chunks first (the scheduler hands items out in this order)
   auto by_count = [](const dk::Item& a, const dk::Item& b) { return a.count > b.count; };
   if (h->sched_order == 0) {
@@ -701,9 +728,73 @@ int dpinn_face_info(dpinn_t* h, int f, int* lo, int* hi, int* axis, int* is_time
   return DPINN_OK;
 }
 
+namespace {
+// Volumetric ghost points: route every point of net A to the net B whose
+// cell holds it (float32 rule), group A's points by B into directed
+// segments (A, B, is_time), and upload them in segment order.
+int set_ghost_points(dpinn* h, const float* pts, const int64_t* counts) {
+  int64_t n = 0;
+  for (int k = 0; k < h->n_nets; ++k) n += counts[k];
+  std::vector<float> hp((size_t)n * h->din);
+  if (n) CK(h, cudaMemcpy(hp.data(), pts, hp.size() * sizeof(float), cudaMemcpyDefault));
+  std::vector<std::array<int, 3>> seg;
+  std::vector<int64_t> seg_counts;
+  std::vector<float> sorted;
+  sorted.reserve(hp.size());
+  int64_t off = 0;
+  for (int A = 0; A < h->n_nets; ++A) {
+    std::vector<std::pair<int, int64_t>> own;   // (owner, point index)
+    for (int64_t i = off; i < off + counts[A]; ++i) {
+      int B = 0;
+      for (int a = 0; a < h->din; ++a) {
+        const int c = cell_fp32(h->cfg, a, hp[(size_t)i * h->din + a]);
+        if (c < 0) return fail(h, DPINN_ERR_INVALID_ARG, "ghost point outside the domain");
+        B += c * h->stride[a];
+      }
+      if (B == A) return fail(h, DPINN_ERR_INVALID_ARG, "ghost point inside its own net's cell");
+      own.push_back({B, i});
+    }
+    off += counts[A];
+    std::stable_sort(own.begin(), own.end(),
+                     [](const std::pair<int, int64_t>& x, const std::pair<int, int64_t>& y) { return x.first < y.first; });
+    for (size_t j = 0; j < own.size(); ++j) {
+      const int B = own[j].first;
+      if (j == 0 || own[j - 1].first != B) {
+        bool same_space = true;
+        for (int a = 0; a < h->ds; ++a) same_space = same_space && h->cell[A][a] == h->cell[B][a];
+        seg.push_back({A, B, (h->unst && same_space) ? 1 : 0});
+        seg_counts.push_back(0);
+      }
+      seg_counts.back() += 1;
+      for (int q = 0; q < h->din; ++q) sorted.push_back(hp[(size_t)own[j].second * h->din + q]);
+    }
+  }
+  CK(h, cudaDeviceSynchronize());
+  CK(h, h->face_pts.ensure((size_t)std::max<int64_t>(n, 1) * h->din));
+  if (n) CK(h, cudaMemcpy(h->face_pts.p, sorted.data(), sorted.size() * sizeof(float), cudaMemcpyHostToDevice));
+  h->seg = seg;
+  h->seg_counts = seg_counts;
+  h->ghost_mode = true;
+  h->have[2] = true;
+  return build_plan(h);
+}
+}  // namespace
+
 int dpinn_set_points(dpinn_t* h, int kind, const float* pts, const float* vals, const int64_t* counts, int n_counts) {
   if (!h) return DPINN_ERR_INVALID_ARG;
-  if (kind < 0 || kind > 2) return fail(h, DPINN_ERR_INVALID_ARG, "bad point kind");
+  if (kind < 0 || kind > 3) return fail(h, DPINN_ERR_INVALID_ARG, "bad point kind");
+  if (kind == DPINN_POINTS_GHOST) {
+    if (n_counts != h->n_nets || !counts) return fail(h, DPINN_ERR_INVALID_ARG, "counts length mismatch");
+    int64_t n = 0;
+    for (int i = 0; i < n_counts; ++i) {
+      if (counts[i] < 0) return fail(h, DPINN_ERR_INVALID_ARG, "negative count");
+      n += counts[i];
+    }
+    if (n > (int64_t)1 << 30) return fail(h, DPINN_ERR_INVALID_ARG, "too many points");
+    if (n > 0 && !pts) return fail(h, DPINN_ERR_INVALID_ARG, "null points");
+    CK(h, cudaSetDevice(h->dev));
+    return set_ghost_points(h, pts, counts);
+  }
   const int expect = kind == DPINN_POINTS_FACE ? h->n_faces : h->n_nets;
   if (n_counts != expect || (!counts && expect > 0)) return fail(h, DPINN_ERR_INVALID_ARG, "counts length mismatch");
   int64_t n = 0;
@@ -731,6 +822,10 @@ int dpinn_set_points(dpinn_t* h, int kind, const float* pts, const float* vals, 
   }
   *dst = cv;
   h->have[kind] = true;
+  if (kind == DPINN_POINTS_FACE && h->ghost_mode) {
+    h->ghost_mode = false;
+    return build_plan(h);
+  }
   if (same && h->plan_ok) return DPINN_OK;
   return build_plan(h);
 }

@@ -283,6 +283,8 @@ class Problem:
     theta0: np.ndarray
     seed: int = 0
     extra: dict = field(default_factory=dict)
+    ghost_pts: np.ndarray | None = None
+    ghost_counts: np.ndarray | None = None
 
     @property
     def n_res(self) -> int:
@@ -341,6 +343,63 @@ def make_problem(cfg, seed=0, res_counts=None, n_obs=None, n_face=None,
         face_pts=cat(fpts, di), face_counts=face_counts,
         theta0=init_params(cfg, seed, bias_std), seed=seed,
     )
+
+
+def cell_fp32(cfg, a, x):
+    """Cell index of coordinate(s) x along axis a with the float32 rule of the
+    interface (floor((x - lo) * (splits / (hi - lo))), clamped); -1 outside."""
+    x = np.asarray(x, np.float32)
+    lo, hi = np.float32(cfg["lo"][a]), np.float32(cfg["hi"][a])
+    inv_h = np.float32(cfg["splits"][a] / (cfg["hi"][a] - cfg["lo"][a]))
+    q = np.float32(np.float32(x - lo) * inv_h)
+    c = np.clip(np.floor(q).astype(np.int64), 0, cfg["splits"][a] - 1)
+    return np.where((x >= lo) & (x <= hi), c, -1)
+
+
+def owner_net(cfg, pts):
+    """Net whose cell holds each float32 point (-1 outside the domain)."""
+    pts = np.asarray(pts, np.float32)
+    net = np.zeros(len(pts), np.int64)
+    bad = np.zeros(len(pts), bool)
+    for a, st in enumerate(strides(cfg)):
+        c = cell_fp32(cfg, a, pts[:, a])
+        bad |= c < 0
+        net += np.maximum(c, 0) * st
+    return np.where(bad, -1, net)
+
+
+def ghost_points(cfg, n_per_net, delta_space, delta_time=None, seed=0):
+    """Volumetric ghost sets: for each net, points uniform in its cell grown by
+    delta_space (spatial axes) / delta_time (time axis), clipped to the domain,
+    outside the net's own cell (float32 ownership).  Returns (pts, counts)."""
+    di, ds = d_in(cfg), cfg["d_space"]
+    delta_time = delta_space if delta_time is None else delta_time
+    g = _rng(seed, 9)
+    out, counts = [], []
+    for k in range(n_nets(cfg)):
+        lo, hi = net_box(cfg, k)
+        d = np.array([delta_space if a < ds else delta_time for a in range(di)])
+        glo = np.maximum(lo - d, np.array(cfg["lo"][:di], np.float64))
+        ghi = np.minimum(hi + d, np.array(cfg["hi"][:di], np.float64))
+        got = np.zeros((0, di), np.float32)
+        tries = 0
+        while len(got) < n_per_net and tries < 1000:
+            cand = _uniform_in_box(g, glo, ghi, 4 * n_per_net + 16).astype(np.float32)
+            own = owner_net(cfg, cand)
+            cand = cand[(own != k) & (own >= 0)]
+            got = np.concatenate([got, cand])[:n_per_net]
+            tries += 1
+        out.append(got)
+        counts.append(len(got))
+    pts = np.concatenate(out) if out else np.zeros((0, di), np.float32)
+    return pts.astype(np.float32), np.asarray(counts, np.int64)
+
+
+def with_ghost_layers(pb: Problem, n_per_net, delta_space, delta_time=None, seed=0) -> Problem:
+    """The same problem with volumetric ghost sets instead of face points."""
+    gp, gc = ghost_points(pb.cfg, n_per_net, delta_space, delta_time, seed)
+    pb.ghost_pts, pb.ghost_counts = gp, gc
+    return pb
 
 
 def query_points(cfg, n, seed=0, margin=0.0):

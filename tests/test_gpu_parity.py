@@ -70,6 +70,10 @@ def small_case(name):
     elif name == "unsteady2d_w128_deep":
         cfg = synth.config("tgv", width=128, depth=3, splits=[1, 2, 3, 1], anchor=[3.0, 1.0, 0.0])
         res, obs, face = (90, 30), (20, 8), (20, 8)
+    elif name in ("tgv_ghost", "beltrami_ghost"):
+        cfg, pb = small_case(name[:-6] if name.startswith("tgv") else "beltrami32")
+        d = (0.4, 0.2) if name.startswith("tgv") else (0.3, 0.15)
+        return cfg, synth.with_ghost_layers(pb, 70, delta_space=d[0], delta_time=d[1], seed=5)
     else:
         raise ValueError(name)
     cfg["lambda_gh_p_space"] = 0.7
@@ -86,7 +90,7 @@ def small_case(name):
 
 
 CASES = ["kovasznay", "tgv", "beltrami32", "beltrami128", "steady3d_w64", "unsteady3d_w32",
-         "unsteady3d_w64", "unsteady2d_w128_deep", "tgv_sin", "beltrami_sin"]
+         "unsteady3d_w64", "unsteady2d_w128_deep", "tgv_sin", "beltrami_sin", "tgv_ghost", "beltrami_ghost"]
 
 
 def compare_losses(gpu, ref, tol=LOSS_TOL):
@@ -285,3 +289,27 @@ def test_comm_interval_and_lr_decay_trajectory(interval):
     gth, _, _, gt = d.get_state()
     assert gt == 6
     assert rel_l2(gth, th) < 1e-4
+
+
+def test_ghost_layers_then_back_to_faces():
+    """Delivering face points after ghost points switches back to the face
+    interfaces: the result equals a handle that only ever had face points."""
+    Dpinn = _gpu()
+    from paper_2602_15883_b300.binding import POINTS_FACE
+    cfg, pb = small_case("tgv_ghost")
+    d = Dpinn(cfg)
+    d.set_problem(pb)
+    d.eval_grad()
+    lg = d.loss()
+    ora = oracle.Oracle(cfg, pb)
+    og, oloss = ora.grad(np.asarray(pb.theta0, np.float64))
+    compare_losses(lg, oloss)
+    d.set_points(POINTS_FACE, np.asarray(pb.face_pts, np.float32), pb.face_counts)
+    d.eval_grad()
+    lf, gf = d.loss(), d.grad()
+    cfg2, pb2 = small_case("tgv")
+    e = Dpinn(cfg2)
+    e.set_problem(pb2)
+    e.eval_grad()
+    np.testing.assert_array_equal(lf, e.loss())
+    np.testing.assert_array_equal(gf, e.grad())
