@@ -14,7 +14,7 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libdpinn.so")
+LIB_PATH = os.environ.get("DPINN_LIB", os.path.join(HERE, "libdpinn.so"))
 
 POINTS_RESIDUAL, POINTS_OBS, POINTS_FACE, POINTS_GHOST = 0, 1, 2, 3
 

@@ -340,6 +340,13 @@ __device__ __forceinline__ void contract(float (&acc)[TM][NCOL], const float* __
   }
 }
 
+// contract() over the k-range [k0, k1) only.
+template <int TM, int NCOL, int VEC, class RowX>
+__device__ __forceinline__ void contract_range(float (&acc)[TM][NCOL], const float* __restrict__ Ws, int ws, int n0,
+                                               const float* __restrict__ Xs, RowX rowx, int col0, int k0, int k1) {
+  contract<TM, NCOL, VEC>(acc, Ws + k0 * ws, ws, n0, Xs, [&](int k) { return rowx(k + k0); }, col0, k1 - k0);
+}
+
 // Deterministic block sum of one float per thread (fixed tree order).
 __device__ __forceinline__ float block_sum(float v, float* red) {
 #pragma unroll
@@ -780,19 +787,22 @@ __global__ void __launch_bounds__(NT, 1)
           act_store(ab, z);
         }
         __syncthreads();
-        {   // dW_l[i][k] += sum_pc Zb_l[i][pc] A_{l-1}[k][pc]
-          // Tile (ig, kg) owns rows ig + NTI a and columns kg + NTI c; its KS
-          // lanes take interleaved float4 chunks of pc and are summed by
-          // shuffles in a fixed order.  With KS > 1 the chunk offset moves
-          // the bank group, so kg is permuted to keep a quarter-warp's
-          // rows 4 groups apart.
-          constexpr int D = T::D, NTI = T::NTI, KS = T::KS;
-          const int ks = t % KS, tile = t / KS;
-          const int kq = tile % NTI;
-          const int kg = (KS > 1 && NTI == 8) ? ((kq & 1) * 4 + (kq >> 1)) : kq;
-          const int ig = tile / NTI;
-          // packed dual FMA: lane .x sums the even, .y the odd pc of a chunk,
-          // so both operands are register pairs of the float4 loads
+        // dW_l[i][k] += sum_pc Zb_l[i][pc] A_{l-1}[k][pc].  Tile (ig, kg) owns
+        // rows ig + NTI a and columns kg + NTI c; its KS lanes take interleaved
+        // float4 chunks of pc.  The lanes' partial tiles are combined by a
+        // shuffle reduce-scatter in a fixed order (lane ks ends with flat
+        // entries [NE ks, NE ks + NE) of the tile), and the read-modify-write of
+        // the entries into the item's gradient slot is software-pipelined into
+        // the next contraction so that its L2 latency overlaps the FMAs.  With
+        // KS > 1 the chunk offset moves the bank group, so kg is permuted to keep
+        // a quarter-warp's rows 4 groups apart.
+        constexpr int D = T::D, NTI = T::NTI, KS = T::KS, NE = D * D / KS;
+        const int ks = t % KS, tile = t / KS;
+        const int kq = tile % NTI;
+        const int kg = (KS > 1 && NTI == 8) ? ((kq & 1) * 4 + (kq >> 1)) : kq;
+        const int ig = tile / NTI;
+        float dwv[NE];
+        {
           float2 acc2[D][D];
 #pragma unroll
           for (int a = 0; a < D; ++a)
@@ -804,6 +814,7 @@ __global__ void __launch_bounds__(NT, 1)
             for (int a = 0; a < D; ++a) zv[a] = *reinterpret_cast<const float4*>(zb + ROW(ig + NTI * a) + pc);
 #pragma unroll
             for (int c = 0; c < D; ++c) av[c] = *reinterpret_cast<const float4*>(ab + ROW(kg + NTI * c) + pc);
+            // packed dual FMA: lane .x sums the even, .y the odd pc of a chunk
 #pragma unroll
             for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -814,32 +825,37 @@ __global__ void __launch_bounds__(NT, 1)
                 acc2[a][c] = s;
               }
           }
-          float acc[D][D];
+          float v[D * D];
 #pragma unroll
           for (int a = 0; a < D; ++a)
 #pragma unroll
-            for (int c = 0; c < D; ++c) acc[a][c] = acc2[a][c].x + acc2[a][c].y;
-          if constexpr (KS > 1) {
+            for (int c = 0; c < D; ++c) v[a * D + c] = acc2[a][c].x + acc2[a][c].y;
+          // reduce-scatter over the KS lanes of the tile: at offset o the
+          // lane keeps the half selected by bit o of ks and adds the partner's
 #pragma unroll
-            for (int o = KS / 2; o > 0; o >>= 1)
+          for (int o = KS / 2, S = D * D; o > 0; o >>= 1, S >>= 1) {
+            const bool hi = (ks & o) != 0;
 #pragma unroll
-              for (int a = 0; a < D; ++a)
-#pragma unroll
-                for (int c = 0; c < D; ++c) acc[a][c] += __shfl_xor_sync(0xffffffffu, acc[a][c], o);
+            for (int i = 0; i < S / 2; ++i) {
+              const float send = hi ? v[i] : v[i + S / 2];
+              const float keep = hi ? v[i + S / 2] : v[i];
+              v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
           }
-          if (ks == 0) {
 #pragma unroll
-            for (int a = 0; a < D; ++a)
-#pragma unroll
-              for (int c = 0; c < D; ++c) grad_rmw(g + sh.woff[l] + (ig + NTI * a) * W + kg + NTI * c, acc[a][c], first);
-          }
-          for (int e = t; e < W; e += NT) {
-            float s = 0.f;
-            for (int p = 0; p < P; ++p) s += zb[ROW(e) + p * C];
-            grad_rmw(g + sh.boff[l] + e, s, first);
-          }
+          for (int i = 0; i < NE; ++i) dwv[i] = v[i];
         }
-        // A_{l-1} adjoint = W_l^T Zb_l
+        for (int e = t; e < W; e += NT) {
+          float s = 0.f;
+          for (int p = 0; p < P; ++p) s += zb[ROW(e) + p * C];
+          grad_rmw(g + sh.boff[l] + e, s, first);
+        }
+        float* const gw = g + sh.woff[l];
+        const auto waddr = [&](int i) {
+          const int e = NE * ks + i;
+          return gw + (ig + NTI * (e / D)) * W + kg + NTI * (e % D);
+        };
+        // A_{l-1} adjoint = W_l^T Zb_l, with the pipelined dW read-modify-write
         mbar_wait(&mbar, phase & 1, b.err);
         ++phase;
         float a[TM][NCOL];
@@ -847,7 +863,33 @@ __global__ void __launch_bounds__(NT, 1)
         for (int m = 0; m < TM; ++m)
 #pragma unroll
           for (int j = 0; j < NCOL; ++j) a[m][j] = 0.f;
-        contract<TM, NCOL, VEC>(a, wbuf, W, n0, zb, ROW, col0, W);
+        {
+          constexpr int NCH = 8, NEH = (NE + NCH - 1) / NCH;
+          float ld[NEH];
+#pragma unroll
+          for (int ch = 0; ch < NCH; ++ch) {
+            contract_range<TM, NCOL, VEC>(a, wbuf, W, n0, zb, ROW, col0, ch * (W / NCH), (ch + 1) * (W / NCH));
+            if (ch > 0) {
+#pragma unroll
+              for (int q = 0; q < NEH; ++q) {
+                const int i = (ch - 1) * NEH + q;
+                if (i < NE) *waddr(i) = first ? dwv[i] : ld[q] + dwv[i];
+              }
+            }
+            if (!first) {
+#pragma unroll
+              for (int q = 0; q < NEH; ++q) {
+                const int i = ch * NEH + q;
+                if (i < NE) ld[q] = *waddr(i);
+              }
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < NEH; ++q) {
+            const int i = (NCH - 1) * NEH + q;
+            if (i < NE) *waddr(i) = first ? dwv[i] : ld[q] + dwv[i];
+          }
+        }
         __syncthreads();
         if (t == 0 && l - 1 >= 1) bulk_load(wbuf, th + sh.woff[l - 1], W * W * 4, &mbar);
         float z[TM][NCOL];
