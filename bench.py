@@ -239,6 +239,7 @@ def main():
     ap.add_argument("--no-baselines", action="store_true", help="skip the plain-form and CPU legs")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     ap.add_argument("--serving-seconds", type=float, default=5.0)
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -262,6 +263,13 @@ def main():
     d = Dpinn(cfg)
     d.set_problem(pb)
     stream = torch.cuda.current_stream()
+    schedule = {"jet_tiles": 0, "val_tiles": 0, "order": 0, "tuned": False}
+    if not args.no_autotune:
+        from paper_2602_15883_b300 import autotune
+        n_val = int(pb.obs_counts.sum() + 2 * pb.face_counts.sum())
+        res = autotune.autotune(d, pb.n_res, n_val, reps=3)
+        schedule = {k: res[k] for k in ("jet_tiles", "val_tiles", "order")}
+        schedule.update(tuned=True, cached=res.get("cached", False), tile_points=d.get_schedule()["tile_points"])
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     d.step(args.warmup, stream)
     d.loss()
@@ -344,7 +352,7 @@ def main():
                            "depth": cfg["depth"], "residual_points": pb.n_res,
                            "obs_points": int(pb.obs_counts.sum()), "face_points": int(pb.face_counts.sum()),
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                           "l2": "flushed between steps (512 MiB write)"},
+                           "l2": "flushed between steps (512 MiB write)", "schedule": schedule},
                 "roofline": roofline, "clocks": clocks, "e2e": e2e,
                 "gpu_launches": d.launches_per_step * args.steps,
                 "step_gflop": step_flops(cfg, pb) / 1e9}
