@@ -130,6 +130,15 @@ def fp32_alu_peak_tflops(sm_mhz):
     return 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
+PRECISIONS = {"fp32": 0, "tf32x3": 1}
+
+
+def tf32_tensor_peak_tflops(pk):
+    # dense TF32 from the measured dense bf16 (cuBLAS) burst figure and the
+    # nominal B300 ratio (1.1 / 2.25 PFLOP/s)
+    return float(pk.get("bf16_tflops", 1800.0)) * 1.1 / 2.25
+
+
 def make_problem(args, rank=0):
     cfg = synth.config(args.workload)
     pb = synth.make_problem(cfg, seed=args.seed + rank)
@@ -240,6 +249,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     ap.add_argument("--serving-seconds", type=float, default=5.0)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3"],
+                    help="hidden-layer contractions of the jet kernel: FP32 FMA, or tcgen05 3xTF32 (width 128)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -260,6 +271,7 @@ def main():
 
     cfg, pb = make_problem(args, rank)
     cfg["device"] = local
+    cfg["precision"] = PRECISIONS[args.precision]
     d = Dpinn(cfg)
     d.set_problem(pb)
     stream = torch.cuda.current_stream()
@@ -314,13 +326,23 @@ def main():
     clocks = clk.summary()
     pk, pk_kind = peaks()
     sm_mhz = float(pk.get("sm_max_mhz", 2032.0))
-    peak = fp32_alu_peak_tflops(sm_mhz)
     jet_flops = flops_per_point(cfg, True) * pb.n_res
     achieved = jet_flops / (jet_ms / 1e3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_pinn train (jets)",
-                "peak_source": f"148 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (max SM clock, {pk_kind})",
-                "kernel_ms": kms}
+    if args.precision == "fp32":
+        peak = fp32_alu_peak_tflops(sm_mhz)
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None, "kernel": "k_pinn train (jets)",
+                    "peak_source": f"148 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (max SM clock, {pk_kind})",
+                    "kernel_ms": kms}
+    else:
+        peak = tf32_tensor_peak_tflops(pk)
+        hidden = 3 * 2 * (synth.d_in(cfg) + 2) * cfg["width"] ** 2 * (cfg["depth"] - 1) * pb.n_res
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None, "kernel": "k_pinn_tc train (jets, tcgen05 3xTF32)",
+                    "peak_source": f"dense TF32 = measured bf16 burst x 1.1/2.25 (nominal ratio, {pk_kind})",
+                    "hw_tflops_3x": 3 * hidden / (jet_ms / 1e3) / 1e12,
+                    "note": "achieved counts every product once; the tensor cores execute three per product",
+                    "kernel_ms": kms}
 
     # ---- end to end through the C ABI with host buffers
     pinned = torch.from_numpy(np.ascontiguousarray(pb.res_pts, np.float32)).pin_memory()
@@ -347,9 +369,10 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "residual-points/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "tf32x3",
+                "data": "synthetic",
                 "config": {"workload": args.workload, "n_nets": d.n_nets, "width": cfg["width"],
-                           "depth": cfg["depth"], "residual_points": pb.n_res,
+                           "depth": cfg["depth"], "residual_points": pb.n_res, "precision": args.precision,
                            "obs_points": int(pb.obs_counts.sum()), "face_points": int(pb.face_counts.sum()),
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "l2": "flushed between steps (512 MiB write)", "schedule": schedule},

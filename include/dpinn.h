@@ -85,7 +85,15 @@ enum { DPINN_POINTS_RESIDUAL = 0, DPINN_POINTS_OBS = 1, DPINN_POINTS_FACE = 2, D
 /* Hidden-layer activation: tanh, or sin (the paper's cylinder cases,
  * Table B1). */
 enum { DPINN_ACT_TANH = 0, DPINN_ACT_SIN = 1 };
-enum { DPINN_PREC_FP32 = 0 };
+/* Arithmetic of the hidden-layer contractions of the jet training kernel.
+ * FP32: FP32 FMA throughout.  TF32X3 (width 128 only): the three W x W
+ * contractions per layer (forward, input adjoint, weight gradient) run on the
+ * tcgen05 tensor cores with every FP32 operand split into two TF32 parts and
+ * the products accumulated as hi*lo + lo*hi + hi*hi in FP32 (relative error
+ * per product ~2^-21, FP32-grade); everything else stays FP32.  Value
+ * kernels (observations, ghost terms, messages) and queries are FP32 in both
+ * modes.  The paper (Sec. 3) trains in FP32 and fixes no kernel arithmetic. */
+enum { DPINN_PREC_FP32 = 0, DPINN_PREC_TF32X3 = 1 };
 
 typedef struct dpinn_config {
   int d_space;            /* 2 or 3 */
@@ -105,7 +113,7 @@ typedef struct dpinn_config {
   double lr, beta1, beta2, eps;
   double clip_norm;       /* per-net gradient-norm clip, 0 = off */
   uint64_t seed;          /* Xavier-normal initialisation seed */
-  int precision;          /* DPINN_PREC_FP32 */
+  int precision;          /* DPINN_PREC_FP32 or DPINN_PREC_TF32X3 */
   int device;             /* CUDA device ordinal */
   /* Step decay of the learning rate (Table B1 "LR factor & interval"): the
    * update of step t (t = 1, 2, ...) uses lr * factor^floor((t-1)/interval);

@@ -224,8 +224,9 @@ cudaError_t enqueue_step(dpinn* h, int mode, cudaStream_t s, int* n_launch, cuda
   if (e == cudaSuccess && h->n_jet) {
     dk::Bufs bb = b;
     bb.counter = h->counters.p + 1;
-    bb.stash_per_cta = h->ks.stash_jet;
-    e = launch_pinn(h->ks.train_jet, h->grid_jet, h->ks.smem_jet, h->shape, bb, h->items_jet.p, h->n_items_d.p + 1, s);
+    bb.stash_per_cta = h->ks.stash_train_jet;
+    e = launch_pinn(h->ks.train_jet_run, h->grid_jet, h->ks.smem_train_jet, h->shape, bb, h->items_jet.p,
+                    h->n_items_d.p + 1, s);
     ++launches;
     mark("train_jet");
   }
@@ -329,7 +330,7 @@ int build_plan(dpinn* h) {
     int64_t c = ((target + P - 1) / P) * P;
     return std::min<int64_t>(std::max<int64_t>(c, P), 64LL * P);
   };
-  const int64_t cj = pick_chunk(res_off[nn], h->ks.P_jet, h->sched_jet);
+  const int64_t cj = pick_chunk(res_off[nn], h->ks.P_train_jet, h->sched_jet);
   const int64_t cv = pick_chunk(obs_off[nn] + 2 * n_face_pts, h->ks.P_val, h->sched_val);
 
   std::vector<dk::Item> ij, iv, ie;
@@ -394,7 +395,7 @@ int build_plan(dpinn* h) {
   h->n_val = (int)iv.size();
   h->n_eval = (int)ie.size();
 
-  const int occ_j = occupancy(h->ks.train_jet, h->ks.smem_jet);
+  const int occ_j = occupancy(h->ks.train_jet_run, h->ks.smem_train_jet);
   const int occ_v = occupancy(h->ks.train_val, h->ks.smem_val);
   h->grid_jet = (int)std::min<int64_t>(h->n_jet, (int64_t)h->n_sms * occ_j);
   h->grid_val = (int)std::min<int64_t>(h->n_val, (int64_t)h->n_sms * occ_v);
@@ -414,7 +415,7 @@ int build_plan(dpinn* h) {
   CK(h, h->grad_part.ensure((size_t)std::max(slot, 1) * h->npp));
   CK(h, h->loss_part.ensure((size_t)std::max(slot, 1) * 5));
   CK(h, cudaMemset(h->loss_part.p, 0, (size_t)std::max(slot, 1) * 5 * sizeof(double)));
-  const size_t st = std::max((size_t)h->grid_jet * h->ks.stash_jet, (size_t)h->grid_val * h->ks.stash_val);
+  const size_t st = std::max((size_t)h->grid_jet * h->ks.stash_train_jet, (size_t)h->grid_val * h->ks.stash_val);
   CK(h, h->stash.ensure(std::max<size_t>(st, 4)));
   CK(h, h->nbr_val.ensure((size_t)std::max<int64_t>(n_face_pts, 1) * 2 * h->dout));
   CK(h, h->nbr_anc.ensure((size_t)std::max<int64_t>(n_face_pts, 1) * 2));
@@ -553,7 +554,10 @@ int dpinn_create(const dpinn_config* cfg, dpinn_t** out) {
   if (c.depth < 1 || c.depth > dk::MAXL) return fail(nullptr, DPINN_ERR_INVALID_ARG, "depth must be in [1, 16]");
   if (c.activation != DPINN_ACT_TANH && c.activation != DPINN_ACT_SIN)
     return fail(nullptr, DPINN_ERR_INVALID_ARG, "activation must be tanh or sin");
-  if (c.precision != DPINN_PREC_FP32) return fail(nullptr, DPINN_ERR_INVALID_ARG, "only FP32 is supported");
+  if (c.precision != DPINN_PREC_FP32 && c.precision != DPINN_PREC_TF32X3)
+    return fail(nullptr, DPINN_ERR_INVALID_ARG, "precision must be FP32 or TF32x3");
+  if (c.precision == DPINN_PREC_TF32X3 && c.width != 128)
+    return fail(nullptr, DPINN_ERR_INVALID_ARG, "TF32x3 tensor-core kernels need width 128");
   if (!(c.nu >= 0)) return fail(nullptr, DPINN_ERR_INVALID_ARG, "nu must be >= 0");
   if (c.comm_interval < 1) return fail(nullptr, DPINN_ERR_INVALID_ARG, "comm_interval must be >= 1");
   if (c.lr_decay_interval < 0 || !(c.lr_decay_factor > 0))
@@ -576,6 +580,17 @@ int dpinn_create(const dpinn_config* cfg, dpinn_t** out) {
   h->n_nets = (int)nn;
   if (!pick_kernels(h->W, h->ds, h->unst, h->L, c.activation, &h->ks))
     return fail(nullptr, DPINN_ERR_INVALID_ARG, "unsupported shape");
+  if (c.precision == DPINN_PREC_TF32X3) {
+    h->ks.train_jet_run = h->ks.train_jet_tc;
+    h->ks.smem_train_jet = h->ks.smem_tc;
+    h->ks.P_train_jet = h->ks.P_tc;
+    h->ks.stash_train_jet = h->ks.stash_tc;
+  } else {
+    h->ks.train_jet_run = h->ks.train_jet;
+    h->ks.smem_train_jet = h->ks.smem_jet;
+    h->ks.P_train_jet = h->ks.P_jet;
+    h->ks.stash_train_jet = h->ks.stash_jet;
+  }
   // decomposition
   int s = 1;
   for (int a = 0; a < din; ++a) { h->stride.push_back(s); s *= c.splits[a]; }
@@ -636,6 +651,9 @@ int dpinn_create(const dpinn_config* cfg, dpinn_t** out) {
   CK(hp, cudaDeviceGetAttribute(&h->n_sms, cudaDevAttrMultiProcessorCount, c.device));
   for (const void* fn : {h->ks.train_jet, h->ks.query_jet})
     CK(hp, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ks.smem_jet));
+  if (h->ks.train_jet_run != h->ks.train_jet)
+    CK(hp, cudaFuncSetAttribute(h->ks.train_jet_run, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)h->ks.smem_train_jet));
   for (const void* fn : {h->ks.train_val, h->ks.eval_val, h->ks.query_val})
     CK(hp, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ks.smem_val));
   const size_t NP = (size_t)h->n_nets * h->npp;
@@ -886,7 +904,7 @@ int dpinn_get_schedule(dpinn_t* h, int* jet_tiles, int* val_tiles, int* order, i
   if (jet_tiles) *jet_tiles = h->sched_jet;
   if (val_tiles) *val_tiles = h->sched_val;
   if (order) *order = h->sched_order;
-  if (tile_points) { tile_points[0] = h->ks.P_jet; tile_points[1] = h->ks.P_val; }
+  if (tile_points) { tile_points[0] = h->ks.P_train_jet; tile_points[1] = h->ks.P_val; }
   return DPINN_OK;
 }
 

@@ -15,6 +15,17 @@ struct KernelSet {
   size_t smem_jet = 0, smem_val = 0;
   int P_jet = 0, P_val = 0;
   long long stash_jet = 0, stash_val = 0;   // floats per CTA
+  // the jet training kernel actually launched (the FP32 one above, or the
+  // tensor-core one below), its shared memory, tile and stash
+  const void* train_jet_run = nullptr;
+  size_t smem_train_jet = 0;
+  int P_train_jet = 0;
+  long long stash_train_jet = 0;
+  // tensor-core (tcgen05, 3xTF32) jet training kernel, width 128 only
+  const void* train_jet_tc = nullptr;
+  size_t smem_tc = 0;
+  int P_tc = 0;
+  long long stash_tc = 0;
 };
 
 // Fill *k for (d_space, unsteady, depth); false if the shape is unsupported.

@@ -1,6 +1,7 @@
 // Instantiates the grouped kernels for width 128 with the sin activation.
 #include "kernel_set.h"
 #include "pinn_kernels.cuh"
+#include "pinn_tc.cuh"
 
 namespace dk {
 namespace {
@@ -20,6 +21,10 @@ KernelSet make_set(int L) {
   k.P_val = Tile<W, 1>::P;
   k.stash_jet = (long long)L * Tile<W, CJ>::NQ * NT * 4;
   k.stash_val = (long long)L * Tile<W, 1>::NQ * NT * 4;
+  k.train_jet_tc = (const void*)k_pinn_tc<DS, UNST, ACT>;
+  k.smem_tc = tc_smem_bytes<CJ, DOUT>(L);
+  k.P_tc = TcTile<CJ>::P;
+  k.stash_tc = tc_stash_floats<CJ>(L);
   return k;
 }
 

@@ -367,6 +367,50 @@ __device__ __forceinline__ void grad_rmw(float* g, float v, bool first) {
   *g = first ? v : (*g + v);
 }
 
+// Navier-Stokes residuals of one point from its output jets Y[j][c]
+// (c = value, d/dx_q for every input, spatial Laplacian; j = velocity
+// components then pressure), Eqs. (7)-(10):
+//   r_j = [d_t u_j] + sum_i u_i d_i u_j + d_j p - nu lap u_j,  r_DS = div u.
+// Returns sum_j r_j^2 and adds into Yb the jet adjoints of (sc / 2) sum_j r_j^2
+// (residual adjoints rb_j = sc r_j pushed through Eqs. (7)-(10)).
+template <int DS, int UNST, int C>
+__device__ __forceinline__ float pde_seed(const float (&Y)[DS + 1][C], float nu, float sc, float (&Yb)[DS + 1][C]) {
+  float r[DS + 1];
+#pragma unroll
+  for (int j = 0; j < DS; ++j) {
+    float v = UNST ? Y[j][1 + DS] : 0.f;
+#pragma unroll
+    for (int i = 0; i < DS; ++i) v = fmaf(Y[i][0], Y[j][1 + i], v);
+    v += Y[DS][1 + j];
+    v = fmaf(-nu, Y[j][C - 1], v);
+    r[j] = v;
+  }
+  float dv = 0.f;
+#pragma unroll
+  for (int i = 0; i < DS; ++i) dv += Y[i][1 + i];
+  r[DS] = dv;
+  float r2 = 0.f;
+#pragma unroll
+  for (int j = 0; j <= DS; ++j) r2 = fmaf(r[j], r[j], r2);
+  float rb[DS + 1];
+#pragma unroll
+  for (int j = 0; j <= DS; ++j) rb[j] = sc * r[j];
+#pragma unroll
+  for (int j = 0; j < DS; ++j) {
+    if (UNST) Yb[j][1 + DS] += rb[j];
+#pragma unroll
+    for (int i = 0; i < DS; ++i) {
+      Yb[i][0] = fmaf(rb[j], Y[j][1 + i], Yb[i][0]);
+      Yb[j][1 + i] = fmaf(rb[j], Y[i][0], Yb[j][1 + i]);
+    }
+    Yb[DS][1 + j] += rb[j];
+    Yb[j][C - 1] = fmaf(-nu, rb[j], Yb[j][C - 1]);
+  }
+#pragma unroll
+  for (int i = 0; i < DS; ++i) Yb[i][1 + i] += rb[DS];
+  return r2;
+}
+
 // ------------------------------------------------------ the kernel ---
 template <int W, int DS, int UNST, bool JETS, int MODE, int ACT>
 __global__ void __launch_bounds__(NT, 1)
@@ -610,41 +654,7 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
               for (int c = 0; c < C; ++c) Yb[j][c] = 0.f;
             if constexpr (JETS) {
-              // residuals, Eqs. (7)-(10): r_j = [d_t u_j] + u_i d_i u_j + d_j p - nu lap u_j
-              float r[DS + 1];
-#pragma unroll
-              for (int j = 0; j < DS; ++j) {
-                float v = UNST ? Y[j][1 + DS] : 0.f;
-#pragma unroll
-                for (int i = 0; i < DS; ++i) v = fmaf(Y[i][0], Y[j][1 + i], v);
-                v += Y[DS][1 + j];
-                v = fmaf(-sh.nu, Y[j][C - 1], v);
-                r[j] = v;
-              }
-              float dv = 0.f;
-#pragma unroll
-              for (int i = 0; i < DS; ++i) dv += Y[i][1 + i];
-              r[DS] = dv;
-              float r2 = 0.f;
-#pragma unroll
-              for (int j = 0; j <= DS; ++j) r2 = fmaf(r[j], r[j], r2);
-              const float sc = valid ? 2.f * sh.lam_pde * ni.inv_npde : 0.f;
-              float rb[DS + 1];
-#pragma unroll
-              for (int j = 0; j <= DS; ++j) rb[j] = sc * r[j];
-#pragma unroll
-              for (int j = 0; j < DS; ++j) {
-                if (UNST) Yb[j][1 + DS] += rb[j];
-#pragma unroll
-                for (int i = 0; i < DS; ++i) {
-                  Yb[i][0] = fmaf(rb[j], Y[j][1 + i], Yb[i][0]);
-                  Yb[j][1 + i] = fmaf(rb[j], Y[i][0], Yb[j][1 + i]);
-                }
-                Yb[DS][1 + j] += rb[j];
-                Yb[j][C - 1] = fmaf(-sh.nu, rb[j], Yb[j][C - 1]);
-              }
-#pragma unroll
-              for (int i = 0; i < DS; ++i) Yb[i][1 + i] += rb[DS];
+              const float r2 = pde_seed<DS, UNST, C>(Y, sh.nu, valid ? 2.f * sh.lam_pde * ni.inv_npde : 0.f, Yb);
               l0 = valid ? r2 : 0.f;
             } else if (item.kind == K_OBS) {
               float e[DS];

@@ -42,7 +42,8 @@ def test_config_default_is_host_only(lib):
     assert c.width == 32 and c.depth == 4 and list(c.splits) == [1, 1, 1, 1]
 
 
-@pytest.mark.parametrize("field,value", [("width", 48), ("depth", 0), ("d_space", 4), ("activation", 2)])
+@pytest.mark.parametrize("field,value", [("width", 48), ("depth", 0), ("d_space", 4), ("activation", 2),
+                                         ("precision", 2), ("precision", 1)])
 def test_create_rejects_bad_configs_before_touching_a_device(lib, field, value):
     c = binding.Config()
     lib.dpinn_config_default(C.addressof(c))
@@ -51,6 +52,16 @@ def test_create_rejects_bad_configs_before_touching_a_device(lib, field, value):
     rc = lib.dpinn_create(C.addressof(c), C.addressof(h))
     assert rc == -1 and not h.value
     assert lib.dpinn_last_error(None)
+
+
+def test_tf32x3_needs_width_128(lib):
+    c = binding.Config()
+    lib.dpinn_config_default(C.addressof(c))
+    c.precision = 1
+    c.width = 64
+    h = C.c_void_p()
+    assert lib.dpinn_create(C.addressof(c), C.addressof(h)) == -1
+    assert b"width 128" in lib.dpinn_last_error(None)
 
 
 def test_create_rejects_anchor_outside_domain(lib):

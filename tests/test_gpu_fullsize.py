@@ -23,13 +23,15 @@ def _threads():
     oracle.set_threads(1)
 
 
-@pytest.mark.parametrize("name", ["tgv", "beltrami32", "beltrami128"])
-def test_full_size_sampled_nets(name):
+@pytest.mark.parametrize("name,precision", [("tgv", 0), ("beltrami32", 0), ("beltrami128", 0),
+                                            ("beltrami32", 1), ("beltrami128", 1)])
+def test_full_size_sampled_nets(name, precision):
+    """precision 1 = the tensor-core (3xTF32) jet kernel."""
     Dpinn = _gpu()
     import torch
     cfg = synth.config(name)
     pb = synth.make_problem(cfg, seed=0)
-    d = Dpinn(cfg)
+    d = Dpinn(dict(cfg, precision=precision))
     d.set_problem(pb)
     d.eval_grad()
     loss, g = d.loss(), d.grad()
