@@ -174,14 +174,14 @@ dk::Bufs make_bufs(dpinn* h) {
 }
 
 cudaError_t launch_pinn(const void* fn, int grid, size_t smem, const dk::Shape& sh, const dk::Bufs& b,
-                        const dk::Item* items, const int* n_items, cudaStream_t s) {
+                        const dk::Item* items, const int* n_items, cudaStream_t s, int threads = dk::NT) {
   void* args[] = {(void*)&sh, (void*)&b, (void*)&items, (void*)&n_items};
-  return cudaLaunchKernel(fn, dim3(grid), dim3(dk::NT), args, smem, s);
+  return cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, smem, s);
 }
 
-int occupancy(const void* fn, size_t smem) {
+int occupancy(const void* fn, size_t smem, int threads = dk::NT) {
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, dk::NT, smem) != cudaSuccess) return 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess) return 1;
   return std::max(occ, 1);
 }
 
@@ -226,7 +226,7 @@ cudaError_t enqueue_step(dpinn* h, int mode, cudaStream_t s, int* n_launch, cuda
     bb.counter = h->counters.p + 1;
     bb.stash_per_cta = h->ks.stash_train_jet;
     e = launch_pinn(h->ks.train_jet_run, h->grid_jet, h->ks.smem_train_jet, h->shape, bb, h->items_jet.p,
-                    h->n_items_d.p + 1, s);
+                    h->n_items_d.p + 1, s, h->ks.threads_train_jet);
     ++launches;
     mark("train_jet");
   }
@@ -395,7 +395,7 @@ int build_plan(dpinn* h) {
   h->n_val = (int)iv.size();
   h->n_eval = (int)ie.size();
 
-  const int occ_j = occupancy(h->ks.train_jet_run, h->ks.smem_train_jet);
+  const int occ_j = occupancy(h->ks.train_jet_run, h->ks.smem_train_jet, h->ks.threads_train_jet);
   const int occ_v = occupancy(h->ks.train_val, h->ks.smem_val);
   h->grid_jet = (int)std::min<int64_t>(h->n_jet, (int64_t)h->n_sms * occ_j);
   h->grid_val = (int)std::min<int64_t>(h->n_val, (int64_t)h->n_sms * occ_v);
@@ -582,11 +582,13 @@ int dpinn_create(const dpinn_config* cfg, dpinn_t** out) {
     return fail(nullptr, DPINN_ERR_INVALID_ARG, "unsupported shape");
   if (c.precision == DPINN_PREC_TF32X3) {
     h->ks.train_jet_run = h->ks.train_jet_tc;
+    h->ks.threads_train_jet = h->ks.threads_tc;
     h->ks.smem_train_jet = h->ks.smem_tc;
     h->ks.P_train_jet = h->ks.P_tc;
     h->ks.stash_train_jet = h->ks.stash_tc;
   } else {
     h->ks.train_jet_run = h->ks.train_jet;
+    h->ks.threads_train_jet = dk::NT;
     h->ks.smem_train_jet = h->ks.smem_jet;
     h->ks.P_train_jet = h->ks.P_jet;
     h->ks.stash_train_jet = h->ks.stash_jet;

@@ -18,11 +18,13 @@ struct KernelSet {
   // the jet training kernel actually launched (the FP32 one above, or the
   // tensor-core one below), its shared memory, tile and stash
   const void* train_jet_run = nullptr;
+  int threads_train_jet = 0;
   size_t smem_train_jet = 0;
   int P_train_jet = 0;
   long long stash_train_jet = 0;
   // tensor-core (tcgen05, 3xTF32) jet training kernel, width 128 only
   const void* train_jet_tc = nullptr;
+  int threads_tc = 0;
   size_t smem_tc = 0;
   int P_tc = 0;
   long long stash_tc = 0;

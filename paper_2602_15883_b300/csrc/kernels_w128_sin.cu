@@ -22,6 +22,7 @@ KernelSet make_set(int L) {
   k.stash_jet = (long long)L * Tile<W, CJ>::NQ * NT * 4;
   k.stash_val = (long long)L * Tile<W, 1>::NQ * NT * 4;
   k.train_jet_tc = (const void*)k_pinn_tc<DS, UNST, ACT>;
+  k.threads_tc = NTC;
   k.smem_tc = tc_smem_bytes<CJ, DOUT>(L);
   k.P_tc = TcTile<CJ>::P;
   k.stash_tc = tc_stash_floats<CJ>(L);

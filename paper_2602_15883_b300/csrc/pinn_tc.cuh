@@ -10,21 +10,23 @@
 //   weight grad   dW_l      = zbar_l  a_{l-1}^T   M = 128,         N = 128,          K = 16 C
 //
 // Every FP32 operand x is split into TF32 parts x = hi + lo (+ O(2^-22 |x|))
-// and a product is accumulated as A_hi B_lo + A_lo B_hi + A_hi B_hi in the
-// FP32 tensor-memory accumulator, which keeps the FP32-grade accuracy of the
-// path (the A_lo B_lo term is below FP32 rounding).
+// and a product is accumulated as A_hi B_hi + (A_hi B_lo + A_lo B_hi) in FP32
+// tensor-memory accumulators, which keeps the FP32-grade accuracy of the path
+// (the A_lo B_lo term is below FP32 rounding).
 //
-// Layout.  Thread (warp w, lane) owns neuron 32 (w % 4) + lane - its lane of
-// tensor memory - and the column half w / 4 (points 8 (w / 4) .. + 7 of the
-// tile), so the jet recursion and its adjoint stay thread-local as in the FFMA
-// kernel.  Columns are channel-major (n = c * 16 + p).  Tensor memory (512
-// columns): [0, 256) the A operand in hi / lo halves (W_l, or W_l^T, or
-// zbar_l), [256, 384) and [384, 512) two accumulators: for the M x N
-// products the main sum in the first and the 3xTF32 corrections in the
-// second, for the weight gradient the other way round.  Shared memory: two operand regions in the 128-byte-swizzled
-// K-major layout, [n][neuron] (a_{l-1} forward, zbar_l reverse; a warp's 32
-// neurons fill one 128-byte row, so the stores are conflict-free) and
-// [neuron][n] (a_{l-1} for the weight gradient, one 16-byte chunk per store).
+// Layout.  512 threads; thread (warp w, lane) owns neuron 32 (w % 4) + lane -
+// its lane of tensor memory - and the column quarter w / 4 (points
+// 4 (w / 4) .. + 3 of the tile), so the jet recursion and its adjoint stay
+// thread-local as in the FFMA kernel.  Columns are channel-major
+// (n = c * 16 + p).  Tensor memory (512 columns): [0, 256) the A operand in
+// hi / lo halves (W_l, or W_l^T, or zbar_l), [256, 384) and [384, 512) two
+// accumulators: for the M x N products the main sum in the first and the
+// corrections in the second, for the weight gradient the other way round.
+// Shared memory: two operand regions in the 128-byte-swizzled K-major layout,
+// [n][neuron] (a_{l-1} forward, zbar_l reverse; a warp's 32 neurons fill one
+// 128-byte row, so the stores are conflict-free) and [neuron][n] (a_{l-1} for
+// the weight gradient, one 16-byte chunk per store).  The next weight matrix
+// is staged by a bulk copy into whichever region is idle while an MMA runs.
 // The first affine map and the output layer (d_out rows) stay on FP32 FMA.
 #pragma once
 #include "pinn_kernels.cuh"
@@ -32,11 +34,14 @@
 
 namespace dk {
 
+constexpr int NTC = 512;   // threads of the tensor-core kernel
+
 template <int C>
 struct TcTile {
   static constexpr int W = 128;
   static constexpr int P = 16;                        // points per tile
-  static constexpr int HP = 8;                        // points per column half
+  static constexpr int NQ = NTC / 128;                // column groups (threads per neuron)
+  static constexpr int HP = P / NQ;                   // points per thread
   static constexpr int NC = P * C;                    // columns, n = c * P + p
   static constexpr int KB = (NC + 31) / 32;           // 32-column blocks of [neuron][n]
   static constexpr uint32_t XT = (uint32_t)NC * 512;  // one [NC][128] tile (hi or lo), bytes
@@ -44,22 +49,23 @@ struct TcTile {
   static constexpr uint32_t R1 = 2 * XT;              // [neuron][n] region
   static constexpr uint32_t SMALL = R1 + 2 * ABT;     // small tensors from here
   static constexpr int RSO = NC + 4;                  // row stride of a_{L-1} (FP32, in region R1)
-  static constexpr int SQ = 2 * C;                    // stashed float4 per thread per layer
+  static_assert(HP == 4, "one float4 per channel and thread");
   static_assert(NC % 16 == 0 && NC <= 128, "accumulator columns");
   static_assert((size_t)W * RSO * 4 <= 2 * (size_t)ABT, "a_{L-1} buffer");
+  static_assert((size_t)W * W * 4 <= 2 * (size_t)XT && (size_t)W * W * 4 <= 2 * (size_t)ABT, "weight staging");
 };
 
 template <int C, int DOUT>
 constexpr size_t tc_smem_bytes(int L) {
   using T = TcTile<C>;
   return 1024 + T::SMALL +
-         4 * ((size_t)2 * DOUT * T::NC + T::P * 4 + T::W * 4 + T::W + DOUT * T::W + 4 + 2 * T::W * 8 +
+         4 * ((size_t)2 * DOUT * T::NC + T::P * 4 + T::W * 4 + T::W + DOUT * T::W + 4 + T::NQ * T::W * 8 +
               (size_t)(L > 1 ? L - 1 : 0) * T::W);
 }
 
-// stash floats per CTA
+// stash floats per CTA: per layer and thread C float4 (4 points x C channels)
 template <int C>
-constexpr long long tc_stash_floats(int L) { return (long long)L * TcTile<C>::SQ * NT * 4; }
+constexpr long long tc_stash_floats(int L) { return (long long)L * C * NTC * 4; }
 
 // Bounded wait for phase `parity` of `bar` (about 2 s); false on time-out.
 __device__ __forceinline__ bool mbar_wait_ok(uint64_t* bar, uint32_t parity) {
@@ -97,12 +103,45 @@ __device__ __forceinline__ void mma3(uint32_t d, uint32_t dx, uint32_t a_hi, uin
   }
 }
 
+// Gradient accumulation into the item's slot: the first tile of an item
+// stores, later tiles add with fire-and-forget reductions performed at L2 (no
+// load round trip).  Every address has one owning thread, whose adds reach
+// memory in program order, so the sums are deterministic.  (f32 reductions
+// flush subnormal values, below 1.2e-38, to zero.)
+__device__ __forceinline__ void gacc(float* p, float v, bool first) {
+  if (first) *p = v;
+  else asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ void gacc4(float* p, float4 v, bool first) {
+  if (first) *reinterpret_cast<float4*>(p) = v;
+  else
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+// Deterministic sum over the CTA of one float per thread (fixed order).
+__device__ __forceinline__ float block_sum_tc(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  float s = 0.f;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int w = 0; w < NTC / 32; ++w) s += red[w];
+  }
+  return s;   // valid in thread 0
+}
+
 template <int DS, int UNST, int ACT>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NTC, 1)
     k_pinn_tc(const Shape sh, const Bufs b, const Item* __restrict__ items, const int* __restrict__ n_items_ptr) {
   constexpr int W = 128, DIN = DS + UNST, C = DIN + 2, DOUT = DS + 1;
   using T = TcTile<C>;
-  constexpr int P = T::P, HP = T::HP, NC = T::NC, RSO = T::RSO, SQ = T::SQ;
+  constexpr int P = T::P, HP = T::HP, NQ = T::NQ, NC = T::NC, RSO = T::RSO;
+  constexpr int KQ = W / NQ;   // weight-row columns per thread
   constexpr uint32_t XT = T::XT, ABT = T::ABT;
   constexpr uint32_t IDN = tc::idesc_tf32(128, NC), IDW = tc::idesc_tf32(128, 128);
   constexpr uint32_t TLO = 128, TD = 256, TG = 384, TCOLS = 512;
@@ -122,23 +161,26 @@ __global__ void __launch_bounds__(NT, 1)
   float* const b0s = w0s + W * 4;         // [W]
   float* const wLs = b0s + W;             // [DOUT][W]
   float* const bLs = wLs + DOUT * W;      // [4]
-  float* const xpart = bLs + 4;           // [2][W][8] column-half partial sums
-  float* const bls = xpart + 2 * W * 8;   // [L-1][W]
-  __shared__ __align__(8) uint64_t mbar;
+  float* const xpart = bLs + 4;           // [NQ][W][8] column-group partial sums
+  float* const bls = xpart + NQ * W * 8;  // [L-1][W]
+  __shared__ __align__(8) uint64_t mbar;   // MMA completion
+  __shared__ __align__(8) uint64_t wbar;   // weight staging copies
   __shared__ uint32_t s_tmem;
   __shared__ int s_item, s_abort;
-  __shared__ float s_red[NT / 32];
+  __shared__ float s_red[NTC / 32];
   __shared__ float s_scale[4];
 
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int qd = warp & 3, hf = warp >> 2;
+  const int qd = warp & 3, hq = warp >> 2;
   const int nrn = qd * 32 + lane;                        // the thread's neuron = tensor-memory lane
+  const int p0 = hq * HP;                                // the thread's first point
   const uint32_t lrow = (uint32_t)(qd * 32) << 16;       // lane field of the warp's accesses
   const int L = sh.L;
   const int n_items = *n_items_ptr;
 
   if (t == 0) {
     mbar_init(&mbar, 1);
+    mbar_init(&wbar, 1);
     s_abort = 0;
   }
   if (warp == 0) tc::alloc(&s_tmem, TCOLS);
@@ -146,7 +188,7 @@ __global__ void __launch_bounds__(NT, 1)
   __syncthreads();
   tc::fence_after();
   const uint32_t tm = s_tmem;
-  uint32_t phase = 0;
+  uint32_t phase = 0, wphase = 0;
   float4* const stash = reinterpret_cast<float4*>(b.stash + (size_t)blockIdx.x * b.stash_per_cta);
 
   // MMA issue (one thread) and completion; after a time-out the remaining
@@ -173,23 +215,23 @@ __global__ void __launch_bounds__(NT, 1)
     __syncthreads();
     tc::fence_after();
   };
-  // stash: float4 q = (channel c, points 4 j .. 4 j + 3 of the thread's half), q = 2 c + j
-  auto stash_st4 = [&](int l, int j, const float (&h)[C][4]) {
+  // stash: one float4 per channel c (the thread's 4 points)
+  auto stash_st = [&](int l, const float (&h)[C][HP]) {
 #pragma unroll
     for (int c = 0; c < C; ++c)
-      stash[((size_t)l * SQ + 2 * c + j) * NT + t] = make_float4(h[c][0], h[c][1], h[c][2], h[c][3]);
+      stash[((size_t)l * C + c) * NTC + t] = make_float4(h[c][0], h[c][1], h[c][2], h[c][3]);
   };
-  auto stash_ld4 = [&](int l, int j, float (&h)[C][4]) {
+  auto stash_ld = [&](int l, float (&h)[C][HP]) {
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      const float4 v = stash[((size_t)l * SQ + 2 * c + j) * NT + t];
+      const float4 v = stash[((size_t)l * C + c) * NTC + t];
       h[c][0] = v.x; h[c][1] = v.y; h[c][2] = v.z; h[c][3] = v.w;
     }
   };
-  // activation jets of 4 points from their stashed form
-  auto act4 = [&](const float (&h)[C][4], float (&a)[C][4]) {
+  // activation jets of the thread's points from their stashed form
+  auto act_pts = [&](const float (&h)[C][HP], float (&a)[C][HP]) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < HP; ++u) {
       float hz[C], av[C];
 #pragma unroll
       for (int c = 0; c < C; ++c) hz[c] = h[c][u];
@@ -198,21 +240,21 @@ __global__ void __launch_bounds__(NT, 1)
       for (int c = 0; c < C; ++c) a[c][u] = av[c];
     }
   };
-  // value of point pp (of the thread's half), channel c, neuron nrn -> [n][neuron]
-  // operand (hi, lo): row n = c P + 8 hf + pp (n % 8 = pp), column nrn
-  auto put_row = [&](int c, int pp, float v) {
-    const int n = c * P + hf * HP + pp;
-    const uint32_t off = (uint32_t)qd * (NC * 128) + (uint32_t)(n >> 3) * 1024 + (uint32_t)pp * 128 +
-                         ((uint32_t)((lane >> 2) ^ pp) << 4) + (uint32_t)(lane & 3) * 4;
+  // value of the thread's point u, channel c, neuron nrn -> [n][neuron]
+  // operand (hi, lo): row n = c P + p0 + u, column nrn
+  auto put_row = [&](int c, int u, float v) {
+    const int n = c * P + p0 + u;
+    const uint32_t off = (uint32_t)qd * (NC * 128) + (uint32_t)(n >> 3) * 1024 + (uint32_t)(n & 7) * 128 +
+                         ((uint32_t)((lane >> 2) ^ (n & 7)) << 4) + (uint32_t)(lane & 3) * 4;
     float hi, lo;
     tc::split_tf32(v, hi, lo);
     *reinterpret_cast<float*>(gX + off) = hi;
     *reinterpret_cast<float*>(gXl + off) = lo;
   };
-  // 4 points (group j) of channel c -> [neuron][n] operand (hi, lo): row nrn,
-  // columns n = c P + 8 hf + 4 j .. + 3 (one 16-byte chunk)
-  auto put_col4 = [&](int c, int j, const float (&v)[4]) {
-    const int chunk = (c & 1) * 4 + hf * 2 + j;
+  // the thread's 4 points of channel c -> [neuron][n] operand (hi, lo): row
+  // nrn, columns n = c P + p0 .. + 3 (one 16-byte chunk)
+  auto put_col4 = [&](int c, const float (&v)[HP]) {
+    const int chunk = (c & 1) * 4 + hq;
     const uint32_t off = (uint32_t)(c >> 1) * 16384 + (uint32_t)(nrn >> 3) * 1024 + (uint32_t)(nrn & 7) * 128 +
                          ((uint32_t)(chunk ^ (nrn & 7)) << 4);
     float4 h4, l4;
@@ -223,35 +265,55 @@ __global__ void __launch_bounds__(NT, 1)
     *reinterpret_cast<float4*>(gA + off) = h4;
     *reinterpret_cast<float4*>(gAl + off) = l4;
   };
-  // 64 columns (the thread's half) of row nrn of a W x W matrix -> tensor memory hi / lo
+  // KQ columns (the thread's quarter) of row nrn of a W x W matrix -> tensor
+  // memory hi / lo, from global memory ...
   auto put_w = [&](const float* row) {
+    float hi[KQ], lo[KQ];
 #pragma unroll
-    for (int h2 = 0; h2 < 2; ++h2) {
-      float hi[32], lo[32];
-#pragma unroll
-      for (int j = 0; j < 32; j += 4) {
-        const float4 v = __ldg(reinterpret_cast<const float4*>(row + h2 * 32 + j));
-        tc::split_tf32(v.x, hi[j], lo[j]);
-        tc::split_tf32(v.y, hi[j + 1], lo[j + 1]);
-        tc::split_tf32(v.z, hi[j + 2], lo[j + 2]);
-        tc::split_tf32(v.w, hi[j + 3], lo[j + 3]);
-      }
-      tc::st32(tm + lrow + (uint32_t)(hf * 64 + h2 * 32), hi);
-      tc::st32(tm + lrow + TLO + (uint32_t)(hf * 64 + h2 * 32), lo);
+    for (int j = 0; j < KQ; j += 4) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(row + j));
+      tc::split_tf32(v.x, hi[j], lo[j]);
+      tc::split_tf32(v.y, hi[j + 1], lo[j + 1]);
+      tc::split_tf32(v.z, hi[j + 2], lo[j + 2]);
+      tc::split_tf32(v.w, hi[j + 3], lo[j + 3]);
     }
+    tc::st32(tm + lrow + (uint32_t)(hq * KQ), hi);
+    tc::st32(tm + lrow + TLO + (uint32_t)(hq * KQ), lo);
   };
-  // activations of 4 points (group j) -> next forward operand, or a_{L-1} in FP32
-  auto put_act4 = [&](int l, int j, const float (&a)[C][4]) {
+  // ... or from a copy staged in shared memory whose element (row nrn,
+  // column k) sits at ws[k W + nrn] (a transposed copy): a warp reads 128
+  // consecutive bytes per column
+  auto put_w_staged = [&](const float* ws) {
+    mbar_wait(&wbar, wphase & 1, b.err);
+    ++wphase;
+    float hi[KQ], lo[KQ];
+#pragma unroll
+    for (int j = 0; j < KQ; ++j) tc::split_tf32(ws[(hq * KQ + j) * W + nrn], hi[j], lo[j]);
+    tc::st32(tm + lrow + (uint32_t)(hq * KQ), hi);
+    tc::st32(tm + lrow + TLO + (uint32_t)(hq * KQ), lo);
+  };
+  // activations -> next forward operand, or a_{L-1} in FP32
+  auto put_act = [&](int l, const float (&a)[C][HP]) {
     if (l + 1 < L) {
 #pragma unroll
       for (int c = 0; c < C; ++c)
 #pragma unroll
-        for (int u = 0; u < 4; ++u) put_row(c, 4 * j + u, a[c][u]);
+        for (int u = 0; u < HP; ++u) put_row(c, u, a[c][u]);
     } else {
 #pragma unroll
       for (int c = 0; c < C; ++c)
-        *reinterpret_cast<float4*>(outa + nrn * RSO + c * P + hf * HP + 4 * j) =
-            make_float4(a[c][0], a[c][1], a[c][2], a[c][3]);
+        *reinterpret_cast<float4*>(outa + nrn * RSO + c * P + p0) = make_float4(a[c][0], a[c][1], a[c][2], a[c][3]);
+    }
+  };
+  // M x N result (main + corrections) of the thread's points
+  auto ld_result = [&](float (&r)[C][HP]) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      float v[4], x[4];
+      tc::ld4(tm + lrow + TD + (uint32_t)(c * P + p0), v);
+      tc::ld4(tm + lrow + TG + (uint32_t)(c * P + p0), x);
+#pragma unroll
+      for (int u = 0; u < HP; ++u) r[c][u] = v[u] + x[u];
     }
   };
 
@@ -265,10 +327,10 @@ __global__ void __launch_bounds__(NT, 1)
     const float* const th = b.theta + (size_t)net * sh.npp;
     const float* const thT = b.thetaT + (size_t)net * sh.nTp;
     const NetInfo ni = b.nets[net];
-    for (int e = t; e < W * DIN; e += NT) w0s[(e / DIN) * 4 + e % DIN] = th[sh.woff[0] + e];
-    for (int e = t; e < W; e += NT) b0s[e] = th[sh.boff[0] + e];
-    for (int e = t; e < (L - 1) * W; e += NT) bls[e] = th[sh.boff[1 + e / W] + e % W];
-    for (int e = t; e < DOUT * W; e += NT) wLs[e] = th[sh.woff[L] + e];
+    for (int e = t; e < W * DIN; e += NTC) w0s[(e / DIN) * 4 + e % DIN] = th[sh.woff[0] + e];
+    for (int e = t; e < W; e += NTC) b0s[e] = th[sh.boff[0] + e];
+    for (int e = t; e < (L - 1) * W; e += NTC) bls[e] = th[sh.boff[1 + e / W] + e % W];
+    for (int e = t; e < DOUT * W; e += NTC) wLs[e] = th[sh.woff[L] + e];
     if (t < DOUT) bLs[t] = th[sh.boff[L] + t];
     if (t < 4) s_scale[t] = t < DIN ? ni.scale[t] : 0.f;
     double lsum0 = 0.0;   // thread 0: sum of r^2 over the item
@@ -295,61 +357,47 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
         for (int q = 0; q < DIN; ++q) w[q] = w0s[nrn * 4 + q];
         const float bias = b0s[nrn];
+        float h[C][HP], a[C][HP];
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          float h[C][4], a[C][4];
+        for (int u = 0; u < HP; ++u) {
+          const int p = p0 + u;
+          float v = bias;
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int p = hf * HP + 4 * j + u;
-            float v = bias;
+          for (int q = 0; q < DIN; ++q) v = fmaf(w[q], xh[p * 4 + q], v);
+          h[0][u] = stash_value<ACT>(v);
 #pragma unroll
-            for (int q = 0; q < DIN; ++q) v = fmaf(w[q], xh[p * 4 + q], v);
-            h[0][u] = stash_value<ACT>(v);
-#pragma unroll
-            for (int q = 0; q < DIN; ++q) h[1 + q][u] = w[q] * s_scale[q];
-            h[C - 1][u] = 0.f;
-          }
-          stash_st4(0, j, h);
-          act4(h, a);
-          put_act4(0, j, a);
+          for (int q = 0; q < DIN; ++q) h[1 + q][u] = w[q] * s_scale[q];
+          h[C - 1][u] = 0.f;
         }
+        stash_st(0, h);
+        act_pts(h, a);
+        put_act(0, a);
       }
-      // ---- hidden layers on the tensor cores
+      // ---- hidden layers on the tensor cores (W_l rows: lane = output neuron)
+      if (L > 1) put_w(th + sh.woff[1] + (size_t)nrn * W + hq * KQ);
       for (int l = 1; l < L; ++l) {
-        put_w(th + sh.woff[l] + (size_t)nrn * W + hf * 64);   // lane = output neuron
         publish();
         issue(tm + TD, tm + TG, sX, sXl, NC * 128, W / 8, IDN);
+        // W_{l+1}^T is staged into the (idle) weight-gradient operand region
+        // while the MMA runs, and moved to tensor memory once it has completed
+        if (t == 0 && l + 1 < L) bulk_load(gA, thT + (size_t)l * W * W, W * W * 4, &wbar);
         wait_mma();
+        float h[C][HP], a[C][HP];
+        ld_result(h);
+        if (l + 1 < L) put_w_staged(reinterpret_cast<const float*>(gA));
         const float bias = bls[(l - 1) * W + nrn];
-        float d8[C][8];
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-          float x8[8];
-          tc::ld8(tm + lrow + TD + (uint32_t)(c * P + hf * HP), d8[c]);
-          tc::ld8(tm + lrow + TG + (uint32_t)(c * P + hf * HP), x8);
-#pragma unroll
-          for (int u = 0; u < 8; ++u) d8[c][u] += x8[u];
-        }
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          float h[C][4], a[C][4];
-#pragma unroll
-          for (int c = 0; c < C; ++c)
-#pragma unroll
-            for (int u = 0; u < 4; ++u) h[c][u] = d8[c][4 * j + u];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) h[0][u] = stash_value<ACT>(h[0][u] + bias);
-          stash_st4(l, j, h);
-          act4(h, a);
-          put_act4(l, j, a);
-        }
+        for (int u = 0; u < HP; ++u) h[0][u] = stash_value<ACT>(h[0][u] + bias);
+        stash_st(l, h);
+        act_pts(h, a);
+        put_act(l, a);
       }
       __syncthreads();
       // ---- output layer (FP32): Y[j][p][c] = W_L[j] . a_{L-1}[.][p][c] (+ b_L on values)
       {
         constexpr int PAIRS = DOUT * P;
-        constexpr int KS = NT / PAIRS >= 4 ? 4 : (NT / PAIRS >= 2 ? 2 : 1);
-        for (int pr = t / KS; pr < PAIRS; pr += NT / KS) {
+        constexpr int KS = NTC / PAIRS >= 8 ? 8 : (NTC / PAIRS >= 4 ? 4 : 2);
+        for (int pr = t / KS; pr < PAIRS; pr += NTC / KS) {
           const int j = pr / P, p = pr % P, lk = t % KS;
           float acc[C];
 #pragma unroll
@@ -390,7 +438,7 @@ __global__ void __launch_bounds__(NT, 1)
           for (int c = 0; c < C; ++c) ybsm[j * NC + t * C + c] = Yb[j][c];
       }
       {
-        const float s = block_sum(l0, s_red);
+        const float s = block_sum_tc(l0, s_red);
         if (t == 0) lsum0 += (double)s;
       }
       __syncthreads();
@@ -398,19 +446,24 @@ __global__ void __launch_bounds__(NT, 1)
 
       // ================= reverse pass =================
       float* const g = b.grad_part + (size_t)item.slot * sh.npp;
+      // the stashed form of layer l is loaded one layer ahead (hsn)
+      float hsn[C][HP];
+      stash_ld(L - 1, hsn);
+      // W_{L-1}^T rows (lane = input neuron)
+      if (L > 1) put_w(thT + (size_t)(L - 2) * W * W + (size_t)nrn * W + hq * KQ);
       // output layer: dW_L[j][k] = sum_{p,c} Yb[j][p][c] a_{L-1}[k][p][c], db_L
-      for (int e = t; e < DOUT * W; e += NT) {
+      for (int e = t; e < DOUT * W; e += NTC) {
         const int j = e / W, k = e % W;
         float s = 0.f;
         for (int p = 0; p < P; ++p)
 #pragma unroll
           for (int c = 0; c < C; ++c) s = fmaf(ybsm[j * NC + p * C + c], outa[k * RSO + c * P + p], s);
-        grad_rmw(g + sh.woff[L] + e, s, first);
+        gacc(g + sh.woff[L] + e, s, first);
       }
       if (t < DOUT) {
         float s = 0.f;
         for (int p = 0; p < P; ++p) s += ybsm[t * NC + p * C];
-        grad_rmw(g + sh.boff[L] + t, s, first);
+        gacc(g + sh.boff[L] + t, s, first);
       }
       // adjoint of a_{L-1} for the thread's neuron and points: W_L^T Yb
       float ab[C][HP];
@@ -419,99 +472,86 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
         for (int j = 0; j < DOUT; ++j) wl[j] = wLs[j * W + nrn];
 #pragma unroll
-        for (int pp = 0; pp < HP; ++pp) {
-          const int p = hf * HP + pp;
+        for (int u = 0; u < HP; ++u) {
+          const int p = p0 + u;
 #pragma unroll
           for (int c = 0; c < C; ++c) {
             float v = 0.f;
 #pragma unroll
             for (int j = 0; j < DOUT; ++j) v = fmaf(wl[j], ybsm[j * NC + p * C + c], v);
-            ab[c][pp] = v;
+            ab[c][u] = v;
           }
         }
       }
       for (int l = L - 1; l >= 1; --l) {
-        // zbar_l = adjoint of the activation at layer l (stashed jets)
+        // zbar_l = adjoint of the activation at layer l
         float zb[C][HP];
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          float hs[C][4];
-          stash_ld4(l, j, hs);
+        for (int u = 0; u < HP; ++u) {
+          float hz[C], av[C], zz[C];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            float hz[C], av[C], zz[C];
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-              hz[c] = hs[c][u];
-              av[c] = ab[c][4 * j + u];
-            }
-            act_bwd<C, DS, DIN, ACT>(hz, av, zz);
-#pragma unroll
-            for (int c = 0; c < C; ++c) zb[c][4 * j + u] = zz[c];
+          for (int c = 0; c < C; ++c) {
+            hz[c] = hsn[c][u];
+            av[c] = ab[c][u];
           }
-        }
-        {
-          float s = 0.f;
+          act_bwd<C, DS, DIN, ACT>(hz, av, zz);
 #pragma unroll
-          for (int pp = 0; pp < HP; ++pp) s += zb[0][pp];
-          xpart[(hf * W + nrn) * 8] = s;
+          for (int c = 0; c < C; ++c) zb[c][u] = zz[c];
         }
+        xpart[(hq * W + nrn) * 8] = (zb[0][0] + zb[0][1]) + (zb[0][2] + zb[0][3]);
 #pragma unroll
         for (int c = 0; c < C; ++c)
 #pragma unroll
-          for (int pp = 0; pp < HP; ++pp) put_row(c, pp, zb[c][pp]);   // zbar_l as [n][out]
-        put_w(thT + (size_t)(l - 1) * W * W + (size_t)nrn * W + hf * 64);   // W_l^T: lane = input neuron
+          for (int u = 0; u < HP; ++u) put_row(c, u, zb[c][u]);   // zbar_l as [n][out]
         publish();
         issue(tm + TD, tm + TG, sX, sXl, NC * 128, W / 8, IDN);   // abar_{l-1} = W_l^T zbar_l
         // meanwhile: a_{l-1} as the [in][n] operand of the weight gradient, and db_l
+        stash_ld(l - 1, hsn);
+        {
+          float a[C][HP];
+          act_pts(hsn, a);
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          float hs[C][4], a[C][4];
-          stash_ld4(l - 1, j, hs);
-          act4(hs, a);
-#pragma unroll
-          for (int c = 0; c < C; ++c) put_col4(c, j, a[c]);
+          for (int c = 0; c < C; ++c) put_col4(c, a[c]);
         }
-        if (hf == 0) grad_rmw(g + sh.boff[l] + nrn, xpart[nrn * 8] + xpart[(W + nrn) * 8], first);
+        if (hq == 0) {
+          float s = 0.f;
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) s += xpart[(q * W + nrn) * 8];
+          gacc(g + sh.boff[l] + nrn, s, first);
+        }
         wait_mma();
+        // W_{l-1} is staged into the [n][neuron] region (idle until the next
+        // layer) while the weight-gradient MMA runs
+        if (t == 0 && l > 1) bulk_load(gX, th + sh.woff[l - 1], W * W * 4, &wbar);
         // zbar_l -> tensor memory (A operand of the weight gradient, lane = output neuron)
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          float hv[8], lv[8];
+          float hv[4], lv[4];
 #pragma unroll
-          for (int pp = 0; pp < HP; ++pp) tc::split_tf32(zb[c][pp], hv[pp], lv[pp]);
-          tc::st8(tm + lrow + (uint32_t)(c * P + hf * HP), hv);
-          tc::st8(tm + lrow + TLO + (uint32_t)(c * P + hf * HP), lv);
+          for (int u = 0; u < HP; ++u) tc::split_tf32(zb[c][u], hv[u], lv[u]);
+          tc::st4(tm + lrow + (uint32_t)(c * P + p0), hv);
+          tc::st4(tm + lrow + TLO + (uint32_t)(c * P + p0), lv);
         }
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-          float v[8], x8[8];
-          tc::ld8(tm + lrow + TD + (uint32_t)(c * P + hf * HP), v);
-          tc::ld8(tm + lrow + TG + (uint32_t)(c * P + hf * HP), x8);
-#pragma unroll
-          for (int pp = 0; pp < HP; ++pp) ab[c][pp] = v[pp] + x8[pp];
-        }
+        ld_result(ab);
         publish();
         issue(tm + TG, tm + TD, sA, sAl, 16384, NC / 8, IDW);    // dW_l = zbar_l a_{l-1}^T
         wait_mma();
         {
-          float* const gw = g + sh.woff[l] + (size_t)nrn * W + hf * 64;
+          float* const gw = g + sh.woff[l] + (size_t)nrn * W + hq * KQ;
 #pragma unroll
-          for (int h2 = 0; h2 < 2; ++h2) {
-            float v[32], x[32];
-            tc::ld32(tm + lrow + TG + (uint32_t)(hf * 64 + h2 * 32), v);
-            tc::ld32(tm + lrow + TD + (uint32_t)(hf * 64 + h2 * 32), x);
+          for (int h2 = 0; h2 < KQ / 16; ++h2) {
+            float v[16], x[16];
+            tc::ld16(tm + lrow + TG + (uint32_t)(hq * KQ + h2 * 16), v);
+            tc::ld16(tm + lrow + TD + (uint32_t)(hq * KQ + h2 * 16), x);
 #pragma unroll
-            for (int j = 0; j < 32; j += 4) {
-              float4* const p4 = reinterpret_cast<float4*>(gw + h2 * 32 + j);
-              float4 o = make_float4(v[j] + x[j], v[j + 1] + x[j + 1], v[j + 2] + x[j + 2], v[j + 3] + x[j + 3]);
-              if (!first) {
-                const float4 q = *p4;
-                o.x += q.x; o.y += q.y; o.z += q.z; o.w += q.w;
-              }
-              *p4 = o;
-            }
+            for (int j = 0; j < 16; j += 4)
+              gacc4(gw + h2 * 16 + j, make_float4(v[j] + x[j], v[j + 1] + x[j + 1], v[j + 2] + x[j + 2], v[j + 3] + x[j + 3]),
+                    first);
           }
+        }
+        if (l > 1) {   // the weight-gradient MMA (A operand zbar_l) has completed
+          put_w_staged(reinterpret_cast<const float*>(gX));
+          __syncthreads();   // all reads of the staged copy precede the next zbar rows
         }
       }
       // first affine map: dW_0[i][q] += sum_p (zbar_val xh_q + s_q zbar_q), db_0
@@ -520,36 +560,34 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
         for (int q = 0; q <= DIN; ++q) part[q] = 0.f;
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          float hs[C][4];
-          stash_ld4(0, j, hs);
+        for (int u = 0; u < HP; ++u) {
+          float hz[C], av[C], zz[C];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            float hz[C], av[C], zz[C];
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-              hz[c] = hs[c][u];
-              av[c] = ab[c][4 * j + u];
-            }
-            act_bwd<C, DS, DIN, ACT>(hz, av, zz);
-            const int p = hf * HP + 4 * j + u;
-#pragma unroll
-            for (int q = 0; q < DIN; ++q) {
-              part[q] = fmaf(zz[0], xh[p * 4 + q], part[q]);
-              part[q] = fmaf(s_scale[q], zz[1 + q], part[q]);
-            }
-            part[DIN] += zz[0];
+          for (int c = 0; c < C; ++c) {
+            hz[c] = hsn[c][u];
+            av[c] = ab[c][u];
           }
+          act_bwd<C, DS, DIN, ACT>(hz, av, zz);
+          const int p = p0 + u;
+#pragma unroll
+          for (int q = 0; q < DIN; ++q) {
+            part[q] = fmaf(zz[0], xh[p * 4 + q], part[q]);
+            part[q] = fmaf(s_scale[q], zz[1 + q], part[q]);
+          }
+          part[DIN] += zz[0];
         }
 #pragma unroll
-        for (int q = 0; q <= DIN; ++q) xpart[(hf * W + nrn) * 8 + q] = part[q];
+        for (int q = 0; q <= DIN; ++q) xpart[(hq * W + nrn) * 8 + q] = part[q];
       }
       __syncthreads();
-      if (hf == 0) {
+      if (hq == 0) {
 #pragma unroll
-        for (int q = 0; q < DIN; ++q)
-          grad_rmw(g + sh.woff[0] + nrn * DIN + q, xpart[nrn * 8 + q] + xpart[(W + nrn) * 8 + q], first);
-        grad_rmw(g + sh.boff[0] + nrn, xpart[nrn * 8 + DIN] + xpart[(W + nrn) * 8 + DIN], first);
+        for (int q = 0; q <= DIN; ++q) {
+          float s = 0.f;
+#pragma unroll
+          for (int r = 0; r < NQ; ++r) s += xpart[(r * W + nrn) * 8 + q];
+          gacc(q < DIN ? g + sh.woff[0] + nrn * DIN + q : g + sh.boff[0] + nrn, s, first);
+        }
       }
       __syncthreads();
     }   // sub-tiles
