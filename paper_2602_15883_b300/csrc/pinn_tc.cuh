@@ -537,17 +537,44 @@ __global__ void __launch_bounds__(NTC, 1)
         issue(tm + TG, tm + TD, sA, sAl, 16384, NC / 8, IDW);    // dW_l = zbar_l a_{l-1}^T
         wait_mma();
         {
-          float* const gw = g + sh.woff[l] + (size_t)nrn * W + hq * KQ;
+          // the thread's 32 columns of row nrn as 8 float4 chunks, then an
+          // 8 x 8 transpose of chunks among each group of 8 lanes, so that the
+          // 8 lanes of a group write one 128-byte row segment per instruction
+          // (full sectors) instead of 8 rows 16 bytes each
+          static_assert(KQ == 32, "8 chunks per thread");
+          float4 q[8];
 #pragma unroll
-          for (int h2 = 0; h2 < KQ / 16; ++h2) {
+          for (int h2 = 0; h2 < 2; ++h2) {
             float v[16], x[16];
             tc::ld16(tm + lrow + TG + (uint32_t)(hq * KQ + h2 * 16), v);
             tc::ld16(tm + lrow + TD + (uint32_t)(hq * KQ + h2 * 16), x);
 #pragma unroll
-            for (int j = 0; j < 16; j += 4)
-              gacc4(gw + h2 * 16 + j, make_float4(v[j] + x[j], v[j + 1] + x[j + 1], v[j + 2] + x[j + 2], v[j + 3] + x[j + 3]),
-                    first);
+            for (int j = 0; j < 4; ++j)
+              q[h2 * 4 + j] = make_float4(v[4 * j] + x[4 * j], v[4 * j + 1] + x[4 * j + 1], v[4 * j + 2] + x[4 * j + 2],
+                                          v[4 * j + 3] + x[4 * j + 3]);
           }
+#pragma unroll
+          for (int sx = 4; sx >= 1; sx >>= 1) {
+            const bool up = (lane & sx) != 0;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              if ((c & sx) == 0) {
+                const float4 snd = up ? q[c] : q[c | sx];
+                float4 rcv;
+                rcv.x = __shfl_xor_sync(0xffffffffu, snd.x, sx);
+                rcv.y = __shfl_xor_sync(0xffffffffu, snd.y, sx);
+                rcv.z = __shfl_xor_sync(0xffffffffu, snd.z, sx);
+                rcv.w = __shfl_xor_sync(0xffffffffu, snd.w, sx);
+                if (up) q[c] = rcv;
+                else q[c | sx] = rcv;
+              }
+            }
+          }
+          // lane (8 gr + j) now holds chunk j of the rows of lanes 8 gr + c
+          const int row0 = qd * 32 + (lane & ~7);
+          float* const gw = g + sh.woff[l] + (size_t)row0 * W + hq * KQ + 4 * (lane & 7);
+#pragma unroll
+          for (int c = 0; c < 8; ++c) gacc4(gw + (size_t)c * W, q[c], first);
         }
         if (l > 1) {   // the weight-gradient MMA (A operand zbar_l) has completed
           put_w_staged(reinterpret_cast<const float*>(gX));

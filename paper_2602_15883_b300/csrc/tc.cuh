@@ -43,11 +43,13 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// round to TF32 (nearest, ties away), result as an FP32 bit pattern
+// round to TF32 (10 explicit mantissa bits; nearest, ties away from zero),
+// result as an FP32 bit pattern with the 13 low bits clear: adding half a
+// TF32 unit to the magnitude bits and truncating rounds |x| half-up (a carry
+// into the exponent is the correct rounding up to the next binade).  Two
+// integer operations instead of a conversion instruction; finite inputs only.
 __device__ __forceinline__ float to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 // x = hi + lo + O(2^-22 |x|), hi and lo both TF32
 __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
