@@ -249,8 +249,9 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     ap.add_argument("--serving-seconds", type=float, default=5.0)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3"],
-                    help="hidden-layer contractions of the jet kernel: FP32 FMA, or tcgen05 3xTF32 (width 128)")
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "tf32x3"],
+                    help="hidden-layer contractions of the jet kernel: FP32 FMA, or tcgen05 3xTF32 (width 128); "
+                         "auto = tf32x3 where the width allows it")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -271,6 +272,8 @@ def main():
 
     cfg, pb = make_problem(args, rank)
     cfg["device"] = local
+    if args.precision == "auto":
+        args.precision = "tf32x3" if cfg["width"] == 128 else "fp32"
     cfg["precision"] = PRECISIONS[args.precision]
     d = Dpinn(cfg)
     d.set_problem(pb)

@@ -119,6 +119,16 @@ __device__ __forceinline__ void gacc4(float* p, float4 v, bool first) {
                  : "memory");
 }
 
+// L2 residency of the per-CTA stash: a bulk prefetch of a contiguous block
+// into L2 ahead of its loads, and a discard of its lines after their last
+// read (the values are dead; a discarded line is never written back to DRAM).
+__device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void l2_discard(const void* p) {
+  asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+}
+
 // Deterministic sum over the CTA of one float per thread (fixed order).
 __device__ __forceinline__ float block_sum_tc(float v, float* red) {
 #pragma unroll
@@ -215,7 +225,16 @@ __global__ void __launch_bounds__(NTC, 1)
     __syncthreads();
     tc::fence_after();
   };
-  // stash: one float4 per channel c (the thread's 4 points)
+  // stash: one float4 per channel c (the thread's 4 points); layer l of the
+  // CTA is one contiguous block of C * NTC float4
+  constexpr uint32_t STASH_LAYER_BYTES = (uint32_t)C * NTC * 16;
+  auto stash_prefetch = [&](int l) {
+    if (t == 0) l2_prefetch(stash + (size_t)l * C * NTC, STASH_LAYER_BYTES);
+  };
+  auto stash_discard = [&](int l) {
+    for (uint32_t o = (uint32_t)t * 128; o < STASH_LAYER_BYTES; o += NTC * 128)
+      l2_discard(reinterpret_cast<const char*>(stash + (size_t)l * C * NTC) + o);
+  };
   auto stash_st = [&](int l, const float (&h)[C][HP]) {
 #pragma unroll
     for (int c = 0; c < C; ++c)
@@ -448,6 +467,7 @@ __global__ void __launch_bounds__(NTC, 1)
       float* const g = b.grad_part + (size_t)item.slot * sh.npp;
       // the stashed form of layer l is loaded one layer ahead (hsn)
       float hsn[C][HP];
+      if (L > 1) stash_prefetch(L - 2);
       stash_ld(L - 1, hsn);
       // W_{L-1}^T rows (lane = input neuron)
       if (L > 1) put_w(thT + (size_t)(L - 2) * W * W + (size_t)nrn * W + hq * KQ);
@@ -505,6 +525,8 @@ __global__ void __launch_bounds__(NTC, 1)
           for (int u = 0; u < HP; ++u) put_row(c, u, zb[c][u]);   // zbar_l as [n][out]
         publish();
         issue(tm + TD, tm + TG, sX, sXl, NC * 128, W / 8, IDN);   // abar_{l-1} = W_l^T zbar_l
+        stash_discard(l);   // its last reads (hsn) precede the barrier above
+        if (l > 1) stash_prefetch(l - 2);
         // meanwhile: a_{l-1} as the [in][n] operand of the weight gradient, and db_l
         stash_ld(l - 1, hsn);
         {
@@ -582,6 +604,8 @@ __global__ void __launch_bounds__(NTC, 1)
         }
       }
       // first affine map: dW_0[i][q] += sum_p (zbar_val xh_q + s_q zbar_q), db_0
+      __syncthreads();
+      stash_discard(0);
       {
         float part[DIN + 1];
 #pragma unroll
