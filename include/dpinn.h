@@ -175,7 +175,41 @@ int dpinn_face_info(dpinn_t* h, int face, int* net_lo, int* net_hi, int* axis, i
 int dpinn_set_points(dpinn_t* h, int kind, const float* pts, const float* vals,
                      const int64_t* counts, int n_counts);
 
-/* Run n_steps training iterations asynchronously on `stream` (one captured
+/* Per-step resampling of the collocation points (mini-batch epochs: fresh
+ * residual points every step, none stored or copied from the host).  The
+ * paper trains on fixed point sets per epoch (Sec. 3, Table B1); this call,
+ * which the paper has no counterpart of, draws counts[k] points uniformly in
+ * net k's interior cell before each training step, losses-only or gradient
+ * evaluation, on the device.  Generator (counter-based, reproducible): with
+ * mix the output function of SplitMix64 (Steele, Lea, Flood 2014:
+ * z ^= z >> 30; z *= 0xBF58476D1CE4E5B9; z ^= z >> 27; z *= 0x94D049BB133111EB;
+ * z ^= z >> 31) and gamma = 0x9E3779B97F4A7C15, all modulo 2^64,
+ *   S_t     = mix(seed + (t + 1) gamma)      t = steps taken so far
+ *   S_{t,k} = mix(S_t + (k + 1) gamma)
+ *   u       = (mix(S_{t,k} + (i d_in + d + 1) gamma) >> 40) * 2^-24
+ *   x_{i,d} = (float)(lo_{k,d} + u * (hi_{k,d} - lo_{k,d}))   (double, no FMA)
+ * for point i (0-based within net k) and input axis d, where lo/hi are the
+ * cell bounds lo_d + c_d (hi_d - lo_d) / splits_d in double.  counts [n_nets]
+ * (host); counts == NULL switches resampling off and keeps the last sampled
+ * set as the residual points.  dpinn_set_points(RESIDUAL) also switches it
+ * off.  Errors: INVALID_ARG (length, negative count, more than 2^30 points),
+ * CUDA. */
+int dpinn_set_resampling(dpinn_t* h, const int64_t* counts, int n_counts, uint64_t seed);
+
+/* Synchronise and copy the current points of a set (kind RESIDUAL, OBS or
+ * FACE; [n][d_in] float32, n = the sum of that set's counts) to host_out.
+ * With resampling, the residual points are those of the most recent step or
+ * evaluation.  Errors: INVALID_ARG, STATE (set not present), CUDA. */
+int dpinn_get_points(dpinn_t* h, int kind, float* host_out);
+
+/* Memory budget (bytes, 0 = the default of 1 GiB) for the per-work-item
+ * gradient partials: the plan enlarges its point chunks until
+ * (number of items) x (per-net parameter stride) x 4 bytes fits, so the
+ * number of points per step is not limited by this memory.  The gradient is
+ * the same sum, in a different (fixed) order.  Rebuilds the plan. */
+int dpinn_set_partial_budget(dpinn_t* h, int64_t bytes);
+
+/* Run n_steps training iterations asynchronously on `stream` (one captured/* Run n_steps training iterations asynchronously on `stream` (one captured
  * CUDA graph per step: exchange, losses + gradients of all nets, Adam).
  * Errors: STATE (points missing), CUDA. */
 int dpinn_step(dpinn_t* h, dpinn_stream_t stream, int n_steps);

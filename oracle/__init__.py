@@ -76,12 +76,20 @@ def lib():
             "ora_step": [vp] * 7,
             "ora_query": [vp, vp, vp, i64, i32, vp, vp],
             "ora_step_cached": [vp] * 9,
+            "ora_sample": [vp, C.c_uint64, i64, vp, vp],
+            "ora_splitmix64_nth": [C.c_uint64, C.c_uint64],
         }
         for name, args in sig.items():
             fn = getattr(_lib, name)
             fn.argtypes = args
             fn.restype = C.c_int if name != "ora_set_threads" else None
+        _lib.ora_splitmix64_nth.restype = C.c_uint64
     return _lib
+
+
+def splitmix64_nth(seed: int, n: int) -> int:
+    """n-th output (n >= 1) of SplitMix64 seeded with ``seed``."""
+    return int(lib().ora_splitmix64_nth(int(seed) & (2**64 - 1), int(n) & (2**64 - 1)))
 
 
 def set_threads(n: int) -> None:
@@ -257,6 +265,14 @@ class Oracle:
         lib().ora_step_cached(C.addressof(self.c), C.addressof(self.pc), _p(th), _p(m), _p(v), C.addressof(tt),
                               _p(loss), _p(cache["val"]), _p(cache["anc"]))
         return th, m, v, tt.value, loss
+
+    def sample(self, seed, t, counts):
+        """Collocation points of step ``t`` (uniform per net cell, SplitMix64
+        streams): float32 [sum counts][d_in], nets in order."""
+        counts = np.ascontiguousarray(counts, np.int64)
+        out = np.empty((int(counts.sum()), self.d_in), np.float32)
+        lib().ora_sample(C.addressof(self.c), int(seed), int(t), counts.ctypes.data, out.ctypes.data)
+        return out
 
     def query(self, th, pts, want_res=False):
         th = np.ascontiguousarray(th, np.float64)

@@ -693,6 +693,28 @@ void adam(const Geo& g, double* th, double* m, double* v, int64_t t, const doubl
 
 }  // namespace
 
+// ------------------------------------------------- collocation sampler ---
+// Uniform collocation points in each net's interior cell for step t, from
+// counter-based SplitMix64 streams (Steele, Lea, Flood 2014): the generator
+// seeded with S yields mix(S + n * gamma) as its n-th output (n = 1, 2, ...),
+// mix being its output function.  Step stream S_t = output t + 1 of the seed;
+// net stream S_{t,k} = output k + 1 of S_t; axis d of point i takes output
+// i * d_in + d + 1 of S_{t,k}, its top 24 bits giving u in [0, 1); the point
+// is lo + u (hi - lo) in double, rounded to float32.  (A sampling scheme the
+// paper leaves open; it trains on fixed point sets, Sec. 3.)
+static uint64_t splitmix64_output(uint64_t z) {
+  z ^= z >> 30;
+  z *= 0xBF58476D1CE4E5B9ull;
+  z ^= z >> 27;
+  z *= 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return z;
+}
+static uint64_t splitmix64_nth(uint64_t seed, uint64_t n) {
+  const uint64_t gamma = 0x9E3779B97F4A7C15ull;
+  return splitmix64_output(seed + n * gamma);
+}
+
 // ================================================================ C API ===
 extern "C" {
 
@@ -711,6 +733,28 @@ int ora_layout(const ora_config* c, int* n_nets, int* n_faces, int* n_params,
   for (int f = 0; faces && f < g.n_faces; ++f) {
     faces[f * 4 + 0] = g.face[f][0]; faces[f * 4 + 1] = g.face[f][1];
     faces[f * 4 + 2] = g.face[f][2]; faces[f * 4 + 3] = g.face_is_time(f) ? 1 : 0;
+  }
+  return 0;
+}
+
+// n-th output of the SplitMix64 generator seeded with `seed` (tests).
+uint64_t ora_splitmix64_nth(uint64_t seed, uint64_t n) { return splitmix64_nth(seed, n); }
+
+// Collocation points of step t: counts[k] points of net k, concatenated in
+// net order, out [sum counts][d_in] float32.
+int ora_sample(const ora_config* c, uint64_t seed, int64_t t, const int64_t* counts, float* out) {
+  Geo g(*c);
+  int64_t row = 0;
+  const uint64_t s_t = splitmix64_nth(seed, (uint64_t)t + 1);
+  for (int k = 0; k < g.n_nets; ++k) {
+    const uint64_t s_tk = splitmix64_nth(s_t, (uint64_t)k + 1);
+    for (int64_t i = 0; i < counts[k]; ++i, ++row)
+      for (int d = 0; d < g.din; ++d) {
+        const uint64_t o = splitmix64_nth(s_tk, (uint64_t)(i * g.din + d) + 1);
+        const double u = (double)(o >> 40) / 16777216.0;
+        const double x = g.blo[k][d] + u * (g.bhi[k][d] - g.blo[k][d]);
+        out[row * g.din + d] = (float)x;
+      }
   }
   return 0;
 }

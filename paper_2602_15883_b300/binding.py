@@ -29,6 +29,7 @@ EXPORTS = (
     "dpinn_apply_grad", "dpinn_launches_per_step", "dpinn_step_timed", "dpinn_query_static",
     "dpinn_eval_loss", "dpinn_set_params", "dpinn_set_schedule", "dpinn_get_schedule",
     "dpinn_qctx_create", "dpinn_qctx_destroy", "dpinn_qctx_query", "dpinn_qctx_status",
+    "dpinn_set_resampling", "dpinn_get_points", "dpinn_set_partial_budget",
 )
 
 
@@ -100,6 +101,9 @@ def load_library(path: str = LIB_PATH):
         "dpinn_qctx_destroy": ([vp], None),
         "dpinn_qctx_query": ([vp, vp, i64, i32, vp, vp], i32),
         "dpinn_qctx_status": ([vp, vp], i32),
+        "dpinn_set_resampling": ([vp, vp, i32, C.c_uint64], i32),
+        "dpinn_get_points": ([vp, i32, vp], i32),
+        "dpinn_set_partial_budget": ([vp, i64], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -221,6 +225,25 @@ class Dpinn:
         p, kp = _ptr(pts)
         q, kq = _ptr(vals)
         self._check(self.lib.dpinn_set_points(self.h, kind, p, q, counts.ctypes.data, len(counts)))
+
+    def set_resampling(self, counts, seed=0):
+        """Fresh uniform residual points in every net's cell before each step
+        (``counts`` per net), or off with ``counts=None``."""
+        if counts is None:
+            self._check(self.lib.dpinn_set_resampling(self.h, None, 0, 0))
+            return
+        counts = np.ascontiguousarray(counts, np.int64)
+        self._check(self.lib.dpinn_set_resampling(self.h, counts.ctypes.data, len(counts), int(seed)))
+        self._res_counts = counts.copy()
+
+    def get_points(self, kind, n):
+        """The current points of a set as float32 [n][d_in] (n = sum of its counts)."""
+        out = np.empty((int(n), self.d_in), np.float32)
+        self._check(self.lib.dpinn_get_points(self.h, int(kind), out.ctypes.data))
+        return out
+
+    def set_partial_budget(self, nbytes):
+        self._check(self.lib.dpinn_set_partial_budget(self.h, int(nbytes)))
 
     def set_problem(self, pb, set_params=True):
         self.set_points(POINTS_RESIDUAL, np.asarray(pb.res_pts, np.float32), pb.res_counts)

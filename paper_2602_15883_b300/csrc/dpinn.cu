@@ -89,6 +89,14 @@ struct dpinn {
   DevBuf<float> res_pts, obs_pts, obs_vals, face_pts;
   std::vector<int64_t> res_counts, obs_counts, face_counts;
   bool have[3] = {false, false, false};
+  // per-step resampling of the residual points (dpinn_set_resampling)
+  bool resample = false;
+  uint64_t rs_seed = 0;
+  int64_t rs_max = 0;
+  DevBuf<long long> rs_off;
+  DevBuf<double> rs_box;
+  // gradient-partial memory budget (bytes) bounding the number of work items
+  int64_t part_budget = (int64_t)1 << 30;
   // volumetric ghost layers: directed segments (own net, owner net, is_time)
   // of the ghost points, grouped by own net then owner
   bool ghost_mode = false;
@@ -213,6 +221,14 @@ cudaError_t enqueue_step(dpinn* h, int mode, cudaStream_t s, int* n_launch, cuda
   dk::Bufs b = make_bufs(h);
   cudaError_t e = cudaMemsetAsync(h->counters.p, 0, 4 * sizeof(int), s);
   mark(nullptr);
+  if (e == cudaSuccess && h->resample && h->rs_max > 0) {
+    const int gx = (int)std::min<int64_t>((h->rs_max + 255) / 256, 64);
+    dk::k_sample<<<dim3(gx, h->n_nets), 256, 0, s>>>(h->din, h->rs_seed, h->step_d.p, h->rs_off.p, h->rs_box.p,
+                                                     h->res_pts.p);
+    e = cudaGetLastError();
+    ++launches;
+    mark("sample");
+  }
   if (e == cudaSuccess && h->n_eval) {
     dk::Bufs bb = b;
     bb.counter = h->counters.p + 0;
@@ -330,8 +346,33 @@ int build_plan(dpinn* h) {
     int64_t c = ((target + P - 1) / P) * P;
     return std::min<int64_t>(std::max<int64_t>(c, P), 64LL * P);
   };
-  const int64_t cj = pick_chunk(res_off[nn], h->ks.P_train_jet, h->sched_jet);
-  const int64_t cv = pick_chunk(obs_off[nn] + 2 * n_face_pts, h->ks.P_val, h->sched_val);
+  int64_t cj = pick_chunk(res_off[nn], h->ks.P_train_jet, h->sched_jet);
+  int64_t cv = pick_chunk(obs_off[nn] + 2 * n_face_pts, h->ks.P_val, h->sched_val);
+  // Every training item owns one gradient partial of npp floats: enlarge the
+  // chunks until the partials fit the memory budget (at least one item per
+  // net and point set remains), so the number of points per step is not
+  // bounded by this memory.
+  {
+    auto n_slots = [&](int64_t a, int64_t b) {
+      int64_t n = 0;
+      for (int k = 0; k < nn; ++k) n += (h->res_counts[k] + a - 1) / a + (h->obs_counts[k] + b - 1) / b;
+      for (int f = 0; f < nf; ++f) n += (directed ? 1 : 2) * ((ifc_counts[f] + b - 1) / b);
+      return n;
+    };
+    const int64_t max_slots = std::max<int64_t>(1, h->part_budget / ((int64_t)h->npp * 4));
+    const int64_t PJ = h->ks.P_train_jet, PV = h->ks.P_val;
+    auto up = [](int64_t x, int64_t p) { return ((x + p - 1) / p) * p; };
+    const int64_t cap_j = up(std::max<int64_t>(res_off[nn], 1), PJ);
+    const int64_t cap_v = up(std::max<int64_t>(obs_off[nn] + n_face_pts, 1), PV);
+    // chunks only grow and stop at the caps, so the loop ends
+    while (n_slots(cj, cv) > max_slots) {
+      const int64_t nj = std::max(cj, std::min(up(cj * 2, PJ), cap_j));
+      const int64_t nv = std::max(cv, std::min(up(cv * 2, PV), cap_v));
+      if (nj == cj && nv == cv) break;
+      cj = nj;
+      cv = nv;
+    }
+  }
 
   std::vector<dk::Item> ij, iv, ie;
   std::vector<int> slot_begin(nn + 1, 0);
@@ -828,7 +869,10 @@ int dpinn_set_points(dpinn_t* h, int kind, const float* pts, const float* vals, 
   CK(h, cudaSetDevice(h->dev));
   std::vector<int64_t> cv(counts, counts + n_counts);
   std::vector<int64_t>* dst = kind == 0 ? &h->res_counts : (kind == 1 ? &h->obs_counts : &h->face_counts);
-  const bool same = h->have[kind] && *dst == cv;
+  // points delivered by the caller replace per-step resampling
+  const bool was_sampling = (kind == DPINN_POINTS_RESIDUAL) && h->resample;
+  if (was_sampling) h->resample = false;
+  const bool same = h->have[kind] && *dst == cv && !was_sampling;
   DevBuf<float>* pb = kind == 0 ? &h->res_pts : (kind == 1 ? &h->obs_pts : &h->face_pts);
   if (!same) {
     // the captured graphs reference the old buffers: drop them first
@@ -847,6 +891,76 @@ int dpinn_set_points(dpinn_t* h, int kind, const float* pts, const float* vals, 
     return build_plan(h);
   }
   if (same && h->plan_ok) return DPINN_OK;
+  return build_plan(h);
+}
+
+int dpinn_set_resampling(dpinn_t* h, const int64_t* counts, int n_counts, uint64_t seed) {
+  if (!h) return DPINN_ERR_INVALID_ARG;
+  if (!counts) {
+    if (h->resample) {
+      CK(h, cudaSetDevice(h->dev));
+      CK(h, cudaDeviceSynchronize());
+      h->resample = false;
+      h->plan_ok = false;
+      return build_plan(h);
+    }
+    return DPINN_OK;
+  }
+  if (n_counts != h->n_nets) return fail(h, DPINN_ERR_INVALID_ARG, "counts length mismatch");
+  int64_t n = 0, mx = 0;
+  for (int i = 0; i < n_counts; ++i) {
+    if (counts[i] < 0) return fail(h, DPINN_ERR_INVALID_ARG, "negative count");
+    n += counts[i];
+    mx = std::max<int64_t>(mx, counts[i]);
+  }
+  if (n > (int64_t)1 << 30) return fail(h, DPINN_ERR_INVALID_ARG, "too many points");
+  CK(h, cudaSetDevice(h->dev));
+  CK(h, cudaDeviceSynchronize());   // the captured graphs reference the old buffers
+  std::vector<long long> off(h->n_nets + 1, 0);
+  std::vector<double> box((size_t)h->n_nets * 8, 0.0);
+  for (int k = 0; k < h->n_nets; ++k) {
+    off[k + 1] = off[k] + counts[k];
+    for (int q = 0; q < h->din; ++q) {
+      box[(size_t)k * 8 + q] = h->blo[k][q];
+      box[(size_t)k * 8 + 4 + q] = h->bhi[k][q] - h->blo[k][q];
+    }
+  }
+  CK(h, h->rs_off.ensure(off.size()));
+  CK(h, cudaMemcpy(h->rs_off.p, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice));
+  CK(h, h->rs_box.ensure(box.size()));
+  CK(h, cudaMemcpy(h->rs_box.p, box.data(), box.size() * sizeof(double), cudaMemcpyHostToDevice));
+  CK(h, h->res_pts.ensure((size_t)std::max<int64_t>(n, 1) * h->din));
+  h->res_counts.assign(counts, counts + n_counts);
+  h->have[0] = true;
+  h->resample = true;
+  h->rs_seed = seed;
+  h->rs_max = mx;
+  h->plan_ok = false;
+  return build_plan(h);
+}
+
+int dpinn_get_points(dpinn_t* h, int kind, float* host_out) {
+  if (!h || !host_out) return DPINN_ERR_INVALID_ARG;
+  if (kind < 0 || kind > 2) return fail(h, DPINN_ERR_INVALID_ARG, "bad point kind");
+  if (!h->have[kind]) return fail(h, DPINN_ERR_STATE, "point set not present");
+  const std::vector<int64_t>& cnt = kind == 0 ? h->res_counts : (kind == 1 ? h->obs_counts : h->face_counts);
+  int64_t n = 0;
+  for (int64_t c : cnt) n += c;
+  const DevBuf<float>& pb = kind == 0 ? h->res_pts : (kind == 1 ? h->obs_pts : h->face_pts);
+  CK(h, cudaSetDevice(h->dev));
+  CK(h, cudaDeviceSynchronize());
+  if (n) CK(h, cudaMemcpy(host_out, pb.p, (size_t)n * h->din * sizeof(float), cudaMemcpyDeviceToHost));
+  return DPINN_OK;
+}
+
+int dpinn_set_partial_budget(dpinn_t* h, int64_t bytes) {
+  if (!h || bytes < 0) return DPINN_ERR_INVALID_ARG;
+  const int64_t b = bytes ? bytes : ((int64_t)1 << 30);
+  if (b == h->part_budget) return DPINN_OK;
+  CK(h, cudaSetDevice(h->dev));
+  CK(h, cudaDeviceSynchronize());
+  h->part_budget = b;
+  h->plan_ok = false;
   return build_plan(h);
 }
 
@@ -1180,9 +1294,9 @@ int dpinn_step_timed(dpinn_t* h, dpinn_stream_t stream, float* ms, int max_kerne
     if (!h->plan_ok) return fail(h, DPINN_ERR_STATE, "residual, observation and face points must be set first");
   }
   cudaStream_t s = (cudaStream_t)stream;
-  cudaEvent_t ev[9];
+  cudaEvent_t ev[12];   // at most 8 kernels per step
   for (auto& e : ev) CK(h, cudaEventCreate(&e));
-  const char* nm[8] = {nullptr};
+  const char* nm[11] = {nullptr};
   int launches = 0;
   cudaError_t e = enqueue_step(h, RUN_STEP, s, &launches, ev, nm);
   if (e == cudaSuccess) e = cudaEventRecord(h->done, s);

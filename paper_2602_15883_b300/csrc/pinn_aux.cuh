@@ -211,4 +211,38 @@ __global__ void k_init(const Shape sh, uint64_t seed, float* __restrict__ theta,
   theta[(size_t)k * sh.npp + j] = val;
 }
 
+// ---- per-step resampling of the collocation points --------------------
+// SplitMix64 (Steele, Lea and Flood, 2014): the n-th output (n = 1, 2, ...) of
+// the generator seeded with S is mix(S + n * gamma).  Streams: S_t = the
+// (t+1)-th output for the step seed, S_{t,k} = the (k+1)-th output of S_t for
+// net k; coordinate d of point i uses output i * d_in + d + 1 of S_{t,k}, whose
+// top 24 bits give u in [0, 1) exactly; x = lo + u * w in double (no fused
+// multiply-add), rounded to float32.
+__device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+constexpr uint64_t SM64_GAMMA = 0x9E3779B97F4A7C15ull;
+
+// grid.y = net; box[k] = {lo[4], w[4]} (double)
+__global__ void k_sample(int din, uint64_t seed, const long long* __restrict__ step,
+                         const long long* __restrict__ offsets, const double* __restrict__ box,
+                         float* __restrict__ pts) {
+  const int k = blockIdx.y;
+  const long long n = offsets[k + 1] - offsets[k];
+  const uint64_t st = sm64_mix(seed + (uint64_t)(*step + 1) * SM64_GAMMA);
+  const uint64_t sk = sm64_mix(st + (uint64_t)(k + 1) * SM64_GAMMA);
+  const double* lo = box + (size_t)k * 8;
+  const double* w = lo + 4;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float* out = pts + (offsets[k] + i) * din;
+    for (int d = 0; d < din; ++d) {
+      const uint64_t o = sm64_mix(sk + (uint64_t)(i * din + d + 1) * SM64_GAMMA);
+      const double u = (double)(o >> 40) * (1.0 / 16777216.0);
+      out[d] = __double2float_rn(__dadd_rn(lo[d], __dmul_rn(u, w[d])));
+    }
+  }
+}
+
 }  // namespace dk
