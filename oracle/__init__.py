@@ -39,7 +39,11 @@ class Config(C.Structure):
         ("clip", C.c_double),
         ("lr_decay_factor", C.c_double), ("lr_decay_interval", C.c_int), ("comm_interval", C.c_int),
         ("activation", C.c_int),
+        ("lam_gh_r", C.c_double), ("lam_gh_c1", C.c_double),
     ]
+
+
+NLOSS = 8   # obs, PDE, gh_u, gh_p space, gh_p time, total, gh_r (residual matching), gh_c1
 
 
 class ProblemC(C.Structure):
@@ -116,6 +120,8 @@ def make_config(cfg: dict) -> Config:
     c.lam_obs, c.lam_pde, c.lam_gh_u = cfg["lambda_obs"], cfg["lambda_pde"], cfg["lambda_gh_u"]
     c.lam_gh_p_space, c.lam_gh_p_time = cfg["lambda_gh_p_space"], cfg["lambda_gh_p_time"]
     c.lr, c.beta1, c.beta2, c.eps, c.clip = cfg["lr"], cfg["beta1"], cfg["beta2"], cfg["eps"], cfg["clip_norm"]
+    c.lam_gh_r = float(cfg.get("lambda_gh_r", 0.0))
+    c.lam_gh_c1 = float(cfg.get("lambda_gh_c1", 0.0))
     c.lr_decay_factor = float(cfg.get("lr_decay_factor", 1.0))
     c.lr_decay_interval = int(cfg.get("lr_decay_interval", 0))
     c.comm_interval = int(cfg.get("comm_interval", 1))
@@ -215,7 +221,7 @@ class Oracle:
 
     def losses(self, th):
         th = np.ascontiguousarray(th, np.float64)
-        out = np.zeros((self.n_nets, 6))
+        out = np.zeros((self.n_nets, NLOSS))
         lib().ora_losses(C.addressof(self.c), C.addressof(self.pc), _p(th), _p(out))
         return out
 
@@ -225,7 +231,7 @@ class Oracle:
         th = np.ascontiguousarray(th, np.float64)
         th_im = None if th_im is None else np.ascontiguousarray(th_im, np.float64)
         thA = None if thA is None else np.ascontiguousarray(thA, np.float64)
-        o_re, o_im = np.zeros(6), np.zeros(6)
+        o_re, o_im = np.zeros(NLOSS), np.zeros(NLOSS)
         lib().ora_net_loss_complex(C.addressof(self.c), C.addressof(self.pc), _p(th), net, _p(thA), _p(th_im),
                                    _p(o_re), _p(o_im))
         return o_re + 1j * o_im
@@ -234,7 +240,7 @@ class Oracle:
         th = np.ascontiguousarray(th, np.float64)
         nets = np.arange(self.n_nets, dtype=np.int32) if nets is None else np.ascontiguousarray(nets, np.int32)
         g = np.zeros((len(nets), self.n_params))
-        loss = np.zeros((len(nets), 6))
+        loss = np.zeros((len(nets), NLOSS))
         lib().ora_grad_nets(C.addressof(self.c), C.addressof(self.pc), _p(th), _p(nets), len(nets), _p(g), _p(loss))
         return g, loss
 
@@ -248,7 +254,7 @@ class Oracle:
     def step(self, th, m, v, t):
         th, m, v = (np.array(a, np.float64) for a in (th, m, v))
         tt = C.c_int64(int(t))
-        loss = np.zeros((self.n_nets, 6))
+        loss = np.zeros((self.n_nets, NLOSS))
         lib().ora_step(C.addressof(self.c), C.addressof(self.pc), _p(th), _p(m), _p(v), C.addressof(tt), _p(loss))
         return th, m, v, tt.value, loss
 
@@ -261,9 +267,11 @@ class Oracle:
             cache["val"] = np.zeros((max(n, 1), 2, self.d_out))
             cache["anc"] = np.zeros((max(n, 1), 2))
         tt = C.c_int64(int(t))
-        loss = np.zeros((self.n_nets, 6))
-        lib().ora_step_cached(C.addressof(self.c), C.addressof(self.pc), _p(th), _p(m), _p(v), C.addressof(tt),
+        loss = np.zeros((self.n_nets, NLOSS))
+        rc = lib().ora_step_cached(C.addressof(self.c), C.addressof(self.pc), _p(th), _p(m), _p(v), C.addressof(tt),
                               _p(loss), _p(cache["val"]), _p(cache["anc"]))
+        if rc:
+            raise ValueError("interface jet terms with a communication interval > 1 are not cached by the oracle")
         return th, m, v, tt.value, loss
 
     def sample(self, seed, t, counts):

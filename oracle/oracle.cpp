@@ -65,6 +65,10 @@ struct ora_config {
   int lr_decay_interval;    // 0: constant learning rate
   int comm_interval;        // Algorithm 1: messages refreshed when t mod I_comm == 0
   int activation;           // 0 tanh, 1 sin
+  // Interface terms beyond C0 (Remark, Sec. 2.2), 0 = off: residual matching
+  // sum_j (r_A - sg r_B)_j^2 and C1 matching sum_{c,q} (d_q Y_A,c - sg d_q Y_B,c)^2
+  // at the ghost points, divided by N_gh like Eqs. (13)-(14).
+  double lam_gh_r, lam_gh_c1;
 };
 
 struct ora_problem {
@@ -384,10 +388,27 @@ struct Prob {
 // for a master side (0 otherwise).
 struct Nbr {
   std::vector<double> val, anc;
+  // with the interface terms: the other side's residual [pt][2][d_s + 1]
+  // and first derivatives [pt][2][d_out][d_in]
+  std::vector<double> res, grd;
   // ghost mode: per ghost point, the owner net and its (u, p) and anchor p
+  // (and residual [pt][d_s + 1] and first derivatives [pt][d_out][d_in])
   std::vector<int> owner;
-  std::vector<double> gval, ganc;
+  std::vector<double> gval, ganc, gres, ggrd;
 };
+
+constexpr int NLOSS = 8;   // loss record: obs, PDE, gh_u, gh_p space, gh_p time, total, gh_r, gh_c1
+
+bool iface_jets(const Geo& g) { return g.cfg.lam_gh_r != 0.0 || g.cfg.lam_gh_c1 != 0.0; }
+
+// Residual and first derivatives of net `net` at x from its jets.
+void point_jets(const Geo& g, int net, const double* th, const double* x, double* r, double* grd) {
+  std::vector<double> Z((size_t)g.L * g.W * g.C), Y((size_t)g.dout * g.C);
+  forward(g, net, th, x, true, Z.data(), Y.data());
+  residual(g, Y.data(), r);
+  for (int c = 0; c < g.dout; ++c)
+    for (int q = 0; q < g.din; ++q) grd[c * g.din + q] = Y[c * g.C + 1 + q];
+}
 
 // Net whose cell holds x (float32 rule), -1 outside the domain.
 int route_fp32(const Geo& g, const double* x) {
@@ -426,6 +447,10 @@ Nbr exchange(const Prob& pb, const double* th_all, const std::vector<char>* need
     nb.owner.assign(n, -1);
     nb.gval.assign((size_t)n * g.dout, 0.0);
     nb.ganc.assign(n, 0.0);
+    if (iface_jets(g)) {
+      nb.gres.assign((size_t)n * (g.ds + 1), 0.0);
+      nb.ggrd.assign((size_t)n * g.dout * g.din, 0.0);
+    }
     std::vector<double> Zg((size_t)g.L * g.W), Yg(g.dout);
     for (int A = 0; A < g.n_nets; ++A) {
       if (need && !(*need)[A]) continue;
@@ -438,6 +463,8 @@ Nbr exchange(const Prob& pb, const double* th_all, const std::vector<char>* need
         const double* th = th_all + (size_t)B * g.n_params;
         forward(g, B, th, x, false, Zg.data(), Yg.data());
         for (int j = 0; j < g.dout; ++j) nb.gval[(size_t)i * g.dout + j] = Yg[j];
+        if (iface_jets(g))
+          point_jets(g, B, th, x, &nb.gres[(size_t)i * (g.ds + 1)], &nb.ggrd[(size_t)i * g.dout * g.din]);
         if (g.master[B]) {
           anchor_point(g, x, xa);
           nb.ganc[i] = value_p(g, B, th, xa);
@@ -449,6 +476,10 @@ Nbr exchange(const Prob& pb, const double* th_all, const std::vector<char>* need
   int64_t nf = pb.face_off.back();
   nb.val.assign((size_t)nf * 2 * g.dout, 0.0);
   nb.anc.assign((size_t)nf * 2, 0.0);
+  if (iface_jets(g)) {
+    nb.res.assign((size_t)nf * 2 * (g.ds + 1), 0.0);
+    nb.grd.assign((size_t)nf * 2 * g.dout * g.din, 0.0);
+  }
   std::vector<double> Z((size_t)g.L * g.W), Y(g.dout);
   for (int f = 0; f < g.n_faces; ++f) {
     if (need && !(*need)[g.face[f][0]] && !(*need)[g.face[f][1]]) continue;
@@ -460,6 +491,9 @@ Nbr exchange(const Prob& pb, const double* th_all, const std::vector<char>* need
         const double* th = th_all + (size_t)net * g.n_params;
         forward(g, net, th, x, false, Z.data(), Y.data());
         for (int j = 0; j < g.dout; ++j) nb.val[((size_t)i * 2 + side) * g.dout + j] = Y[j];
+        if (iface_jets(g))
+          point_jets(g, net, th, x, &nb.res[((size_t)i * 2 + side) * (g.ds + 1)],
+                     &nb.grd[((size_t)i * 2 + side) * g.dout * g.din]);
         if (g.master[net]) {  // Eq. (15): master sends p~ = p(x,t) - p(x_anc,t)
           anchor_point(g, x, xa);
           nb.anc[(size_t)i * 2 + side] = value_p(g, net, th, xa);
@@ -498,9 +532,26 @@ void ghost_target_vol(const Prob& pb, const Nbr& nb, int A, int64_t i, double* U
   *is_time = g.unst && same_space;
 }
 
+// The other side's residual and first derivatives at ghost point i (face
+// mode: face f, own side `side`; ghost mode: the owner of point i).
+void jet_targets(const Prob& pb, const Nbr& nb, bool ghost, int f_unused, int64_t i, int side, const double** rB,
+                 const double** gB) {
+  const Geo& g = pb.g;
+  (void)f_unused;
+  if (ghost) {
+    *rB = &nb.gres[(size_t)i * (g.ds + 1)];
+    *gB = &nb.ggrd[(size_t)i * g.dout * g.din];
+  } else {
+    const int other = 1 - side;
+    *rB = &nb.res[((size_t)i * 2 + other) * (g.ds + 1)];
+    *gB = &nb.grd[((size_t)i * 2 + other) * g.dout * g.din];
+  }
+}
+
 // Loss terms of net A at parameters thA (T = double or complex for the
 // complex-step pins): out = {L_obs, L_PDE, L_gh_u, L_gh_p^space,
-// L_gh_p^time, L_total}.  Eq. (3), Eq. (5), Eqs. (13)-(14), Eq. (16).
+// L_gh_p^time, L_total, L_gh_r, L_gh_c1}.  Eq. (3), Eq. (5), Eqs. (13)-(14),
+// Eq. (16), and the optional interface terms of the Remark in Sec. 2.2.
 template <class T>
 void net_loss(const Prob& pb, const Nbr& nb, int A, const T* thA, T* out) {
   const Geo& g = pb.g;
@@ -526,43 +577,67 @@ void net_loss(const Prob& pb, const Nbr& nb, int A, const T* thA, T* out) {
     }
   }
   int64_t ngh = pb.n_gh(A);
+  T lr = 0.0, lc1 = 0.0;
+  std::vector<T> rj(g.ds + 1);
+  // one ghost point: C0 terms (Eqs. (13)-(14)) and, when enabled, residual
+  // and C1 matching against the other side's jets
+  auto ghost_point = [&](const double* x, const double* U, double P, bool tm, const double* rB, const double* gB) {
+    const bool jets = iface_jets(g);
+    if (jets) forward(g, A, thA, x, true, Z.data(), Y.data());
+    else forward(g, A, thA, x, false, Zv.data(), Yv.data());
+    const int st = jets ? g.C : 1;
+    const T* Yc = jets ? Y.data() : Yv.data();
+    for (int c = 0; c < g.ds; ++c) {
+      T e = Yc[c * st] - U[c];
+      lgu += g.cfg.comp_w[c] * e * e;
+    }
+    T ep = Yc[g.ds * st] - P;
+    if (tm) ltm += ep * ep; else lsp += ep * ep;
+    if (jets) {
+      residual(g, Y.data(), rj.data());
+      for (int j = 0; j <= g.ds; ++j) {
+        T d = rj[j] - rB[j];
+        lr += d * d;
+      }
+      for (int c = 0; c < g.dout; ++c)
+        for (int q = 0; q < g.din; ++q) {
+          T d = Y[c * g.C + 1 + q] - gB[c * g.din + q];
+          lc1 += d * d;
+        }
+    }
+  };
   for (auto& fs : g.net_faces[A]) {
     if (pb.ghost_mode()) break;
     int f = fs.first, side = fs.second;
     for (int64_t i = pb.face_off[f]; i < pb.face_off[f + 1]; ++i) {
       double x[4], U[3], P;
+      const double *rB = nullptr, *gB = nullptr;
       pb.face_x(i, x);
       ghost_target(pb, nb, f, i, side, U, &P);
-      forward(g, A, thA, x, false, Zv.data(), Yv.data());
-      for (int c = 0; c < g.ds; ++c) {
-        T e = Yv[c] - U[c];
-        lgu += g.cfg.comp_w[c] * e * e;
-      }
-      T ep = Yv[g.ds] - P;
-      if (g.face_is_time(f)) ltm += ep * ep; else lsp += ep * ep;
+      if (iface_jets(g)) jet_targets(pb, nb, false, f, i, side, &rB, &gB);
+      ghost_point(x, U, P, g.face_is_time(f), rB, gB);
     }
   }
   if (pb.ghost_mode())
     for (int64_t i = pb.ghost_off[A]; i < pb.ghost_off[A + 1]; ++i) {
       double x[4], U[3], P;
       bool tm;
+      const double *rB = nullptr, *gB = nullptr;
       pb.ghost_x(i, x);
       ghost_target_vol(pb, nb, A, i, U, &P, &tm);
-      forward(g, A, thA, x, false, Zv.data(), Yv.data());
-      for (int c = 0; c < g.ds; ++c) {
-        T e = Yv[c] - U[c];
-        lgu += g.cfg.comp_w[c] * e * e;
-      }
-      T ep = Yv[g.ds] - P;
-      if (tm) ltm += ep * ep; else lsp += ep * ep;
+      if (iface_jets(g)) jet_targets(pb, nb, true, 0, i, 0, &rB, &gB);
+      ghost_point(x, U, P, tm, rB, gB);
     }
   out[0] = nobs ? lobs / (double)nobs : T(0.0);
   out[1] = npde ? lpde / (double)npde : T(0.0);
   out[2] = ngh ? lgu / (double)ngh : T(0.0);
   out[3] = ngh ? lsp / (double)ngh : T(0.0);
   out[4] = ngh ? ltm / (double)ngh : T(0.0);
+  out[6] = ngh ? lr / (double)ngh : T(0.0);
+  out[7] = ngh ? lc1 / (double)ngh : T(0.0);
   out[5] = g.cfg.lam_obs * out[0] + g.cfg.lam_pde * out[1] + g.cfg.lam_gh_u * out[2] +
-           lam_space(g, A) * out[3] + g.cfg.lam_gh_p_time * out[4];
+           lam_space(g, A) * out[3] + g.cfg.lam_gh_p_time * out[4] + g.cfg.lam_gh_r * out[6] +
+           g.cfg.lam_gh_c1 * out[7];
 }
 
 // Hand-written gradient of L_A with respect to theta_A (neighbour values are
@@ -588,7 +663,7 @@ void net_grad(const Prob& pb, const Nbr& nb, int A, const double* thA, double* g
   }
   int T = std::max(1, g_threads);
   std::vector<std::vector<double>> gbuf(T, std::vector<double>(g.n_params, 0.0));
-  std::vector<std::array<double, 5>> lbuf(T, {0, 0, 0, 0, 0});
+  std::vector<std::array<double, 7>> lbuf(T, {0, 0, 0, 0, 0, 0, 0});
   auto work = [&](int t) {
     size_t n = items.size();
     size_t b = n * t / T, e = n * (t + 1) / T;
@@ -620,6 +695,7 @@ void net_grad(const Prob& pb, const Nbr& nb, int A, const double* thA, double* g
       } else {
         double U[3], P;
         bool tm;
+        const double *rB = nullptr, *gB = nullptr;
         if (w.kind == 2) {
           pb.face_x(w.i, x);
           ghost_target(pb, nb, w.f, w.i, w.side, U, &P);
@@ -628,17 +704,37 @@ void net_grad(const Prob& pb, const Nbr& nb, int A, const double* thA, double* g
           pb.ghost_x(w.i, x);
           ghost_target_vol(pb, nb, A, w.i, U, &P, &tm);
         }
-        forward(g, A, thA, x, false, Z.data(), Y.data());
+        const bool jets = iface_jets(g);
+        if (jets) jet_targets(pb, nb, w.kind == 3, w.f, w.i, w.side, &rB, &gB);
+        forward(g, A, thA, x, jets, Z.data(), Y.data());
+        const int st = jets ? g.C : 1;   // value channel stride
         for (int c = 0; c < g.ds; ++c) {
-          double e_ = Y[c] - U[c];
+          double e_ = Y[c * st] - U[c];
           lbuf[t][2] += g.cfg.comp_w[c] * e_ * e_;
-          Yb[c] = 2.0 * g.cfg.lam_gh_u * g.cfg.comp_w[c] * e_ / (double)ngh;
+          Yb[c * st] = 2.0 * g.cfg.lam_gh_u * g.cfg.comp_w[c] * e_ / (double)ngh;
         }
-        double ep = Y[g.ds] - P;
+        double ep = Y[g.ds * st] - P;
         lbuf[t][tm ? 4 : 3] += ep * ep;
         double lam = tm ? g.cfg.lam_gh_p_time : lam_space(g, A);
-        Yb[g.ds] = 2.0 * lam * ep / (double)ngh;
-        backward(g, A, thA, x, false, Z.data(), Yb.data(), gbuf[t].data());
+        Yb[g.ds * st] = 2.0 * lam * ep / (double)ngh;
+        if (jets) {
+          // residual matching: d/dY of lam_r / N_gh sum_j (r_j - rB_j)^2
+          residual(g, Y.data(), r);
+          for (int j = 0; j <= g.ds; ++j) {
+            const double d = r[j] - rB[j];
+            lbuf[t][5] += d * d;
+            rb[j] = 2.0 * g.cfg.lam_gh_r * d / (double)ngh;
+          }
+          residual_adjoint(g, Y.data(), rb, Yb.data());
+          // C1 matching on every first derivative of every output
+          for (int c = 0; c < g.dout; ++c)
+            for (int q = 0; q < g.din; ++q) {
+              const double d = Y[c * g.C + 1 + q] - gB[c * g.din + q];
+              lbuf[t][6] += d * d;
+              Yb[c * g.C + 1 + q] += 2.0 * g.cfg.lam_gh_c1 * d / (double)ngh;
+            }
+        }
+        backward(g, A, thA, x, jets, Z.data(), Yb.data(), gbuf[t].data());
       }
     }
   };
@@ -649,10 +745,10 @@ void net_grad(const Prob& pb, const Nbr& nb, int A, const double* thA, double* g
     for (auto& x : th) x.join();
   }
   std::fill(grad, grad + g.n_params, 0.0);
-  double l[5] = {0, 0, 0, 0, 0};
+  double l[7] = {0, 0, 0, 0, 0, 0, 0};
   for (int t = 0; t < T; ++t) {
     for (int j = 0; j < g.n_params; ++j) grad[j] += gbuf[t][j];
-    for (int q = 0; q < 5; ++q) l[q] += lbuf[t][q];
+    for (int q = 0; q < 7; ++q) l[q] += lbuf[t][q];
   }
   if (loss) {
     loss[0] = nobs ? l[0] / nobs : 0.0;
@@ -660,8 +756,11 @@ void net_grad(const Prob& pb, const Nbr& nb, int A, const double* thA, double* g
     loss[2] = ngh ? l[2] / ngh : 0.0;
     loss[3] = ngh ? l[3] / ngh : 0.0;
     loss[4] = ngh ? l[4] / ngh : 0.0;
+    loss[6] = ngh ? l[5] / ngh : 0.0;
+    loss[7] = ngh ? l[6] / ngh : 0.0;
     loss[5] = g.cfg.lam_obs * loss[0] + g.cfg.lam_pde * loss[1] + g.cfg.lam_gh_u * loss[2] +
-              lam_space(g, A) * loss[3] + g.cfg.lam_gh_p_time * loss[4];
+              lam_space(g, A) * loss[3] + g.cfg.lam_gh_p_time * loss[4] + g.cfg.lam_gh_r * loss[6] +
+              g.cfg.lam_gh_c1 * loss[7];
   }
 }
 
@@ -832,12 +931,12 @@ int ora_exchange(const ora_config* c, const ora_problem* p, const double* th, do
   return 0;
 }
 
-// Loss record [n_nets][6] by direct evaluation (no derivatives of theta).
+// Loss record [n_nets][8] by direct evaluation (no derivatives of theta).
 int ora_losses(const ora_config* c, const ora_problem* p, const double* th, double* out) {
   Geo g(*c);
   Prob pb(g, *p);
   Nbr nb = exchange(pb, th);
-  for (int k = 0; k < g.n_nets; ++k) net_loss<double>(pb, nb, k, th + (size_t)k * g.n_params, out + k * 6);
+  for (int k = 0; k < g.n_nets; ++k) net_loss<double>(pb, nb, k, th + (size_t)k * g.n_params, out + k * NLOSS);
   return 0;
 }
 
@@ -845,7 +944,7 @@ int ora_losses(const ora_config* c, const ora_problem* p, const double* th, doub
 // messages computed from the real parameters th (held constant, as the
 // paper's cached neighbour values).  Serves both the complex-step pins
 // (thA_im = perturbation) and central differences (thA_re shifted).
-// out_re/out_im [6].
+// out_re/out_im [8].
 int ora_net_loss_complex(const ora_config* c, const ora_problem* p, const double* th, int A,
                          const double* thA_re, const double* thA_im, double* out_re, double* out_im) {
   Geo g(*c);
@@ -854,14 +953,14 @@ int ora_net_loss_complex(const ora_config* c, const ora_problem* p, const double
   std::vector<cplx> thA(g.n_params);
   for (int j = 0; j < g.n_params; ++j)
     thA[j] = cplx(thA_re ? thA_re[j] : th[(size_t)A * g.n_params + j], thA_im ? thA_im[j] : 0.0);
-  cplx out[6];
+  cplx out[NLOSS];
   net_loss<cplx>(pb, nb, A, thA.data(), out);
-  for (int q = 0; q < 6; ++q) { out_re[q] = out[q].real(); out_im[q] = out[q].imag(); }
+  for (int q = 0; q < NLOSS; ++q) { out_re[q] = out[q].real(); out_im[q] = out[q].imag(); }
   return 0;
 }
 
 // Gradient (hand-written reverse pass) and loss record for the selected nets:
-// grad [n_sel][n_params], loss [n_sel][6].
+// grad [n_sel][n_params], loss [n_sel][8].
 int ora_grad_nets(const ora_config* c, const ora_problem* p, const double* th, const int* nets,
                   int n_sel, double* grad, double* loss) {
   Geo g(*c);
@@ -871,7 +970,7 @@ int ora_grad_nets(const ora_config* c, const ora_problem* p, const double* th, c
   Nbr nb = exchange(pb, th, &need);
   for (int s = 0; s < n_sel; ++s) {
     int A = nets[s];
-    net_grad(pb, nb, A, th + (size_t)A * g.n_params, grad + (size_t)s * g.n_params, loss ? loss + s * 6 : nullptr);
+    net_grad(pb, nb, A, th + (size_t)A * g.n_params, grad + (size_t)s * g.n_params, loss ? loss + s * NLOSS : nullptr);
   }
   return 0;
 }
@@ -893,7 +992,7 @@ int ora_adam(const ora_config* c, double* th, double* m, double* v, int64_t* t, 
 
 // One full training iteration of Algorithm 1 with I_comm = 1: exchange,
 // losses and gradients at the current parameters, then the optimiser step.
-// loss [n_nets][6] holds the pre-update losses.
+// loss [n_nets][8] holds the pre-update losses.
 int ora_step(const ora_config* c, const ora_problem* p, double* th, double* m, double* v,
              int64_t* t, double* loss) {
   Geo g(*c);
@@ -915,6 +1014,7 @@ int ora_step_cached(const ora_config* c, const ora_problem* p, double* th, doubl
   Prob pb(g, *p);
   Nbr nb;
   const int64_t nf = pb.face_off.back();
+  if (iface_jets(g) && c->comm_interval > 1) return -2;   // the cache holds values only
   if (c->comm_interval <= 1 || (*t % c->comm_interval) == 0) {
     nb = exchange(pb, th);
     std::copy(nb.val.begin(), nb.val.end(), val);
@@ -925,7 +1025,7 @@ int ora_step_cached(const ora_config* c, const ora_problem* p, double* th, doubl
   }
   std::vector<double> grad((size_t)g.n_nets * g.n_params);
   for (int k = 0; k < g.n_nets; ++k)
-    net_grad(pb, nb, k, th + (size_t)k * g.n_params, grad.data() + (size_t)k * g.n_params, loss ? loss + k * 6 : nullptr);
+    net_grad(pb, nb, k, th + (size_t)k * g.n_params, grad.data() + (size_t)k * g.n_params, loss ? loss + k * NLOSS : nullptr);
   *t += 1;
   adam(g, th, m, v, *t, grad.data());
   return 0;
