@@ -124,6 +124,18 @@ typedef struct dpinn_config {
    * are recomputed before step t (t = 0, 1, ... counted before the update)
    * when t mod I_comm == 0 and reused (stale) otherwise.  1 = every step. */
   int comm_interval;
+  /* Interface terms beyond C0 continuity (the Remark of Sec. 2.2; the paper
+   * leaves them off, 0 = off): residual matching
+   *   L_gh_r  = (1/N_gh) sum_ghost ||r_A(x) - sg(r_B(x))||^2  (r: Eqs. (7)-(10))
+   * and first-derivative (C1) matching
+   *   L_gh_c1 = (1/N_gh) sum_ghost sum_{c,q} (d_q Y_A,c - sg(d_q Y_B,c))^2
+   * over every output c (velocity and pressure) and input q, with B the net
+   * on the other side (face points) or owning the point (ghost layers);
+   * added to L_total with these weights.  Both depend on derivatives only,
+   * so no anchor normalisation enters.  When either is > 0 the exchange
+   * evaluates jets at the ghost points and the face items train in the FP32
+   * jet kernel. */
+  double lambda_gh_r, lambda_gh_c1;
 } dpinn_config;
 
 typedef struct dpinn_layout {
@@ -231,6 +243,10 @@ int dpinn_set_params(dpinn_t* h, const float* params);
  * [n_nets][6].  Errors: NONFINITE (a loss is NaN/Inf; host_out still
  * filled), TIMEOUT (a device wait gave up), CUDA. */
 int dpinn_loss(dpinn_t* h, float* host_out);
+
+/* As dpinn_loss with the 8-entry record [n_nets][8]: the 6 entries above
+ * (the total includes the interface terms), then L_gh_r and L_gh_c1. */
+int dpinn_loss_ext(dpinn_t* h, float* host_out);
 
 /* Gradient of the most recent step or dpinn_eval_grad (before clipping),
  * out [n_nets][n_params] in the parameter-block order (host or device

@@ -29,7 +29,7 @@ EXPORTS = (
     "dpinn_apply_grad", "dpinn_launches_per_step", "dpinn_step_timed", "dpinn_query_static",
     "dpinn_eval_loss", "dpinn_set_params", "dpinn_set_schedule", "dpinn_get_schedule",
     "dpinn_qctx_create", "dpinn_qctx_destroy", "dpinn_qctx_query", "dpinn_qctx_status",
-    "dpinn_set_resampling", "dpinn_get_points", "dpinn_set_partial_budget",
+    "dpinn_set_resampling", "dpinn_get_points", "dpinn_set_partial_budget", "dpinn_loss_ext",
 )
 
 
@@ -52,6 +52,7 @@ class Config(C.Structure):
         ("clip_norm", C.c_double),
         ("seed", C.c_uint64), ("precision", C.c_int), ("device", C.c_int),
         ("lr_decay_factor", C.c_double), ("lr_decay_interval", C.c_int), ("comm_interval", C.c_int),
+        ("lambda_gh_r", C.c_double), ("lambda_gh_c1", C.c_double),
     ]
 
 
@@ -104,6 +105,7 @@ def load_library(path: str = LIB_PATH):
         "dpinn_set_resampling": ([vp, vp, i32, C.c_uint64], i32),
         "dpinn_get_points": ([vp, i32, vp], i32),
         "dpinn_set_partial_budget": ([vp, i64], i32),
+        "dpinn_loss_ext": ([vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -137,6 +139,8 @@ def make_config(cfg: dict) -> Config:
     c.lr_decay_factor = float(cfg.get("lr_decay_factor", 1.0))
     c.lr_decay_interval = int(cfg.get("lr_decay_interval", 0))
     c.comm_interval = int(cfg.get("comm_interval", 1))
+    c.lambda_gh_r = float(cfg.get("lambda_gh_r", 0.0))
+    c.lambda_gh_c1 = float(cfg.get("lambda_gh_c1", 0.0))
     return c
 
 
@@ -280,6 +284,15 @@ class Dpinn:
     def loss(self, check=True):
         out = np.zeros((self.n_nets, 6), np.float32)
         rc = self.lib.dpinn_loss(self.h, out.ctypes.data)
+        if check:
+            self._check(rc)
+        return out
+
+    def loss_ext(self, check=True):
+        """Loss record with the interface terms: [n_nets][8] (L_obs, L_PDE,
+        L_gh_u, L_gh_p space, L_gh_p time, L_total, L_gh_r, L_gh_c1)."""
+        out = np.zeros((self.n_nets, 8), np.float32)
+        rc = self.lib.dpinn_loss_ext(self.h, out.ctypes.data)
         if check:
             self._check(rc)
         return out

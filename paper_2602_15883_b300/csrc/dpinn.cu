@@ -103,10 +103,12 @@ struct dpinn {
   std::vector<std::array<int, 3>> seg;
   std::vector<int64_t> seg_counts;
   // plan
-  DevBuf<dk::Item> items_eval, items_jet, items_val;
-  int n_eval = 0, n_jet = 0, n_val = 0, n_slots = 0;
-  int grid_eval = 0, grid_jet = 0, grid_val = 0;
-  DevBuf<float> grad_part, stash, nbr_val, nbr_anc, loss_rec;
+  DevBuf<dk::Item> items_eval, items_jet, items_val, items_jf;
+  int n_eval = 0, n_jet = 0, n_val = 0, n_jf = 0, n_slots = 0;
+  int grid_eval = 0, grid_jet = 0, grid_val = 0, grid_jf = 0;
+  // interface residual / C1 terms on (face items train with jets)
+  bool iface = false;
+  DevBuf<float> grad_part, stash, nbr_val, nbr_anc, nbr_res, nbr_grd, loss_rec;
   DevBuf<double> loss_part;
   float* loss_host = nullptr;
   bool plan_ok = false;
@@ -127,7 +129,7 @@ struct dpinn {
     if (cap) cudaStreamDestroy(cap);
     if (loss_host) cudaFreeHost(loss_host);
     for (auto* b : {&theta, &thetaT, &m, &v, &grad, &norm_part, &coef, &res_pts, &obs_pts, &obs_vals, &face_pts,
-                    &grad_part, &stash, &nbr_val, &nbr_anc, &loss_rec})
+                    &grad_part, &stash, &nbr_val, &nbr_anc, &nbr_res, &nbr_grd, &loss_rec})
       b->free_();
     step_d.free_(); nets_d.free_(); loss_part.free_();
     for (auto* b : {&face_info_d, &err_d, &counters, &n_items_d, &slot_begin_d, &iota_d, &q_net, &q_perm,
@@ -170,6 +172,8 @@ dk::Bufs make_bufs(dpinn* h) {
   b.face_info = h->face_info_d.p;
   b.nbr_val = h->nbr_val.p;
   b.nbr_anc = h->nbr_anc.p;
+  b.nbr_res = h->nbr_res.p;
+  b.nbr_grd = h->nbr_grd.p;
   b.grad_part = h->grad_part.p;
   b.loss_part = h->loss_part.p;
   b.stash = h->stash.p;
@@ -232,7 +236,12 @@ cudaError_t enqueue_step(dpinn* h, int mode, cudaStream_t s, int* n_launch, cuda
   if (e == cudaSuccess && h->n_eval) {
     dk::Bufs bb = b;
     bb.counter = h->counters.p + 0;
-    e = launch_pinn(h->ks.eval_val, h->grid_eval, h->ks.smem_val, h->shape, bb, h->items_eval.p, h->n_items_d.p + 0, s);
+    if (h->iface)   // the messages include the residual and first derivatives
+      e = launch_pinn(h->ks.eval_jet, h->grid_eval, h->ks.smem_jet, h->shape, bb, h->items_eval.p, h->n_items_d.p + 0,
+                      s);
+    else
+      e = launch_pinn(h->ks.eval_val, h->grid_eval, h->ks.smem_val, h->shape, bb, h->items_eval.p, h->n_items_d.p + 0,
+                      s);
     ++launches;
     mark("exchange");
   }
@@ -245,6 +254,14 @@ cudaError_t enqueue_step(dpinn* h, int mode, cudaStream_t s, int* n_launch, cuda
                     h->n_items_d.p + 1, s, h->ks.threads_train_jet);
     ++launches;
     mark("train_jet");
+  }
+  if (e == cudaSuccess && h->n_jf) {   // face items with the interface jet terms (FP32 jet kernel)
+    dk::Bufs bb = b;
+    bb.counter = h->counters.p + 3;
+    bb.stash_per_cta = h->ks.stash_jet;
+    e = launch_pinn(h->ks.train_jet, h->grid_jf, h->ks.smem_jet, h->shape, bb, h->items_jf.p, h->n_items_d.p + 3, s);
+    ++launches;
+    mark("train_face_jets");
   }
   if (e == cudaSuccess && h->n_val) {
     dk::Bufs bb = b;
@@ -374,7 +391,7 @@ int build_plan(dpinn* h) {
     }
   }
 
-  std::vector<dk::Item> ij, iv, ie;
+  std::vector<dk::Item> ij, iv, ie, ijf;
   std::vector<int> slot_begin(nn + 1, 0);
   std::vector<dk::NetInfo> ni(nn);
   int slot = 0;
@@ -391,7 +408,7 @@ int build_plan(dpinn* h) {
       const int f = fs.first, side = fs.second;
       ngh += ifc_counts[f];
       chunks(face_off[f], ifc_counts[f], cv, [&](int64_t b, int64_t c) {
-        iv.push_back({dk::K_FACE, k, (int)b, (int)c, slot++, f, side, 0});
+        (h->iface ? ijf : iv).push_back({dk::K_FACE, k, (int)b, (int)c, slot++, f, side, 0});
       });
     }
     dk::NetInfo& n = ni[k];
@@ -435,31 +452,43 @@ int build_plan(dpinn* h) {
   h->n_jet = (int)ij.size();
   h->n_val = (int)iv.size();
   h->n_eval = (int)ie.size();
+  h->n_jf = (int)ijf.size();
 
   const int occ_j = occupancy(h->ks.train_jet_run, h->ks.smem_train_jet, h->ks.threads_train_jet);
   const int occ_v = occupancy(h->ks.train_val, h->ks.smem_val);
   h->grid_jet = (int)std::min<int64_t>(h->n_jet, (int64_t)h->n_sms * occ_j);
   h->grid_val = (int)std::min<int64_t>(h->n_val, (int64_t)h->n_sms * occ_v);
-  h->grid_eval = (int)std::min<int64_t>(h->n_eval, (int64_t)h->n_sms * occ_v);
+  const int occ_e = h->iface ? occupancy(h->ks.eval_jet, h->ks.smem_jet) : occ_v;
+  h->grid_eval = (int)std::min<int64_t>(h->n_eval, (int64_t)h->n_sms * occ_e);
+  const int occ_f = occupancy(h->ks.train_jet, h->ks.smem_jet);
+  h->grid_jf = (int)std::min<int64_t>(h->n_jf, (int64_t)h->n_sms * occ_f);
 
   CK(h, h->items_jet.ensure(ij.size()));
   CK(h, h->items_val.ensure(iv.size()));
   CK(h, h->items_eval.ensure(ie.size()));
+  CK(h, h->items_jf.ensure(ijf.size()));
+  if (!ijf.empty())
+    CK(h, cudaMemcpy(h->items_jf.p, ijf.data(), ijf.size() * sizeof(dk::Item), cudaMemcpyHostToDevice));
   if (!ij.empty()) CK(h, cudaMemcpy(h->items_jet.p, ij.data(), ij.size() * sizeof(dk::Item), cudaMemcpyHostToDevice));
   if (!iv.empty()) CK(h, cudaMemcpy(h->items_val.p, iv.data(), iv.size() * sizeof(dk::Item), cudaMemcpyHostToDevice));
   if (!ie.empty()) CK(h, cudaMemcpy(h->items_eval.p, ie.data(), ie.size() * sizeof(dk::Item), cudaMemcpyHostToDevice));
-  int nitems[3] = {h->n_eval, h->n_jet, h->n_val};
+  int nitems[4] = {h->n_eval, h->n_jet, h->n_val, h->n_jf};
   CK(h, cudaMemcpy(h->n_items_d.p, nitems, sizeof(nitems), cudaMemcpyHostToDevice));
   CK(h, h->slot_begin_d.ensure(nn + 1));
   CK(h, cudaMemcpy(h->slot_begin_d.p, slot_begin.data(), (nn + 1) * sizeof(int), cudaMemcpyHostToDevice));
   CK(h, cudaMemcpy(h->nets_d.p, ni.data(), nn * sizeof(dk::NetInfo), cudaMemcpyHostToDevice));
   CK(h, h->grad_part.ensure((size_t)std::max(slot, 1) * h->npp));
-  CK(h, h->loss_part.ensure((size_t)std::max(slot, 1) * 5));
-  CK(h, cudaMemset(h->loss_part.p, 0, (size_t)std::max(slot, 1) * 5 * sizeof(double)));
-  const size_t st = std::max((size_t)h->grid_jet * h->ks.stash_train_jet, (size_t)h->grid_val * h->ks.stash_val);
+  CK(h, h->loss_part.ensure((size_t)std::max(slot, 1) * dk::LP));
+  CK(h, cudaMemset(h->loss_part.p, 0, (size_t)std::max(slot, 1) * dk::LP * sizeof(double)));
+  const size_t st = std::max({(size_t)h->grid_jet * h->ks.stash_train_jet, (size_t)h->grid_val * h->ks.stash_val,
+                              (size_t)h->grid_jf * h->ks.stash_jet});
   CK(h, h->stash.ensure(std::max<size_t>(st, 4)));
   CK(h, h->nbr_val.ensure((size_t)std::max<int64_t>(n_face_pts, 1) * 2 * h->dout));
   CK(h, h->nbr_anc.ensure((size_t)std::max<int64_t>(n_face_pts, 1) * 2));
+  if (h->iface) {
+    CK(h, h->nbr_res.ensure((size_t)std::max<int64_t>(n_face_pts, 1) * 2 * (h->ds + 1)));
+    CK(h, h->nbr_grd.ensure((size_t)std::max<int64_t>(n_face_pts, 1) * 2 * h->dout * h->din));
+  }
   CK(h, cudaMemset(h->nbr_anc.p, 0, (size_t)std::max<int64_t>(n_face_pts, 1) * 2 * sizeof(float)));
   int rc = capture(h, RUN_STEP, &h->g_step);
   if (rc) return rc;
@@ -580,6 +609,7 @@ int dpinn_config_default(dpinn_config* c) {
   c->lr_decay_factor = 1.0;
   c->lr_decay_interval = 0;
   c->comm_interval = 1;
+  c->lambda_gh_r = c->lambda_gh_c1 = 0.0;
   return DPINN_OK;
 }
 
@@ -601,6 +631,8 @@ int dpinn_create(const dpinn_config* cfg, dpinn_t** out) {
     return fail(nullptr, DPINN_ERR_INVALID_ARG, "TF32x3 tensor-core kernels need width 128");
   if (!(c.nu >= 0)) return fail(nullptr, DPINN_ERR_INVALID_ARG, "nu must be >= 0");
   if (c.comm_interval < 1) return fail(nullptr, DPINN_ERR_INVALID_ARG, "comm_interval must be >= 1");
+  if (!(c.lambda_gh_r >= 0.0) || !(c.lambda_gh_c1 >= 0.0))
+    return fail(nullptr, DPINN_ERR_INVALID_ARG, "interface weights must be >= 0");
   if (c.lr_decay_interval < 0 || !(c.lr_decay_factor > 0))
     return fail(nullptr, DPINN_ERR_INVALID_ARG, "bad learning-rate decay");
   const int din = c.d_space + c.unsteady;
@@ -687,6 +719,9 @@ int dpinn_create(const dpinn_config* cfg, dpinn_t** out) {
   for (int a = 0; a < 3; ++a) { sh.anchor[a] = (float)c.anchor_x[a]; sh.comp_w[a] = (float)c.comp_w[a]; }
   sh.lam_obs = (float)c.lambda_obs; sh.lam_pde = (float)c.lambda_pde; sh.lam_gh_u = (float)c.lambda_gh_u;
   sh.lam_time = (float)c.lambda_gh_p_time;
+  sh.lam_gh_r = (float)c.lambda_gh_r;
+  sh.lam_gh_c1 = (float)c.lambda_gh_c1;
+  h->iface = (c.lambda_gh_r != 0.0 || c.lambda_gh_c1 != 0.0);
 
   dpinn* hp = h.get();
   CK(hp, cudaSetDevice(c.device));
@@ -694,6 +729,7 @@ int dpinn_create(const dpinn_config* cfg, dpinn_t** out) {
   CK(hp, cudaDeviceGetAttribute(&h->n_sms, cudaDevAttrMultiProcessorCount, c.device));
   for (const void* fn : {h->ks.train_jet, h->ks.query_jet})
     CK(hp, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ks.smem_jet));
+  CK(hp, cudaFuncSetAttribute(h->ks.eval_jet, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ks.smem_jet));
   if (h->ks.train_jet_run != h->ks.train_jet)
     CK(hp, cudaFuncSetAttribute(h->ks.train_jet_run, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)h->ks.smem_train_jet));
@@ -709,14 +745,14 @@ int dpinn_create(const dpinn_config* cfg, dpinn_t** out) {
   CK(hp, h->nets_d.ensure(h->n_nets));
   CK(hp, h->face_info_d.ensure((size_t)std::max(h->n_faces, 1) * 3));
   CK(hp, h->err_d.ensure(4)); CK(hp, h->counters.ensure(4)); CK(hp, h->n_items_d.ensure(4));
-  CK(hp, h->loss_rec.ensure((size_t)h->n_nets * 6));
+  CK(hp, h->loss_rec.ensure((size_t)h->n_nets * 8));
   CK(hp, h->iota_d.ensure(h->n_nets + 1));
-  CK(hp, cudaMallocHost(&h->loss_host, (size_t)h->n_nets * 6 * sizeof(float)));
+  CK(hp, cudaMallocHost(&h->loss_host, (size_t)h->n_nets * 8 * sizeof(float)));
   CK(hp, cudaMemset(h->theta.p, 0, NP * 4)); CK(hp, cudaMemset(h->m.p, 0, NP * 4));
   CK(hp, cudaMemset(h->v.p, 0, NP * 4)); CK(hp, cudaMemset(h->grad.p, 0, NP * 4));
   CK(hp, cudaMemset(h->step_d.p, 0, sizeof(long long)));
   CK(hp, cudaMemset(h->err_d.p, 0, 4 * sizeof(int)));
-  CK(hp, cudaMemset(h->loss_rec.p, 0, (size_t)h->n_nets * 6 * sizeof(float)));
+  CK(hp, cudaMemset(h->loss_rec.p, 0, (size_t)h->n_nets * 8 * sizeof(float)));
   CK(hp, cudaMemset(h->coef.p, 0, (size_t)h->n_nets * sizeof(float)));
   std::vector<int> fi((size_t)std::max(h->n_faces, 1) * 3, 0);
   for (int f = 0; f < h->n_faces; ++f) {
@@ -1035,7 +1071,16 @@ int dpinn_set_params(dpinn_t* h, const float* params) {
 int dpinn_loss(dpinn_t* h, float* host_out) {
   if (!h || !host_out) return DPINN_ERR_INVALID_ARG;
   CK(h, cudaEventSynchronize(h->done));
-  CK(h, cudaMemcpy(host_out, h->loss_rec.p, (size_t)h->n_nets * 6 * sizeof(float), cudaMemcpyDeviceToHost));
+  // the first 6 of the 8 entries per net
+  CK(h, cudaMemcpy2D(host_out, 6 * sizeof(float), h->loss_rec.p, 8 * sizeof(float), 6 * sizeof(float), h->n_nets,
+                     cudaMemcpyDeviceToHost));
+  return check_errors(h);
+}
+
+int dpinn_loss_ext(dpinn_t* h, float* host_out) {
+  if (!h || !host_out) return DPINN_ERR_INVALID_ARG;
+  CK(h, cudaEventSynchronize(h->done));
+  CK(h, cudaMemcpy(host_out, h->loss_rec.p, (size_t)h->n_nets * 8 * sizeof(float), cudaMemcpyDeviceToHost));
   return check_errors(h);
 }
 

@@ -10,6 +10,7 @@ struct KernelSet {
   const void* train_jet = nullptr;
   const void* train_val = nullptr;
   const void* eval_val = nullptr;
+  const void* eval_jet = nullptr;   // exchange with jets (interface residual / C1 terms)
   const void* query_val = nullptr;
   const void* query_jet = nullptr;
   size_t smem_jet = 0, smem_val = 0;

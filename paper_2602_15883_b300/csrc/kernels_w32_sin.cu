@@ -12,6 +12,7 @@ KernelSet make_set(int L) {
   k.train_jet = (const void*)k_pinn<W, DS, UNST, true, M_TRAIN, ACT>;
   k.train_val = (const void*)k_pinn<W, DS, UNST, false, M_TRAIN, ACT>;
   k.eval_val = (const void*)k_pinn<W, DS, UNST, false, M_EVAL, ACT>;
+  k.eval_jet = (const void*)k_pinn<W, DS, UNST, true, M_EVAL, ACT>;
   k.query_val = (const void*)k_pinn<W, DS, UNST, false, M_QUERY, ACT>;
   k.query_jet = (const void*)k_pinn<W, DS, UNST, true, M_QUERY, ACT>;
   k.smem_jet = smem_floats<W, CJ, DOUT>(L) * sizeof(float);

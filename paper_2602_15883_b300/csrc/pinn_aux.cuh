@@ -105,16 +105,17 @@ __global__ void k_loss_record(const Shape sh, const double* __restrict__ loss_pa
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k == 0 && bump) *step += 1;
   if (k >= n_nets) return;
-  double s[5] = {0, 0, 0, 0, 0};
+  double s[LP] = {0, 0, 0, 0, 0, 0, 0};
   for (int i = slot_begin[k]; i < slot_begin[k + 1]; ++i)
-    for (int q = 0; q < 5; ++q) s[q] += loss_part[(size_t)i * 5 + q];
+    for (int q = 0; q < LP; ++q) s[q] += loss_part[(size_t)i * LP + q];
   const NetInfo ni = nets[k];
   const double lo = s[0] * ni.inv_nobs, lp = s[1] * ni.inv_npde, lu = s[2] * ni.inv_ngh,
-               ls = s[3] * ni.inv_ngh, lt = s[4] * ni.inv_ngh;
-  const double tot = sh.lam_obs * lo + sh.lam_pde * lp + sh.lam_gh_u * lu + ni.lam_space * ls + sh.lam_time * lt;
-  const double v[6] = {lo, lp, lu, ls, lt, tot};
-  for (int q = 0; q < 6; ++q) {
-    rec[k * 6 + q] = (float)v[q];
+               ls = s[3] * ni.inv_ngh, lt = s[4] * ni.inv_ngh, lr = s[5] * ni.inv_ngh, lc = s[6] * ni.inv_ngh;
+  const double tot = sh.lam_obs * lo + sh.lam_pde * lp + sh.lam_gh_u * lu + ni.lam_space * ls + sh.lam_time * lt +
+                     sh.lam_gh_r * lr + sh.lam_gh_c1 * lc;
+  const double v[8] = {lo, lp, lu, ls, lt, tot, lr, lc};
+  for (int q = 0; q < 8; ++q) {
+    rec[k * 8 + q] = (float)v[q];
     if (!isfinite(v[q])) atomicExch(err + ERR_NONFINITE, 1);
   }
 }

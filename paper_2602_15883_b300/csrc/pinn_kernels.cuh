@@ -49,7 +49,12 @@ struct Shape {
   float anchor[3];
   float lam_obs, lam_pde, lam_gh_u, lam_time;
   float comp_w[3];
+  float lam_gh_r, lam_gh_c1;   // interface residual and C1 matching (0 = off)
 };
+
+// loss numerators per work item: obs, PDE, gh_u, gh_p space, gh_p time,
+// gh_r (residual matching), gh_c1 (first-derivative matching)
+constexpr int LP = 7;
 
 struct NetInfo {
   float center[4], scale[4];
@@ -72,6 +77,8 @@ struct Bufs {
   const int* face_info;    // [n_faces][3] = net_lo, net_hi, is_time
   float* nbr_val;          // [n_face_pts][2][dout]
   float* nbr_anc;          // [n_face_pts][2]
+  float* nbr_res;          // interface terms: residual [n_face_pts][2][ds + 1]
+  float* nbr_grd;          // and first derivatives [n_face_pts][2][dout][din]
   float* grad_part;        // [n_slots][npp]
   double* loss_part;       // [n_slots][5]
   float* stash;            // [grid][stash_per_cta]
@@ -371,11 +378,12 @@ __device__ __forceinline__ void grad_rmw(float* g, float v, bool first) {
 // (c = value, d/dx_q for every input, spatial Laplacian; j = velocity
 // components then pressure), Eqs. (7)-(10):
 //   r_j = [d_t u_j] + sum_i u_i d_i u_j + d_j p - nu lap u_j,  r_DS = div u.
-// Returns sum_j r_j^2 and adds into Yb the jet adjoints of (sc / 2) sum_j r_j^2
-// (residual adjoints rb_j = sc r_j pushed through Eqs. (7)-(10)).
+// Returns sum_j (r_j - rt_j)^2 and adds into Yb the jet adjoints of
+// (sc / 2) sum_j (r_j - rt_j)^2 (residual adjoints rb_j = sc (r_j - rt_j)
+// pushed through Eqs. (7)-(10)); rt = 0 when null (the PDE loss), the
+// neighbour's residual for the interface residual matching.
 template <int DS, int UNST, int C>
-__device__ __forceinline__ float pde_seed(const float (&Y)[DS + 1][C], float nu, float sc, float (&Yb)[DS + 1][C]) {
-  float r[DS + 1];
+__device__ __forceinline__ void ns_residual(const float (&Y)[DS + 1][C], float nu, float (&r)[DS + 1]) {
 #pragma unroll
   for (int j = 0; j < DS; ++j) {
     float v = UNST ? Y[j][1 + DS] : 0.f;
@@ -389,6 +397,17 @@ __device__ __forceinline__ float pde_seed(const float (&Y)[DS + 1][C], float nu,
 #pragma unroll
   for (int i = 0; i < DS; ++i) dv += Y[i][1 + i];
   r[DS] = dv;
+}
+
+template <int DS, int UNST, int C>
+__device__ __forceinline__ float pde_seed(const float (&Y)[DS + 1][C], float nu, float sc, float (&Yb)[DS + 1][C],
+                                          const float* rt = nullptr) {
+  float r[DS + 1];
+  ns_residual<DS, UNST, C>(Y, nu, r);
+  if (rt) {
+#pragma unroll
+    for (int j = 0; j <= DS; ++j) r[j] -= rt[j];
+  }
   float r2 = 0.f;
 #pragma unroll
   for (int j = 0; j <= DS; ++j) r2 = fmaf(r[j], r[j], r2);
@@ -539,7 +558,7 @@ __global__ void __launch_bounds__(NT, 1)
         s_is_time = 0;
       }
     }
-    double lsum0 = 0.0, lsum1 = 0.0;   // thread 0: loss numerators of this item
+    double lsum0 = 0.0, lsum1 = 0.0, lsum2 = 0.0, lsum3 = 0.0;   // thread 0: loss numerators of this item
     const int npass = (MODE == M_QUERY && ni.master) ? 2 : 1;
 
     for (int sub = 0; sub < item.count; sub += P) {
@@ -638,7 +657,7 @@ __global__ void __launch_bounds__(NT, 1)
         }
         __syncthreads();
         // ---- per-point epilogue
-        float l0 = 0.f, l1 = 0.f;
+        float l0 = 0.f, l1 = 0.f, l2 = 0.f, l3 = 0.f;
         if (t < P) {
           const int p = t;
           const bool valid = p < npts;
@@ -654,8 +673,41 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
               for (int c = 0; c < C; ++c) Yb[j][c] = 0.f;
             if constexpr (JETS) {
+             if (item.kind == K_PDE) {
               const float r2 = pde_seed<DS, UNST, C>(Y, sh.nu, valid ? 2.f * sh.lam_pde * ni.inv_npde : 0.f, Yb);
               l0 = valid ? r2 : 0.f;
+             } else if (valid) {   // K_FACE with the interface terms: C0 on the value channel, r and C1 matching
+                const size_t pt = (size_t)(item.begin + sub + p);
+                const int o = 1 - item.side;
+                const float* nv = b.nbr_val + (pt * 2 + o) * DOUT;
+                float su = 0.f;
+#pragma unroll
+                for (int c = 0; c < DS; ++c) {
+                  const float e = Y[c][0] - nv[c];
+                  su = fmaf(sh.comp_w[c] * e, e, su);
+                  Yb[c][0] = 2.f * sh.lam_gh_u * sh.comp_w[c] * e * ni.inv_ngh;
+                }
+                float Pn = nv[DS];
+                if (s_other_master) Pn = Pn - b.nbr_anc[pt * 2 + o];   // Eq. (15)
+                const float ep = Y[DS][0] - Pn;
+                const float lam = s_is_time ? sh.lam_time : ni.lam_space;
+                Yb[DS][0] = 2.f * lam * ep * ni.inv_ngh;
+                l0 = su;
+                l1 = ep * ep;
+                const float* rt = b.nbr_res + (pt * 2 + o) * (DS + 1);
+                l2 = pde_seed<DS, UNST, C>(Y, sh.nu, 2.f * sh.lam_gh_r * ni.inv_ngh, Yb, rt);
+                const float* gt = b.nbr_grd + (pt * 2 + o) * DOUT * DIN;
+                float sc1 = 0.f;
+#pragma unroll
+                for (int c = 0; c < DOUT; ++c)
+#pragma unroll
+                  for (int q = 0; q < DIN; ++q) {
+                    const float e = Y[c][1 + q] - gt[c * DIN + q];
+                    sc1 = fmaf(e, e, sc1);
+                    Yb[c][1 + q] = fmaf(2.f * sh.lam_gh_c1 * ni.inv_ngh, e, Yb[c][1 + q]);
+                  }
+                l3 = sc1;
+             }
             } else if (item.kind == K_OBS) {
               float e[DS];
 #pragma unroll
@@ -708,6 +760,17 @@ __global__ void __launch_bounds__(NT, 1)
               if (item.kind == K_EVAL) {
 #pragma unroll
                 for (int j = 0; j < DOUT; ++j) b.nbr_val[(pt * 2 + item.side) * DOUT + j] = Y[j][0];
+                if constexpr (JETS) {   // the interface terms' messages: residual and first derivatives
+                  float r[DS + 1];
+                  ns_residual<DS, UNST, C>(Y, sh.nu, r);
+#pragma unroll
+                  for (int j = 0; j <= DS; ++j) b.nbr_res[(pt * 2 + item.side) * (DS + 1) + j] = r[j];
+#pragma unroll
+                  for (int c = 0; c < DOUT; ++c)
+#pragma unroll
+                    for (int q = 0; q < DIN; ++q)
+                      b.nbr_grd[((pt * 2 + item.side) * DOUT + c) * DIN + q] = Y[c][1 + q];
+                }
               } else {
                 b.nbr_anc[pt * 2 + item.side] = Y[DS][0];
               }
@@ -747,6 +810,12 @@ __global__ void __launch_bounds__(NT, 1)
           if (item.kind == K_FACE) {
             const float s1 = block_sum(l1, s_red);
             if (t == 0) lsum1 += (double)s1;
+            if constexpr (JETS) {
+              const float s2 = block_sum(l2, s_red);
+              if (t == 0) lsum2 += (double)s2;
+              const float s3 = block_sum(l3, s_red);
+              if (t == 0) lsum3 += (double)s3;
+            }
           }
         }
         __syncthreads();
@@ -931,13 +1000,15 @@ __global__ void __launch_bounds__(NT, 1)
       __syncthreads();
     }   // sub-tiles
     if (TRAIN && t == 0) {
-      double* lp = b.loss_part + (size_t)item.slot * 5;
-      for (int q = 0; q < 5; ++q) lp[q] = 0.0;
+      double* lp = b.loss_part + (size_t)item.slot * LP;
+      for (int q = 0; q < LP; ++q) lp[q] = 0.0;
       if (item.kind == K_PDE) lp[1] = lsum0;
       else if (item.kind == K_OBS) lp[0] = lsum0;
       else {
         lp[2] = lsum0;
         lp[s_is_time ? 4 : 3] = lsum1;
+        lp[5] = lsum2;
+        lp[6] = lsum3;
       }
     }
   }   // items

@@ -643,8 +643,8 @@ __global__ void __launch_bounds__(NTC, 1)
       __syncthreads();
     }   // sub-tiles
     if (t == 0) {
-      double* lp = b.loss_part + (size_t)item.slot * 5;
-      for (int q = 0; q < 5; ++q) lp[q] = 0.0;
+      double* lp = b.loss_part + (size_t)item.slot * LP;
+      for (int q = 0; q < LP; ++q) lp[q] = 0.0;
       lp[1] = lsum0;
     }
   }   // items

@@ -1,0 +1,85 @@
+"""GPU-vs-oracle parity with the interface residual and C1 matching terms
+(the Remark of Sec. 2.2): every entry of the 8-term loss record <= 1e-5
+relative (L2 over nets), gradients <= 1e-4 relative per net.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from tests.helpers import rel_l2
+from tests.test_gpu_parity import GRAD_TOL, LOSS_TOL, _gpu, small_case
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _threads():
+    oracle.set_threads(os.cpu_count() or 1)
+    yield
+    oracle.set_threads(1)
+
+
+def _case(name, precision=0, lam_r=0.6, lam_c1=0.35):
+    cfg, pb = small_case(name)
+    return dict(cfg, lambda_gh_r=lam_r, lambda_gh_c1=lam_c1, precision=precision), pb
+
+
+def _compare(loss, oloss, tol=LOSS_TOL):
+    for q in range(8):
+        r = oloss[:, q]
+        if np.linalg.norm(r) == 0:
+            assert np.all(loss[:, q] == 0), q
+        else:
+            assert rel_l2(loss[:, q], r) <= tol, (q, rel_l2(loss[:, q], r))
+
+
+@pytest.mark.parametrize("name,precision", [("tgv", 0), ("steady3d_w64", 0), ("beltrami32", 0), ("beltrami32", 1),
+                                            ("tgv_ghost", 0), ("beltrami_sin", 0)])
+def test_interface_terms_losses_and_gradients_match_oracle(name, precision):
+    Dpinn = _gpu()
+    cfg, pb = _case(name, precision)
+    d = Dpinn(cfg)
+    d.set_problem(pb)
+    d.eval_grad()
+    loss, g = d.loss_ext(), d.grad()
+    ora = oracle.Oracle(cfg, pb)
+    og, oloss = ora.grad(np.asarray(pb.theta0, np.float64))
+    assert np.all(oloss[:, 6] > 0) and np.all(oloss[:, 7] > 0)
+    _compare(loss, oloss)
+    for k in range(ora.n_nets):
+        assert rel_l2(g[k], og[k]) <= GRAD_TOL, (k, rel_l2(g[k], og[k]))
+    # the 6-entry record is the first 6 entries
+    np.testing.assert_array_equal(d.loss(), loss[:, :6])
+
+
+def test_interface_terms_one_step_and_losses_only():
+    Dpinn = _gpu()
+    cfg, pb = _case("tgv")
+    d = Dpinn(cfg)
+    d.set_problem(pb)
+    d.eval_loss()
+    l_only = d.loss_ext()
+    d.step(1)
+    loss = d.loss_ext()
+    np.testing.assert_array_equal(l_only, loss)
+    ora = oracle.Oracle(cfg, pb)
+    th0 = np.asarray(pb.theta0, np.float64)
+    n = th0.size
+    oth, _, _, _, oloss = ora.step(th0, np.zeros(n), np.zeros(n), 0)
+    _compare(loss, oloss)
+    assert rel_l2(d.get_state()[0], oth) <= 1e-5
+
+
+def test_terms_off_leave_the_plain_step_unchanged():
+    Dpinn = _gpu()
+    cfg, pb = small_case("tgv")
+    a = Dpinn(cfg)
+    a.set_problem(pb)
+    a.eval_grad()
+    b = Dpinn(dict(cfg, lambda_gh_r=0.0, lambda_gh_c1=0.0))
+    b.set_problem(pb)
+    b.eval_grad()
+    np.testing.assert_array_equal(a.grad(), b.grad())
+    assert np.all(b.loss_ext()[:, 6:] == 0)
