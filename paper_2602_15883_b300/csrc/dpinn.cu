@@ -240,8 +240,8 @@ cudaError_t enqueue_step(dpinn* h, int mode, cudaStream_t s, int* n_launch, cuda
       e = launch_pinn(h->ks.eval_jet, h->grid_eval, h->ks.smem_jet, h->shape, bb, h->items_eval.p, h->n_items_d.p + 0,
                       s);
     else
-      e = launch_pinn(h->ks.eval_val, h->grid_eval, h->ks.smem_val, h->shape, bb, h->items_eval.p, h->n_items_d.p + 0,
-                      s);
+      e = launch_pinn(h->ks.eval_val_run, h->grid_eval, h->ks.smem_val_run, h->shape, bb, h->items_eval.p,
+                      h->n_items_d.p + 0, s, h->ks.threads_val_run);
     ++launches;
     mark("exchange");
   }
@@ -266,8 +266,9 @@ cudaError_t enqueue_step(dpinn* h, int mode, cudaStream_t s, int* n_launch, cuda
   if (e == cudaSuccess && h->n_val) {
     dk::Bufs bb = b;
     bb.counter = h->counters.p + 2;
-    bb.stash_per_cta = h->ks.stash_val;
-    e = launch_pinn(h->ks.train_val, h->grid_val, h->ks.smem_val, h->shape, bb, h->items_val.p, h->n_items_d.p + 2, s);
+    bb.stash_per_cta = h->ks.stash_val_run;
+    e = launch_pinn(h->ks.train_val_run, h->grid_val, h->ks.smem_val_run, h->shape, bb, h->items_val.p,
+                    h->n_items_d.p + 2, s, h->ks.threads_val_run);
     ++launches;
     mark("train_val");
   }
@@ -364,7 +365,7 @@ int build_plan(dpinn* h) {
     return std::min<int64_t>(std::max<int64_t>(c, P), 64LL * P);
   };
   int64_t cj = pick_chunk(res_off[nn], h->ks.P_train_jet, h->sched_jet);
-  int64_t cv = pick_chunk(obs_off[nn] + 2 * n_face_pts, h->ks.P_val, h->sched_val);
+  int64_t cv = pick_chunk(obs_off[nn] + 2 * n_face_pts, h->ks.P_val_run, h->sched_val);
   // Every training item owns one gradient partial of npp floats: enlarge the
   // chunks until the partials fit the memory budget (at least one item per
   // net and point set remains), so the number of points per step is not
@@ -377,7 +378,7 @@ int build_plan(dpinn* h) {
       return n;
     };
     const int64_t max_slots = std::max<int64_t>(1, h->part_budget / ((int64_t)h->npp * 4));
-    const int64_t PJ = h->ks.P_train_jet, PV = h->ks.P_val;
+    const int64_t PJ = h->ks.P_train_jet, PV = h->ks.P_val_run;
     auto up = [](int64_t x, int64_t p) { return ((x + p - 1) / p) * p; };
     const int64_t cap_j = up(std::max<int64_t>(res_off[nn], 1), PJ);
     const int64_t cap_v = up(std::max<int64_t>(obs_off[nn] + n_face_pts, 1), PV);
@@ -455,10 +456,11 @@ int build_plan(dpinn* h) {
   h->n_jf = (int)ijf.size();
 
   const int occ_j = occupancy(h->ks.train_jet_run, h->ks.smem_train_jet, h->ks.threads_train_jet);
-  const int occ_v = occupancy(h->ks.train_val, h->ks.smem_val);
+  const int occ_v = occupancy(h->ks.train_val_run, h->ks.smem_val_run, h->ks.threads_val_run);
   h->grid_jet = (int)std::min<int64_t>(h->n_jet, (int64_t)h->n_sms * occ_j);
   h->grid_val = (int)std::min<int64_t>(h->n_val, (int64_t)h->n_sms * occ_v);
-  const int occ_e = h->iface ? occupancy(h->ks.eval_jet, h->ks.smem_jet) : occ_v;
+  const int occ_e = h->iface ? occupancy(h->ks.eval_jet, h->ks.smem_jet)
+                             : occupancy(h->ks.eval_val_run, h->ks.smem_val_run, h->ks.threads_val_run);
   h->grid_eval = (int)std::min<int64_t>(h->n_eval, (int64_t)h->n_sms * occ_e);
   const int occ_f = occupancy(h->ks.train_jet, h->ks.smem_jet);
   h->grid_jf = (int)std::min<int64_t>(h->n_jf, (int64_t)h->n_sms * occ_f);
@@ -480,7 +482,7 @@ int build_plan(dpinn* h) {
   CK(h, h->grad_part.ensure((size_t)std::max(slot, 1) * h->npp));
   CK(h, h->loss_part.ensure((size_t)std::max(slot, 1) * dk::LP));
   CK(h, cudaMemset(h->loss_part.p, 0, (size_t)std::max(slot, 1) * dk::LP * sizeof(double)));
-  const size_t st = std::max({(size_t)h->grid_jet * h->ks.stash_train_jet, (size_t)h->grid_val * h->ks.stash_val,
+  const size_t st = std::max({(size_t)h->grid_jet * h->ks.stash_train_jet, (size_t)h->grid_val * h->ks.stash_val_run,
                               (size_t)h->grid_jf * h->ks.stash_jet});
   CK(h, h->stash.ensure(std::max<size_t>(st, 4)));
   CK(h, h->nbr_val.ensure((size_t)std::max<int64_t>(n_face_pts, 1) * 2 * h->dout));
@@ -659,12 +661,24 @@ int dpinn_create(const dpinn_config* cfg, dpinn_t** out) {
     h->ks.smem_train_jet = h->ks.smem_tc;
     h->ks.P_train_jet = h->ks.P_tc;
     h->ks.stash_train_jet = h->ks.stash_tc;
+    h->ks.train_val_run = h->ks.train_val_tc;
+    h->ks.eval_val_run = h->ks.eval_val_tc;
+    h->ks.threads_val_run = h->ks.threads_tcv;
+    h->ks.smem_val_run = h->ks.smem_tcv;
+    h->ks.P_val_run = h->ks.P_tcv;
+    h->ks.stash_val_run = h->ks.stash_tcv;
   } else {
     h->ks.train_jet_run = h->ks.train_jet;
     h->ks.threads_train_jet = dk::NT;
     h->ks.smem_train_jet = h->ks.smem_jet;
     h->ks.P_train_jet = h->ks.P_jet;
     h->ks.stash_train_jet = h->ks.stash_jet;
+    h->ks.train_val_run = h->ks.train_val;
+    h->ks.eval_val_run = h->ks.eval_val;
+    h->ks.threads_val_run = dk::NT;
+    h->ks.smem_val_run = h->ks.smem_val;
+    h->ks.P_val_run = h->ks.P_val;
+    h->ks.stash_val_run = h->ks.stash_val;
   }
   // decomposition
   int s = 1;
@@ -730,6 +744,12 @@ int dpinn_create(const dpinn_config* cfg, dpinn_t** out) {
   for (const void* fn : {h->ks.train_jet, h->ks.query_jet})
     CK(hp, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ks.smem_jet));
   CK(hp, cudaFuncSetAttribute(h->ks.eval_jet, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ks.smem_jet));
+  if (h->ks.train_val_run != h->ks.train_val) {
+    CK(hp, cudaFuncSetAttribute(h->ks.train_val_run, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)h->ks.smem_val_run));
+    CK(hp, cudaFuncSetAttribute(h->ks.eval_val_run, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)h->ks.smem_val_run));
+  }
   if (h->ks.train_jet_run != h->ks.train_jet)
     CK(hp, cudaFuncSetAttribute(h->ks.train_jet_run, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)h->ks.smem_train_jet));
@@ -1056,7 +1076,7 @@ int dpinn_get_schedule(dpinn_t* h, int* jet_tiles, int* val_tiles, int* order, i
   if (jet_tiles) *jet_tiles = h->sched_jet;
   if (val_tiles) *val_tiles = h->sched_val;
   if (order) *order = h->sched_order;
-  if (tile_points) { tile_points[0] = h->ks.P_train_jet; tile_points[1] = h->ks.P_val; }
+  if (tile_points) { tile_points[0] = h->ks.P_train_jet; tile_points[1] = h->ks.P_val_run; }
   return DPINN_OK;
 }
 

@@ -29,6 +29,20 @@ struct KernelSet {
   size_t smem_tc = 0;
   int P_tc = 0;
   long long stash_tc = 0;
+  // the value kernels actually launched (training of observation / face
+  // items, and the exchange): FP32 ones above or the tensor-core ones below
+  const void* train_val_run = nullptr;
+  const void* eval_val_run = nullptr;
+  int threads_val_run = 0, P_val_run = 0;
+  size_t smem_val_run = 0;
+  long long stash_val_run = 0;
+  // tensor-core value kernels, width 128 only
+  const void* train_val_tc = nullptr;
+  const void* eval_val_tc = nullptr;
+  int threads_tcv = 0;
+  size_t smem_tcv = 0;
+  int P_tcv = 0;
+  long long stash_tcv = 0;
 };
 
 // Fill *k for (d_space, unsteady, depth); false if the shape is unsupported.

@@ -2,6 +2,7 @@
 #include "kernel_set.h"
 #include "pinn_kernels.cuh"
 #include "pinn_tc.cuh"
+#include "pinn_tcv.cuh"
 
 namespace dk {
 namespace {
@@ -27,6 +28,12 @@ KernelSet make_set(int L) {
   k.smem_tc = tc_smem_bytes<CJ, DOUT>(L);
   k.P_tc = TcTile<CJ>::P;
   k.stash_tc = tc_stash_floats<CJ>(L);
+  k.train_val_tc = (const void*)k_pinn_tcv<DS, UNST, ACT, M_TRAIN>;
+  k.eval_val_tc = (const void*)k_pinn_tcv<DS, UNST, ACT, M_EVAL>;
+  k.threads_tcv = NTC;
+  k.smem_tcv = tcv_smem_bytes<DOUT>(L);
+  k.P_tcv = TcvTile::P;
+  k.stash_tcv = tcv_stash_floats(L);
   return k;
 }
 

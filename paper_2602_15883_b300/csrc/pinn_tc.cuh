@@ -34,7 +34,7 @@
 
 namespace dk {
 
-constexpr int NTC = 512;   // threads of the tensor-core kernel
+constexpr int NTC = 512;   // threads of the tensor-core kernels
 
 template <int C>
 struct TcTile {
