@@ -574,7 +574,10 @@ int enqueue_query(dpinn* h, const QueryScratch& q, const float* pts, int64_t n, 
   b.q_w = h->dout + (want_residual ? h->ds + 1 : 0);
   const void* fn = want_residual ? h->ks.query_jet : h->ks.query_val;
   const size_t smem = want_residual ? h->ks.smem_jet : h->ks.smem_val;
-  const int grid = (int)std::min<size_t>(max_items, (size_t)h->n_sms * occupancy(fn, smem));
+  // One CTA per work item rather than a persistent grid: CTAs retire as their
+  // items finish, so the block scheduler can interleave the kernels of other
+  // (higher-priority) streams with a large query.
+  const int grid = (int)std::min<size_t>(max_items, (size_t)1 << 30);
   CK(h, launch_pinn(fn, grid, smem, h->shape, b, q.items, q.nitems, s));
   return DPINN_OK;
 }

@@ -2,16 +2,21 @@
 
 Requests (point clouds of any size, asking for (u, v, [w], p) and optionally
 the Navier-Stokes residuals) arrive at any time.  A dispatcher thread keeps
-``slots`` batches in flight, each on its own CUDA stream with its own query
-context and pre-allocated buffers: whenever a slot is free it admits the
-oldest waiting requests that fit the slot and the in-flight memory cap,
-copies their points into one pinned staging buffer, and issues one
-host-to-device copy, one value launch (requests without residual), one
-residual launch, one device-to-host copy and an event.  Requests that arrive
-while other batches run are admitted as slots and memory free up, so the
-copies and kernels of different batches overlap on the device.  Each point
-is computed by the same kernel code whatever batch it lands in (no
-cross-point reduction), so a request's result does not depend on the mix.
+``slots`` batches in flight, each with its own query contexts, pre-allocated
+buffers and two CUDA streams: whenever a slot is free it admits the oldest
+waiting requests that fit the slot and the in-flight memory cap, copies
+their points into one pinned staging buffer, and issues one host-to-device
+copy, the value launch (requests without residual) with its device-to-host
+copy on a high-priority stream, and the residual launch (jets, several times
+the work per point) with its copy on a low-priority stream.  The query
+kernels run one CTA per work item, so the block scheduler serves the
+high-priority value work between the CTAs of a large residual request, and
+value requests complete on their own event without waiting for the
+residuals of their batch.  Requests that arrive while other batches run are
+admitted as slots and memory free up, so the copies and kernels of
+different batches overlap on the device.  Each point is computed by the same
+kernel code whatever batch it lands in (no cross-point reduction), so a
+request's result does not depend on the mix.
 """
 from __future__ import annotations
 
@@ -21,6 +26,8 @@ from collections import deque
 from dataclasses import dataclass, field
 
 import numpy as np
+
+ERR_INVALID_ARG = -1   # include/dpinn.h: DPINN_ERR_INVALID_ARG (an outside point)
 
 
 @dataclass
@@ -32,6 +39,7 @@ class Request:
     result: np.ndarray | None = None
     error: str | None = None
     rid: int = 0
+    retries: int = 0
     done: threading.Event = field(default_factory=threading.Event)
 
     @property
@@ -81,8 +89,12 @@ class Server:
         self.slots = []
         for _ in range(slots):
             self.slots.append({
-                "stream": torch.cuda.Stream(),
+                # lower numbers are higher priorities; out-of-range values map
+                # to the nearest valid one (the highest for the value stream)
+                "stream": torch.cuda.Stream(priority=-8),   # values
+                "stream_r": torch.cuda.Stream(priority=0),  # residuals (the lowest)
                 "qctx": QueryContext(handle, self.max_points),
+                "qctx_r": QueryContext(handle, self.max_points),
                 "pts_h": torch.empty((self.max_points, self.d_in), dtype=torch.float32).pin_memory(),
                 "pts_d": torch.empty((self.max_points, self.d_in), dtype=torch.float32, device="cuda"),
                 "val_d": torch.empty((self.max_points, self.w_val), dtype=torch.float32, device="cuda"),
@@ -108,10 +120,11 @@ class Server:
         with self.lock:
             r.rid = self._next_id
             self._next_id += 1
+        # The domain is checked on the device while routing; only a batch that
+        # reports an outside point is checked request by request on the host
+        # (see _complete), which keeps the check off the common path.
         if r.n > self.max_points:
             r.error = f"request of {r.n} points exceeds the batch capacity {self.max_points}"
-        elif r.n and not np.all((pts >= self.lo) & (pts <= self.hi)):
-            r.error = "query point outside the domain"
         if r.error or r.n == 0:
             r.result = np.zeros((0, self._width(r)), np.float32) if not r.error else None
             r.t_done = time.perf_counter()
@@ -146,6 +159,7 @@ class Server:
             self._thread.join()
         for s in self.slots:
             s["qctx"].close()
+            s["qctx_r"].close()
 
     def _run(self):
         torch = self.torch
@@ -186,48 +200,72 @@ class Server:
         for r in order:
             ph[off:off + r.n] = r.pts
             off += r.n
-        stream = s["stream"]
+        stream, stream_r = s["stream"], s["stream_r"]
+        ev_v = ev_r = None
         with torch.cuda.stream(stream):
             s["pts_d"][:off].copy_(s["pts_h"][:off], non_blocking=True)
+            ev_in = torch.cuda.Event()
+            ev_in.record(stream)
             if nv:
                 s["qctx"].query_into(s["pts_d"][:nv], s["val_d"][:nv], False, stream)
                 s["val_h"][:nv].copy_(s["val_d"][:nv], non_blocking=True)
-            if nr:
-                s["qctx"].query_into(s["pts_d"][nv:off], s["res_d"][:nr], True, stream)
+                ev_v = torch.cuda.Event()
+                ev_v.record(stream)
+        if nr:
+            with torch.cuda.stream(stream_r):
+                stream_r.wait_event(ev_in)
+                s["qctx_r"].query_into(s["pts_d"][nv:off], s["res_d"][:nr], True, stream_r)
                 s["res_h"][:nr].copy_(s["res_d"][:nr], non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(stream)
-        s["busy"] = (ev, vals, ress, mem)
+                ev_r = torch.cuda.Event()
+                ev_r.record(stream_r)
+        s["busy"] = {"ev_v": ev_v, "ev_r": ev_r, "vals": vals, "ress": ress, "mem": mem}
 
     def _complete(self):
         done_any = False
         for s in self.slots:
-            if s["busy"] is None:
+            b = s["busy"]
+            if b is None:
                 continue
-            ev, vals, ress, mem = s["busy"]
-            if not ev.query():
-                continue
-            st = s["qctx"].status(s["stream"])
-            t = time.perf_counter()
-            vh, rh = s["val_h"].numpy(), s["res_h"].numpy()
-            off = 0
-            for r in vals:
-                r.result = vh[off:off + r.n].copy()
-                off += r.n
-            off = 0
-            for r in ress:
-                r.result = rh[off:off + r.n].copy()
-                off += r.n
-            for r in vals + ress:
-                if st != 0:
-                    r.error = f"query failed with status {st}"
-                r.t_done = t
-                r.done.set()
-            with self.lock:
-                self.in_flight_bytes -= mem
-                self.completed.extend(vals + ress)
-                s["busy"] = None
-            done_any = True
+            t = None
+            # values and residuals of a batch complete on their own events
+            for key_ev, key_reqs, qctx, stream, buf, w in (("ev_v", "vals", s["qctx"], s["stream"], "val_h", self.w_val),
+                                                           ("ev_r", "ress", s["qctx_r"], s["stream_r"], "res_h",
+                                                            self.w_res)):
+                ev = b[key_ev]
+                if ev is None or not ev.query():
+                    continue
+                st = qctx.status(stream)
+                t = time.perf_counter()
+                h = s[buf].numpy()
+                finished, retry = [], []
+                off = 0
+                for r in b[key_reqs]:
+                    if st == 0:
+                        r.result = h[off:off + r.n].copy()
+                    elif (st == ERR_INVALID_ARG and r.retries == 0 and
+                          np.all((r.pts >= self.lo) & (r.pts <= self.hi))):
+                        r.retries += 1       # an innocent neighbour of an outside point: run it again
+                        retry.append(r)
+                        off += r.n
+                        continue
+                    else:
+                        r.error = ("query point outside the domain" if st == ERR_INVALID_ARG
+                                   else f"query failed with status {st}")
+                    off += r.n
+                    r.t_done = t
+                    finished.append(r)
+                for r in finished:
+                    r.done.set()
+                with self.lock:
+                    self.completed.extend(finished)
+                    for r in reversed(retry):
+                        self.pending.appendleft(r)
+                b[key_ev] = None
+                done_any = True
+            if b["ev_v"] is None and b["ev_r"] is None:
+                with self.lock:
+                    self.in_flight_bytes -= b["mem"]
+                    s["busy"] = None
         return done_any
 
 
