@@ -133,6 +133,21 @@ def fp32_alu_peak_tflops(sm_mhz):
 PRECISIONS = {"fp32": 0, "tf32x3": 1}
 
 
+def max_over_ranks(dist, values, device):
+    """Element-wise maximum of a list of floats over all ranks (the slowest
+    replica's times); ``device`` "cuda" for NCCL, "cpu" for gloo."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def whole_job_value(world, n_res_per_rank, steps, total_ms_max):
+    """Whole-job residual points per second: every replica's points over the
+    slowest replica's time (weak scaling: each rank runs its own problem)."""
+    return world * n_res_per_rank * steps / (total_ms_max / 1e3)
+
+
 def tf32_tensor_peak_tflops(pk):
     # dense TF32 from the measured dense bf16 (cuBLAS) burst figure and the
     # nominal B300 ratio (1.1 / 2.25 PFLOP/s)
@@ -312,10 +327,8 @@ def main():
     step_ms = float(np.median(ms))
     total_ms = float(ms.sum())
     if dist:
-        t = torch.tensor([total_ms, step_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms, step_ms = float(t[0]), float(t[1])
-    value = world * pb.n_res * args.steps / (total_ms / 1e3)
+        total_ms, step_ms = max_over_ranks(dist, [total_ms, step_ms], "cuda")
+    value = whole_job_value(world, pb.n_res, args.steps, total_ms)
 
     # ---- per-kernel timing of the same kernels (events on this stream)
     kt = {}
@@ -363,9 +376,7 @@ def main():
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t[0])
+        (e2e_s,) = max_over_ranks(dist, [e2e_s], "cuda")
     e2e = {"value": world * pb.n_res * e2e_steps / e2e_s, "unit": "residual-points/s",
            "h2d_bytes_per_step": int(pinned.numel() * 4), "d2h_bytes_per_step": int(out.nbytes)}
 
