@@ -224,13 +224,14 @@ def plain_form_rate(cfg, pb, steps=2):
             "kind": "per-net eager PyTorch autograd double backward + torch.optim.Adam, FP32"}
 
 
-def serving_leg(seconds=5.0, rate=200.0, train_steps=20, seed=0):
+def serving_leg(seconds=5.0, rate=200.0, train_steps=20, seed=0, precision="tf32x3"):
     """Continuous-batching serving of the trained 32-net Beltrami ensemble:
     Poisson arrivals, log-uniform 1k-1M point clouds, 10 % with residuals,
-    8 GB in-flight memory cap; p50/p99 latency and points/s."""
+    8 GB in-flight memory cap; p50/p99 latency and points/s.  The ensemble
+    (width 128) trains and answers on the tensor-core kernels by default."""
     from paper_2602_15883_b300.binding import Dpinn
     from paper_2602_15883_b300.serve import Server, latency_summary, poisson_load
-    cfg = synth.config("beltrami32")
+    cfg = synth.config("beltrami32", precision=PRECISIONS[precision])
     pb = synth.make_problem(cfg, seed=seed)
     d = Dpinn(cfg)
     d.set_problem(pb)
@@ -245,7 +246,7 @@ def serving_leg(seconds=5.0, rate=200.0, train_steps=20, seed=0):
     out = latency_summary(reqs)
     out.update({"workload": "beltrami32 ensemble (32 nets of 8x128) after %d training steps" % train_steps,
                 "arrivals": f"Poisson {rate:g} req/s for {seconds:g} s", "points_per_request": "log-uniform 1e3..1e6",
-                "residual_fraction": 0.1, "mem_cap_gb": 8, "slots": 4,
+                "residual_fraction": 0.1, "mem_cap_gb": 8, "slots": 4, "precision": precision,
                 "max_concurrent_batches": srv.max_concurrent,
                 "offered_points_per_s": sum(r.n for r in reqs) / seconds})
     d.close()

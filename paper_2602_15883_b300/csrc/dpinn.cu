@@ -545,7 +545,7 @@ struct QueryScratch {
 // launch the grouped query kernel, all on stream s.
 int enqueue_query(dpinn* h, const QueryScratch& q, const float* pts, int64_t n, int want_residual, float* out,
                   cudaStream_t s) {
-  const int P = want_residual ? h->ks.P_jet : h->ks.P_val;
+  const int P = want_residual ? h->ks.P_qjet : h->ks.P_qval;
   const int chunk = 4 * P;
   const size_t max_items = (size_t)(n / chunk) + h->n_nets + 1;
   dk::Route rt{};
@@ -572,13 +572,14 @@ int enqueue_query(dpinn* h, const QueryScratch& q, const float* pts, int64_t n, 
   b.q_perm = q.perm;
   b.q_out = out;
   b.q_w = h->dout + (want_residual ? h->ds + 1 : 0);
-  const void* fn = want_residual ? h->ks.query_jet : h->ks.query_val;
-  const size_t smem = want_residual ? h->ks.smem_jet : h->ks.smem_val;
+  const void* fn = want_residual ? h->ks.query_jet_run : h->ks.query_val_run;
+  const size_t smem = want_residual ? h->ks.smem_qjet : h->ks.smem_qval;
+  const int threads = want_residual ? h->ks.threads_qjet : h->ks.threads_qval;
   // One CTA per work item rather than a persistent grid: CTAs retire as their
   // items finish, so the block scheduler can interleave the kernels of other
   // (higher-priority) streams with a large query.
   const int grid = (int)std::min<size_t>(max_items, (size_t)1 << 30);
-  CK(h, launch_pinn(fn, grid, smem, h->shape, b, q.items, q.nitems, s));
+  CK(h, launch_pinn(fn, grid, smem, h->shape, b, q.items, q.nitems, s, threads));
   return DPINN_OK;
 }
 
@@ -670,6 +671,13 @@ int dpinn_create(const dpinn_config* cfg, dpinn_t** out) {
     h->ks.smem_val_run = h->ks.smem_tcv;
     h->ks.P_val_run = h->ks.P_tcv;
     h->ks.stash_val_run = h->ks.stash_tcv;
+    h->ks.query_val_run = h->ks.query_val_tc;
+    h->ks.query_jet_run = h->ks.query_jet_tc;
+    h->ks.threads_qval = h->ks.threads_qjet = h->ks.threads_tcv;
+    h->ks.P_qval = h->ks.P_tcv;
+    h->ks.P_qjet = h->ks.P_tc;
+    h->ks.smem_qval = h->ks.smem_tcv;
+    h->ks.smem_qjet = h->ks.smem_tc;
   } else {
     h->ks.train_jet_run = h->ks.train_jet;
     h->ks.threads_train_jet = dk::NT;
@@ -682,6 +690,13 @@ int dpinn_create(const dpinn_config* cfg, dpinn_t** out) {
     h->ks.smem_val_run = h->ks.smem_val;
     h->ks.P_val_run = h->ks.P_val;
     h->ks.stash_val_run = h->ks.stash_val;
+    h->ks.query_val_run = h->ks.query_val;
+    h->ks.query_jet_run = h->ks.query_jet;
+    h->ks.threads_qval = h->ks.threads_qjet = dk::NT;
+    h->ks.P_qval = h->ks.P_val;
+    h->ks.P_qjet = h->ks.P_jet;
+    h->ks.smem_qval = h->ks.smem_val;
+    h->ks.smem_qjet = h->ks.smem_jet;
   }
   // decomposition
   int s = 1;
@@ -748,6 +763,10 @@ int dpinn_create(const dpinn_config* cfg, dpinn_t** out) {
     CK(hp, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ks.smem_jet));
   CK(hp, cudaFuncSetAttribute(h->ks.eval_jet, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ks.smem_jet));
   if (h->ks.train_val_run != h->ks.train_val) {
+    CK(hp, cudaFuncSetAttribute(h->ks.query_val_run, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)h->ks.smem_qval));
+    CK(hp, cudaFuncSetAttribute(h->ks.query_jet_run, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)h->ks.smem_qjet));
     CK(hp, cudaFuncSetAttribute(h->ks.train_val_run, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)h->ks.smem_val_run));
     CK(hp, cudaFuncSetAttribute(h->ks.eval_val_run, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1168,7 +1187,7 @@ int dpinn_query(dpinn_t* h, const float* pts, int64_t n, int want_residual, floa
   if (n < 0 || n > ((int64_t)1 << 30)) return fail(h, DPINN_ERR_INVALID_ARG, "bad point count");
   if (n == 0) return DPINN_OK;
   if (!pts || !out) return fail(h, DPINN_ERR_INVALID_ARG, "null pointer");
-  const int P = want_residual ? h->ks.P_jet : h->ks.P_val;
+  const int P = want_residual ? h->ks.P_qjet : h->ks.P_qval;
   const size_t max_items = (size_t)(n / (4 * P)) + h->n_nets + 1;
   CK(h, h->q_net.ensure(n));
   CK(h, h->q_perm.ensure(n));
@@ -1250,7 +1269,7 @@ int dpinn_query_static(dpinn_t* h, const float* pts, int64_t n, int want_residua
   int* nitems = reinterpret_cast<int*>(sb + QS_OFF_NITEMS);
   dk::Item* items = reinterpret_cast<dk::Item*>(sb + QS_OFF_ITEMS);
   cudaStream_t s = (cudaStream_t)stream;
-  const int P = want_residual ? h->ks.P_jet : h->ks.P_val;
+  const int P = want_residual ? h->ks.P_qjet : h->ks.P_qval;
   const int chunk = 4 * P;   // >= 64, so at most QS_MAX_ITEMS items
   const size_t max_items = (size_t)(n / chunk) + h->n_nets + 1;
   dk::Route rt{};
@@ -1277,10 +1296,11 @@ int dpinn_query_static(dpinn_t* h, const float* pts, int64_t n, int want_residua
   b.q_perm = perm;
   b.q_out = out;
   b.q_w = h->dout + (want_residual ? h->ds + 1 : 0);
-  const void* fn = want_residual ? h->ks.query_jet : h->ks.query_val;
-  const size_t smem = want_residual ? h->ks.smem_jet : h->ks.smem_val;
-  const int grid = (int)std::min<size_t>(max_items, (size_t)h->n_sms * occupancy(fn, smem));
-  CK(h, launch_pinn(fn, grid, smem, h->shape, b, items, nitems, s));
+  const void* fn = want_residual ? h->ks.query_jet_run : h->ks.query_val_run;
+  const size_t smem = want_residual ? h->ks.smem_qjet : h->ks.smem_qval;
+  const int threads = want_residual ? h->ks.threads_qjet : h->ks.threads_qval;
+  const int grid = (int)std::min<size_t>(max_items, (size_t)h->n_sms * occupancy(fn, smem, threads));
+  CK(h, launch_pinn(fn, grid, smem, h->shape, b, items, nitems, s, threads));
   return DPINN_OK;
 }
 
@@ -1291,7 +1311,7 @@ int dpinn_qctx_create(dpinn_t* h, int64_t max_points, dpinn_qctx_t** out) {
   std::unique_ptr<dpinn_qctx> q(new dpinn_qctx());
   q->h = h;
   q->cap = max_points;
-  const int Pmin = std::min(h->ks.P_jet, h->ks.P_val);
+  const int Pmin = std::min(h->ks.P_qjet, h->ks.P_qval);
   CK(h, q->net_of.ensure(max_points));
   CK(h, q->perm.ensure(max_points));
   CK(h, q->counts.ensure(h->n_nets));

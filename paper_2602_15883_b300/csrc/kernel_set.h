@@ -39,6 +39,13 @@ struct KernelSet {
   // tensor-core value kernels, width 128 only
   const void* train_val_tc = nullptr;
   const void* eval_val_tc = nullptr;
+  const void* query_val_tc = nullptr;
+  const void* query_jet_tc = nullptr;
+  // the query kernels actually launched and their launch shapes
+  const void* query_val_run = nullptr;
+  const void* query_jet_run = nullptr;
+  int threads_qval = 0, threads_qjet = 0, P_qval = 0, P_qjet = 0;
+  size_t smem_qval = 0, smem_qjet = 0;
   int threads_tcv = 0;
   size_t smem_tcv = 0;
   int P_tcv = 0;

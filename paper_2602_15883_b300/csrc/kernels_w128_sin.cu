@@ -30,6 +30,8 @@ KernelSet make_set(int L) {
   k.stash_tc = tc_stash_floats<CJ>(L);
   k.train_val_tc = (const void*)k_pinn_tcv<DS, UNST, ACT, M_TRAIN>;
   k.eval_val_tc = (const void*)k_pinn_tcv<DS, UNST, ACT, M_EVAL>;
+  k.query_val_tc = (const void*)k_pinn_tcv<DS, UNST, ACT, M_QUERY>;
+  k.query_jet_tc = (const void*)k_pinn_tc<DS, UNST, ACT, M_QUERY>;
   k.threads_tcv = NTC;
   k.smem_tcv = tcv_smem_bytes<DOUT>(L);
   k.P_tcv = TcvTile::P;

@@ -145,10 +145,14 @@ __device__ __forceinline__ float block_sum_tc(float v, float* red) {
   return s;   // valid in thread 0
 }
 
-template <int DS, int UNST, int ACT>
+// MODE M_TRAIN: residual items (losses, reverse pass); MODE M_QUERY: jets of
+// routed query points and their residuals (forward only, the anchored
+// pressure of Eq. (18) by a second pass at x_anc for master nets).
+template <int DS, int UNST, int ACT, int MODE = M_TRAIN>
 __global__ void __launch_bounds__(NTC, 1)
     k_pinn_tc(const Shape sh, const Bufs b, const Item* __restrict__ items, const int* __restrict__ n_items_ptr) {
   constexpr int W = 128, DIN = DS + UNST, C = DIN + 2, DOUT = DS + 1;
+  constexpr bool TRAIN = (MODE == M_TRAIN);
   using T = TcTile<C>;
   constexpr int P = T::P, HP = T::HP, NQ = T::NQ, NC = T::NC, RSO = T::RSO;
   constexpr int KQ = W / NQ;   // weight-row columns per thread
@@ -199,7 +203,7 @@ __global__ void __launch_bounds__(NTC, 1)
   tc::fence_after();
   const uint32_t tm = s_tmem;
   uint32_t phase = 0, wphase = 0;
-  float4* const stash = reinterpret_cast<float4*>(b.stash + (size_t)blockIdx.x * b.stash_per_cta);
+  float4* const stash = reinterpret_cast<float4*>(b.stash + (TRAIN ? (size_t)blockIdx.x * b.stash_per_cta : 0));
 
   // MMA issue (one thread) and completion; after a time-out the remaining
   // MMAs and waits are skipped and the host sees ERR_TIMEOUT.
@@ -353,18 +357,26 @@ __global__ void __launch_bounds__(NTC, 1)
     if (t < DOUT) bLs[t] = th[sh.boff[L] + t];
     if (t < 4) s_scale[t] = t < DIN ? ni.scale[t] : 0.f;
     double lsum0 = 0.0;   // thread 0: sum of r^2 over the item
+    const int npass = (!TRAIN && ni.master) ? 2 : 1;
 
     for (int sub = 0; sub < item.count; sub += P) {
       const int npts = min(P, item.count - sub);
       const bool first = (sub == 0);
+      float pkeep = 0.f;   // query: raw pressure of a master point (thread t = point)
+     for (int pass = 0; pass < npass; ++pass) {
       // ---- inputs mapped to the net's box: xh = (x - c) * s
       if (t < P) {
         const bool valid = t < npts;
         float x[4] = {0.f, 0.f, 0.f, 0.f};
         if (valid) {
-          const float* src = b.res_pts + (size_t)(item.begin + sub + t) * DIN;
+          const float* src = TRAIN ? b.res_pts + (size_t)(item.begin + sub + t) * DIN
+                                   : b.q_pts + (size_t)b.q_perm[item.begin + sub + t] * DIN;
 #pragma unroll
           for (int q = 0; q < DIN; ++q) x[q] = src[q];
+          if (pass == 1) {   // p(x_anc, t) at the point's time
+#pragma unroll
+            for (int q = 0; q < DS; ++q) x[q] = sh.anchor[q];
+          }
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) xh[t * 4 + q] = (valid && q < DIN) ? (x[q] - ni.center[q]) * ni.scale[q] : 0.f;
@@ -388,7 +400,7 @@ __global__ void __launch_bounds__(NTC, 1)
           for (int q = 0; q < DIN; ++q) h[1 + q][u] = w[q] * s_scale[q];
           h[C - 1][u] = 0.f;
         }
-        stash_st(0, h);
+        if (TRAIN) stash_st(0, h);
         act_pts(h, a);
         put_act(0, a);
       }
@@ -407,7 +419,7 @@ __global__ void __launch_bounds__(NTC, 1)
         const float bias = bls[(l - 1) * W + nrn];
 #pragma unroll
         for (int u = 0; u < HP; ++u) h[0][u] = stash_value<ACT>(h[0][u] + bias);
-        stash_st(l, h);
+        if (TRAIN) stash_st(l, h);
         act_pts(h, a);
         put_act(l, a);
       }
@@ -437,6 +449,30 @@ __global__ void __launch_bounds__(NTC, 1)
         }
       }
       __syncthreads();
+      if constexpr (!TRAIN) {   // query outputs: (u, p) and the residuals
+        if (t < P && t < npts) {
+          float Y[DOUT][C];
+#pragma unroll
+          for (int j = 0; j < DOUT; ++j)
+#pragma unroll
+            for (int c = 0; c < C; ++c) Y[j][c] = ysm[j * NC + t * C + c];
+          float* o = b.q_out + (size_t)b.q_perm[item.begin + sub + t] * b.q_w;
+          if (pass == 0) {
+#pragma unroll
+            for (int j = 0; j < DS; ++j) o[j] = Y[j][0];
+            if (npass == 1) o[DS] = Y[DS][0] + sh.p_ref;
+            else pkeep = Y[DS][0];
+            float r[DS + 1];
+            ns_residual<DS, UNST, C>(Y, sh.nu, r);
+#pragma unroll
+            for (int j = 0; j <= DS; ++j) o[DOUT + j] = r[j];
+          } else {
+            o[DS] = (pkeep - Y[DS][0]) + sh.p_ref;
+          }
+        }
+        __syncthreads();
+        continue;
+      }
       // ---- residuals, L_PDE and the output adjoint seeds (thread = point)
       float l0 = 0.f;
       if (t < P) {
@@ -461,6 +497,8 @@ __global__ void __launch_bounds__(NTC, 1)
         if (t == 0) lsum0 += (double)s;
       }
       __syncthreads();
+     }   // pass
+      if constexpr (!TRAIN) continue;
       if (b.no_reverse) continue;
 
       // ================= reverse pass =================
@@ -642,7 +680,7 @@ __global__ void __launch_bounds__(NTC, 1)
       }
       __syncthreads();
     }   // sub-tiles
-    if (t == 0) {
+    if (TRAIN && t == 0) {
       double* lp = b.loss_part + (size_t)item.slot * LP;
       for (int q = 0; q < LP; ++q) lp[q] = 0.0;
       lp[1] = lsum0;

@@ -1,11 +1,13 @@
 // Tensor-core (tcgen05, 3xTF32) variant of the value kernels for width 128:
 // k_pinn<128, DS, UNST, false, MODE, ACT> for MODE = M_TRAIN (observation
 // items, L_obs of Eq. (3), and the ghost terms of Eqs. (13)-(15) on face
-// items, with the reverse pass) and MODE = M_EVAL (the exchange of
+// items, with the reverse pass), MODE = M_EVAL (the exchange of
 // Algorithm 1: both sides' (u, p) at the face points and the masters'
-// p(x_anc, t)).  Values only (one channel), 64 points per tile; the hidden
-// contractions run as in k_pinn_tc (operands split into TF32 hi/lo, main and
-// correction products in separate accumulators):
+// p(x_anc, t)) and MODE = M_QUERY (routed query points, with the anchored
+// pressure of Eq. (18) by a second pass at x_anc for master nets).  Values
+// only (one channel), 64 points per tile; the hidden contractions run as in
+// k_pinn_tc (operands split into TF32 hi/lo, main and correction products in
+// separate accumulators):
 //
 //   forward       Z_l       = W_l     a_{l-1}     M = 128 neurons, N = 64 points, K = 128
 //   input adjoint abar_{l-1} = W_l^T  zbar_l      M = 128,         N = 64,        K = 128
@@ -234,19 +236,24 @@ __global__ void __launch_bounds__(NTC, 1)
       }
     }
     double lsum0 = 0.0, lsum1 = 0.0;   // thread 0: loss numerators of the item
+    const int npass = (MODE == M_QUERY && ni.master) ? 2 : 1;
 
     for (int sub = 0; sub < item.count; sub += P) {
       const int npts = min(P, item.count - sub);
       const bool first = (sub == 0);
+      float pkeep = 0.f;   // query: raw pressure of a master point (thread t = point)
+     for (int pass = 0; pass < npass; ++pass) {
       // ---- inputs mapped to the net's box
       if (t < P) {
         const bool valid = t < npts;
         float x[4] = {0.f, 0.f, 0.f, 0.f};
         if (valid) {
-          const float* src = (item.kind == K_OBS ? b.obs_pts : b.face_pts) + (size_t)(item.begin + sub + t) * DIN;
+          const float* src =
+              MODE == M_QUERY ? b.q_pts + (size_t)b.q_perm[item.begin + sub + t] * DIN
+                              : (item.kind == K_OBS ? b.obs_pts : b.face_pts) + (size_t)(item.begin + sub + t) * DIN;
 #pragma unroll
           for (int q = 0; q < DIN; ++q) x[q] = src[q];
-          if (item.kind == K_EVAL_ANC) {   // p(x_anc, t) at the point's time, Eq. (15)
+          if (item.kind == K_EVAL_ANC || pass == 1) {   // p(x_anc, t) at the point's time, Eqs. (15), (18)
 #pragma unroll
             for (int q = 0; q < DS; ++q) x[q] = sh.anchor[q];
           }
@@ -340,6 +347,18 @@ __global__ void __launch_bounds__(NTC, 1)
           }
 #pragma unroll
           for (int j = 0; j < DOUT; ++j) ybsm[j * P + t] = Yb[j];
+        } else if (MODE == M_QUERY) {
+          if (valid) {
+            float* o = b.q_out + (size_t)b.q_perm[item.begin + sub + t] * b.q_w;
+            if (pass == 0) {
+#pragma unroll
+              for (int j = 0; j < DS; ++j) o[j] = Y[j];
+              if (npass == 1) o[DS] = Y[DS] + sh.p_ref;
+              else pkeep = Y[DS];
+            } else {
+              o[DS] = (pkeep - Y[DS]) + sh.p_ref;
+            }
+          }
         } else if (valid) {
           if (item.kind == K_EVAL) {
 #pragma unroll
@@ -358,6 +377,7 @@ __global__ void __launch_bounds__(NTC, 1)
         }
       }
       __syncthreads();
+     }   // pass
       if constexpr (!TRAIN) continue;
       if (b.no_reverse) continue;
 

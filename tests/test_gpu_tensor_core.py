@@ -149,3 +149,42 @@ def test_tf32x3_multi_step_trajectory_tracks_oracle():
         th, m, v, t, oloss = ora.step(th, m, v, t)
         compare_losses(loss, oloss, tol=1e-4)
     assert rel_l2(d.get_state()[0], th) < 1e-4
+
+
+@pytest.mark.parametrize("name", ["beltrami32", "steady3d_w128", "beltrami_sin"])
+@pytest.mark.parametrize("want_res", [False, True])
+def test_tf32x3_queries_match_oracle(name, want_res):
+    """Queries through the tensor-core value / jet kernels (routing, the
+    anchored pressure of Eq. (18) for master cells, residuals)."""
+    import torch
+    from tests.helpers import query_jets, residual_error, residual_term_scale
+    Dpinn = _gpu()
+    cfg, pb = tc_case(name)
+    d = make(Dpinn, cfg, pb)
+    pts = synth.query_points(cfg, 3001, seed=4)
+    out = d.query(torch.from_numpy(pts).cuda(), want_residual=want_res).cpu().numpy()
+    ora = oracle.Oracle(cfg, pb)
+    th = np.asarray(pb.theta0, np.float64)
+    ref, nets, st = ora.query(th, pts, want_res=want_res)
+    assert st == 0
+    do = ora.d_out
+    for c in range(do):
+        assert rel_l2(out[:, c], ref[:, c]) <= 1e-5, (c, rel_l2(out[:, c], ref[:, c]))
+    if want_res:
+        scale = residual_term_scale(query_jets(ora, th, pts, nets), cfg)
+        assert residual_error(out[:, do:], ref[:, do:], scale) <= 1e-5
+
+
+def test_tf32x3_anchor_identity():
+    import torch
+    Dpinn = _gpu()
+    cfg, pb = tc_case("beltrami32")
+    cfg = dict(cfg, p_ref=-0.75)
+    d = make(Dpinn, cfg, pb)
+    ts = np.linspace(0.0, 1.0, 41, dtype=np.float32)
+    pts = np.zeros((41, 4), np.float32)
+    pts[:, :3] = np.asarray(cfg["anchor"][:3], np.float32)
+    pts[:, 3] = ts
+    for want in (False, True):
+        out = d.query(torch.from_numpy(pts).cuda(), want_residual=want).cpu().numpy()
+        assert np.all(out[:, 3] == np.float32(-0.75))
