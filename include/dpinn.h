@@ -187,7 +187,20 @@ int dpinn_face_info(dpinn_t* h, int face, int* net_lo, int* net_hi, int* axis, i
 int dpinn_set_points(dpinn_t* h, int kind, const float* pts, const float* vals,
                      const int64_t* counts, int n_counts);
 
-/* Per-step resampling of the collocation points (mini-batch epochs: fresh
+/* Asynchronous upload of the residual points for the next step (same
+ * counts as the current set; other layouts fall back to dpinn_set_points).
+ * The host -> device copy runs on an internal stream into a staging buffer,
+ * overlapping the work already queued; the next dpinn_step / dpinn_eval_*
+ * waits for it on its own stream and moves the points into place (a
+ * device-to-device copy) before its kernels.  `pts` (pinned host memory for
+ * a true overlap) must stay unchanged until that next call has been issued
+ * and its work has completed.  One upload may be pending at a time.
+ * `stream` is unused (reserved).  Errors: INVALID_ARG (kind other than
+ * RESIDUAL, counts length), STATE (an upload already pending), CUDA. */
+int dpinn_set_points_async(dpinn_t* h, int kind, const float* pts, const int64_t* counts, int n_counts,
+                           dpinn_stream_t stream);
+
+/* Per-step resampling of the collocation points/* Per-step resampling of the collocation points (mini-batch epochs: fresh
  * residual points every step, none stored or copied from the host).  The
  * paper trains on fixed point sets per epoch (Sec. 3, Table B1); this call,
  * which the paper has no counterpart of, draws counts[k] points uniformly in

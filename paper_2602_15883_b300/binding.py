@@ -30,6 +30,7 @@ EXPORTS = (
     "dpinn_eval_loss", "dpinn_set_params", "dpinn_set_schedule", "dpinn_get_schedule",
     "dpinn_qctx_create", "dpinn_qctx_destroy", "dpinn_qctx_query", "dpinn_qctx_status",
     "dpinn_set_resampling", "dpinn_get_points", "dpinn_set_partial_budget", "dpinn_loss_ext",
+    "dpinn_set_points_async",
 )
 
 
@@ -106,6 +107,7 @@ def load_library(path: str = LIB_PATH):
         "dpinn_get_points": ([vp, i32, vp], i32),
         "dpinn_set_partial_budget": ([vp, i64], i32),
         "dpinn_loss_ext": ([vp, vp], i32),
+        "dpinn_set_points_async": ([vp, i32, vp, vp, i32, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -229,6 +231,16 @@ class Dpinn:
         p, kp = _ptr(pts)
         q, kq = _ptr(vals)
         self._check(self.lib.dpinn_set_points(self.h, kind, p, q, counts.ctypes.data, len(counts)))
+
+    def set_points_async(self, kind, pts, counts, stream=None):
+        """Upload the next step's residual points asynchronously (``pts``
+        pinned host memory kept unchanged until that step has completed)."""
+        counts = np.ascontiguousarray(counts, np.int64)
+        p, keep = _ptr(pts)
+        if keep is not pts:   # a temporary copy would not outlive the copy in flight
+            return self.set_points(kind, pts, counts)
+        self._check(self.lib.dpinn_set_points_async(self.h, kind, p, counts.ctypes.data, len(counts),
+                                                    _stream(stream)))
 
     def set_resampling(self, counts, seed=0):
         """Fresh uniform residual points in every net's cell before each step

@@ -114,6 +114,13 @@ struct dpinn {
   bool plan_ok = false;
   int sched_jet = 0, sched_val = 0, sched_order = 0;   // 0 = automatic / longest first
   cudaStream_t cap = nullptr;
+  // asynchronous residual-point upload: host -> staging buffer on copy_st
+  // (overlapping the running step), staging -> res_pts at the next launch
+  cudaStream_t copy_st = nullptr;
+  cudaEvent_t stage_ready = nullptr, stage_free = nullptr;
+  DevBuf<float> res_stage;
+  bool stage_pending = false;
+  size_t stage_bytes = 0;
   cudaGraphExec_t g_step = nullptr, g_grad = nullptr, g_loss = nullptr;
   cudaEvent_t done = nullptr;
   int launches = 0;
@@ -127,6 +134,10 @@ struct dpinn {
     if (g_loss) cudaGraphExecDestroy(g_loss);
     if (done) cudaEventDestroy(done);
     if (cap) cudaStreamDestroy(cap);
+    if (stage_ready) cudaEventDestroy(stage_ready);
+    if (stage_free) cudaEventDestroy(stage_free);
+    if (copy_st) cudaStreamDestroy(copy_st);
+    res_stage.free_();
     if (loss_host) cudaFreeHost(loss_host);
     for (auto* b : {&theta, &thetaT, &m, &v, &grad, &norm_part, &coef, &res_pts, &obs_pts, &obs_vals, &face_pts,
                     &grad_part, &stash, &nbr_val, &nbr_anc, &nbr_res, &nbr_grd, &loss_rec})
@@ -824,6 +835,10 @@ int dpinn_create(const dpinn_config* cfg, dpinn_t** out) {
   if (rc) { g_create_err = h->err; return rc; }
   CK(hp, cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
   CK(hp, cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming));
+  CK(hp, cudaStreamCreateWithFlags(&h->copy_st, cudaStreamNonBlocking));
+  CK(hp, cudaEventCreateWithFlags(&h->stage_ready, cudaEventDisableTiming));
+  CK(hp, cudaEventCreateWithFlags(&h->stage_free, cudaEventDisableTiming));
+  CK(hp, cudaEventRecord(h->stage_free, h->copy_st));
   CK(hp, cudaDeviceSynchronize());
   *out = h.release();
   return DPINN_OK;
@@ -945,6 +960,10 @@ int dpinn_set_points(dpinn_t* h, int kind, const float* pts, const float* vals, 
   if (n > 0 && !pts) return fail(h, DPINN_ERR_INVALID_ARG, "null points");
   if (kind == DPINN_POINTS_OBS && n > 0 && !vals) return fail(h, DPINN_ERR_INVALID_ARG, "null observation values");
   CK(h, cudaSetDevice(h->dev));
+  if (kind == DPINN_POINTS_RESIDUAL && h->stage_pending) {   // the new points replace a pending upload
+    CK(h, cudaStreamSynchronize(h->copy_st));
+    h->stage_pending = false;
+  }
   std::vector<int64_t> cv(counts, counts + n_counts);
   std::vector<int64_t>* dst = kind == 0 ? &h->res_counts : (kind == 1 ? &h->obs_counts : &h->face_counts);
   // points delivered by the caller replace per-step resampling
@@ -970,6 +989,46 @@ int dpinn_set_points(dpinn_t* h, int kind, const float* pts, const float* vals, 
   }
   if (same && h->plan_ok) return DPINN_OK;
   return build_plan(h);
+}
+
+// A pending asynchronous upload enters res_pts on the launching stream just
+// before the work that reads it.
+static int apply_stage(dpinn* h, cudaStream_t s) {
+  if (!h->stage_pending) return DPINN_OK;
+  CK(h, cudaStreamWaitEvent(s, h->stage_ready, 0));
+  CK(h, cudaMemcpyAsync(h->res_pts.p, h->res_stage.p, h->stage_bytes, cudaMemcpyDeviceToDevice, s));
+  CK(h, cudaEventRecord(h->stage_free, s));
+  h->stage_pending = false;
+  return DPINN_OK;
+}
+
+int dpinn_set_points_async(dpinn_t* h, int kind, const float* pts, const int64_t* counts, int n_counts,
+                           dpinn_stream_t stream) {
+  (void)stream;
+  if (!h) return DPINN_ERR_INVALID_ARG;
+  if (kind != DPINN_POINTS_RESIDUAL) return fail(h, DPINN_ERR_INVALID_ARG, "asynchronous upload of residual points only");
+  if (n_counts != h->n_nets || !counts) return fail(h, DPINN_ERR_INVALID_ARG, "counts length mismatch");
+  const bool same = h->have[0] && !h->resample &&
+                    std::equal(counts, counts + n_counts, h->res_counts.begin(), h->res_counts.end());
+  if (!same)   // a new layout needs a new plan: the synchronous path
+    return dpinn_set_points(h, kind, pts, nullptr, counts, n_counts);
+  int64_t n = 0;
+  for (int i = 0; i < n_counts; ++i) n += counts[i];
+  if (n == 0) return DPINN_OK;
+  if (!pts) return fail(h, DPINN_ERR_INVALID_ARG, "null points");
+  CK(h, cudaSetDevice(h->dev));
+  const size_t bytes = (size_t)n * h->din * sizeof(float);
+  if (h->stage_pending) return fail(h, DPINN_ERR_STATE, "an earlier asynchronous upload has not been consumed");
+  if (h->res_stage.n < (size_t)n * h->din) {
+    CK(h, cudaEventSynchronize(h->stage_free));
+    CK(h, h->res_stage.ensure((size_t)n * h->din));
+  }
+  CK(h, cudaStreamWaitEvent(h->copy_st, h->stage_free, 0));   // the previous upload has been moved out
+  CK(h, cudaMemcpyAsync(h->res_stage.p, pts, bytes, cudaMemcpyHostToDevice, h->copy_st));
+  CK(h, cudaEventRecord(h->stage_ready, h->copy_st));
+  h->stage_bytes = bytes;
+  h->stage_pending = true;
+  return DPINN_OK;
 }
 
 int dpinn_set_resampling(dpinn_t* h, const int64_t* counts, int n_counts, uint64_t seed) {
@@ -1050,6 +1109,7 @@ int dpinn_step(dpinn_t* h, dpinn_stream_t stream, int n_steps) {
     if (!h->plan_ok) return fail(h, DPINN_ERR_STATE, "residual, observation and face points must be set first");
   }
   cudaStream_t s = (cudaStream_t)stream;
+  if (int rc = apply_stage(h, s)) return rc;
   for (int i = 0; i < n_steps; ++i) CK(h, cudaGraphLaunch(h->g_step, s));
   CK(h, cudaEventRecord(h->done, s));
   return DPINN_OK;
@@ -1063,6 +1123,7 @@ int dpinn_eval_grad(dpinn_t* h, dpinn_stream_t stream) {
     if (!h->plan_ok) return fail(h, DPINN_ERR_STATE, "residual, observation and face points must be set first");
   }
   cudaStream_t s = (cudaStream_t)stream;
+  if (int rc = apply_stage(h, s)) return rc;
   CK(h, cudaGraphLaunch(h->g_grad, s));
   CK(h, cudaEventRecord(h->done, s));
   return DPINN_OK;
@@ -1076,6 +1137,7 @@ int dpinn_eval_loss(dpinn_t* h, dpinn_stream_t stream) {
     if (!h->plan_ok) return fail(h, DPINN_ERR_STATE, "residual, observation and face points must be set first");
   }
   cudaStream_t s = (cudaStream_t)stream;
+  if (int rc = apply_stage(h, s)) return rc;
   CK(h, cudaGraphLaunch(h->g_loss, s));
   CK(h, cudaEventRecord(h->done, s));
   return DPINN_OK;
@@ -1382,6 +1444,7 @@ int dpinn_step_timed(dpinn_t* h, dpinn_stream_t stream, float* ms, int max_kerne
     if (!h->plan_ok) return fail(h, DPINN_ERR_STATE, "residual, observation and face points must be set first");
   }
   cudaStream_t s = (cudaStream_t)stream;
+  if (int rc = apply_stage(h, s)) return rc;
   cudaEvent_t ev[12];   // at most 8 kernels per step
   for (auto& e : ev) CK(h, cudaEventCreate(&e));
   const char* nm[11] = {nullptr};

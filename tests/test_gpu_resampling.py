@@ -1,5 +1,5 @@
-"""Per-step resampling of the collocation points and the gradient-partial
-memory budget, against the oracle.
+"""Per-step resampling of the collocation points, the gradient-partial memory
+budget and the asynchronous point upload, against the oracle.
 
 The device sampler and the oracle's implement the same counter-based streams
 independently; the sampled float32 coordinates must agree bit for bit, and a
@@ -127,3 +127,30 @@ def test_partial_budget_changes_the_plan_not_the_gradient():
     d.set_partial_budget(0)          # back to the default plan
     d.eval_grad()
     np.testing.assert_array_equal(d.grad(), g0)
+
+
+def test_async_upload_equals_synchronous_upload():
+    """Points uploaded asynchronously for the next step give bit-identical
+    steps to synchronous uploads (which the parity tests tie to the oracle)."""
+    import torch
+    Dpinn = _gpu()
+    cfg, pb = small_case("tgv")
+    rng = np.random.default_rng(8)
+    sets = [np.ascontiguousarray(pb.res_pts + rng.normal(scale=1e-3, size=pb.res_pts.shape), np.float32)
+            for _ in range(3)]
+    a = Dpinn(cfg)
+    a.set_problem(pb)
+    b = Dpinn(cfg)
+    b.set_problem(pb)
+    pinned = [torch.from_numpy(x).pin_memory() for x in sets]
+    b.set_points_async(RESIDUAL, pinned[0], pb.res_counts)
+    for i in range(3):
+        a.set_points(RESIDUAL, sets[i], pb.res_counts)
+        a.step(1)
+        b.step(1)
+        if i + 1 < 3:
+            b.set_points_async(RESIDUAL, pinned[i + 1], pb.res_counts)
+        np.testing.assert_array_equal(a.loss(), b.loss())
+    for x, y in zip(a.get_state()[:3], b.get_state()[:3]):
+        np.testing.assert_array_equal(x, y)
+    np.testing.assert_array_equal(b.get_points(RESIDUAL, int(pb.res_counts.sum())), sets[2])
