@@ -187,7 +187,16 @@ int dpinn_face_info(dpinn_t* h, int face, int* net_lo, int* net_hi, int* axis, i
 int dpinn_set_points(dpinn_t* h, int kind, const float* pts, const float* vals,
                      const int64_t* counts, int n_counts);
 
-/* Asynchronous upload of the residual points for the next step (same
+/* Self-test of failure detection (no counterpart in the paper): runs a
+ * one-block kernel that waits, with the same bounded wait the kernels use
+ * for their copies and MMAs, on an mbarrier that nothing ever completes.
+ * Expected result: DPINN_ERR_TIMEOUT after about 2 s; the kernel returns
+ * normally, so the CUDA context and the handle stay usable (the handle's own
+ * error words are not touched).  STATE if the wait returned without giving
+ * up.  Synchronises the device. */
+int dpinn_selftest_wait(dpinn_t* h);
+
+/* Asynchronous upload of the residual points for the next step/* Asynchronous upload of the residual points for the next step (same
  * counts as the current set; other layouts fall back to dpinn_set_points).
  * The host -> device copy runs on an internal stream into a staging buffer,
  * overlapping the work already queued; the next dpinn_step / dpinn_eval_*

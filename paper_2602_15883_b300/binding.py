@@ -30,7 +30,7 @@ EXPORTS = (
     "dpinn_eval_loss", "dpinn_set_params", "dpinn_set_schedule", "dpinn_get_schedule",
     "dpinn_qctx_create", "dpinn_qctx_destroy", "dpinn_qctx_query", "dpinn_qctx_status",
     "dpinn_set_resampling", "dpinn_get_points", "dpinn_set_partial_budget", "dpinn_loss_ext",
-    "dpinn_set_points_async",
+    "dpinn_set_points_async", "dpinn_selftest_wait",
 )
 
 
@@ -108,6 +108,7 @@ def load_library(path: str = LIB_PATH):
         "dpinn_set_partial_budget": ([vp, i64], i32),
         "dpinn_loss_ext": ([vp, vp], i32),
         "dpinn_set_points_async": ([vp, i32, vp, vp, i32, vp], i32),
+        "dpinn_selftest_wait": ([vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

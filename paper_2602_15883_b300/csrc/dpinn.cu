@@ -1031,6 +1031,22 @@ int dpinn_set_points_async(dpinn_t* h, int kind, const float* pts, const int64_t
   return DPINN_OK;
 }
 
+int dpinn_selftest_wait(dpinn_t* h) {
+  if (!h) return DPINN_ERR_INVALID_ARG;
+  CK(h, cudaSetDevice(h->dev));
+  DevBuf<int> e;
+  CK(h, e.ensure(3));
+  CK(h, cudaMemset(e.p, 0, 3 * sizeof(int)));
+  dk::k_selftest_wait<<<1, 32>>>(e.p);
+  CK(h, cudaGetLastError());
+  CK(h, cudaDeviceSynchronize());
+  int w[3] = {0, 0, 0};
+  CK(h, cudaMemcpy(w, e.p, sizeof(w), cudaMemcpyDeviceToHost));
+  e.free_();
+  if (w[dk::ERR_TIMEOUT]) return fail(h, DPINN_ERR_TIMEOUT, "self-test: the bounded wait gave up as designed");
+  return fail(h, DPINN_ERR_STATE, "self-test: a wait that nothing completes returned without a time-out");
+}
+
 int dpinn_set_resampling(dpinn_t* h, const int64_t* counts, int n_counts, uint64_t seed) {
   if (!h) return DPINN_ERR_INVALID_ARG;
   if (!counts) {

@@ -246,4 +246,14 @@ __global__ void k_sample(int din, uint64_t seed, const long long* __restrict__ s
   }
 }
 
+// Self-test of the bounded device waits: an mbarrier that nothing ever
+// completes.  mbar_wait gives up after about 2 s and raises ERR_TIMEOUT in
+// `err`; the kernel then returns normally.
+__global__ void k_selftest_wait(int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  mbar_wait(&bar, 0, err);
+}
+
 }  // namespace dk
