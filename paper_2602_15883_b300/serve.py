@@ -30,7 +30,7 @@ import numpy as np
 ERR_INVALID_ARG = -1   # include/dpinn.h: DPINN_ERR_INVALID_ARG (an outside point)
 
 
-@dataclass
+@dataclass(eq=False)   # requests compare by identity: their point arrays do not compare
 class Request:
     pts: np.ndarray
     want_residual: bool
@@ -40,6 +40,7 @@ class Request:
     error: str | None = None
     rid: int = 0
     retries: int = 0
+    cancelled: bool = False
     done: threading.Event = field(default_factory=threading.Event)
 
     @property
@@ -134,6 +135,22 @@ class Server:
             self.pending.append(r)
             self.lock.notify()
         return r
+
+    def cancel(self, r: Request) -> bool:
+        """Withdraw a request: a waiting one leaves the queue at once; one
+        already on the GPU finishes there but its result is dropped.  Both end
+        with error "cancelled" (True); a finished request is left as it is
+        (False)."""
+        with self.lock:
+            if r.done.is_set():
+                return False
+            r.cancelled = True
+            if r in self.pending:
+                self.pending.remove(r)
+                r.error = "cancelled"
+                r.t_done = time.perf_counter()
+                r.done.set()
+        return True
 
     def _width(self, r):
         return self.w_res if r.want_residual else self.w_val
@@ -240,7 +257,9 @@ class Server:
                 finished, retry = [], []
                 off = 0
                 for r in b[key_reqs]:
-                    if st == 0:
+                    if r.cancelled:
+                        r.error = "cancelled"
+                    elif st == 0:
                         r.result = h[off:off + r.n].copy()
                     elif (st == ERR_INVALID_ARG and r.retries == 0 and
                           np.all((r.pts >= self.lo) & (r.pts <= self.hi))):

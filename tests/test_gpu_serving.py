@@ -92,3 +92,20 @@ def test_bad_requests_fail_alone():
         assert good.error is None and good.result.shape == (100, 4)
     finally:
         srv.stop()
+
+
+def test_cancelled_requests_end_alone():
+    cfg, pb, d, srv = _server(slots=1)
+    try:
+        first = srv.submit(synth.query_points(cfg, 200000, seed=3), True)     # occupies the only slot
+        waiting = srv.submit(synth.query_points(cfg, 1000, seed=4))
+        other = srv.submit(synth.query_points(cfg, 1000, seed=5))
+        assert srv.cancel(waiting)
+        for r in (first, waiting, other):
+            r.done.wait()
+        assert waiting.error == "cancelled" and waiting.result is None
+        assert first.error is None and first.result.shape == (200000, 8)
+        assert other.error is None and other.result.shape == (1000, 4)
+        assert not srv.cancel(other)          # already finished
+    finally:
+        srv.stop()
