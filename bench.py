@@ -363,22 +363,36 @@ def main():
 
     # ---- end to end through the C ABI with host buffers: every step's points
     # are copied from pinned host memory (two buffers, alternating) and its
-    # loss record read back; the upload of step i + 1 overlaps step i
+    # loss record copied back into pinned memory and read on the host.  The
+    # loop keeps one step queued ahead: the upload of step i + 1 overlaps
+    # step i, and the host reads step i's losses while step i + 1 runs.
     pinned = [torch.from_numpy(np.ascontiguousarray(pb.res_pts, np.float32)).pin_memory() for _ in range(2)]
     counts = pb.res_counts
+    lbuf = [torch.zeros((d.n_nets, 6), dtype=torch.float32).pin_memory() for _ in range(2)]
+    lev = [torch.cuda.Event() for _ in range(2)]
     out = np.zeros((d.n_nets, 6), np.float32)
+    losses_read = 0
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
     e2e_steps = max(3, args.steps // 2)
     d.set_points_async(POINTS_RESIDUAL, pinned[0], counts)
-    for i in range(e2e_steps):
-        d.step(1, stream)
-        if i + 1 < e2e_steps:
-            d.set_points_async(POINTS_RESIDUAL, pinned[(i + 1) % 2], counts)
-        out = d.loss()
+    for i in range(e2e_steps + 1):
+        if i < e2e_steps:
+            d.step(1, stream)
+            d.loss_async(lbuf[i % 2], stream)
+            lev[i % 2].record(stream)
+            if i + 1 < e2e_steps:
+                d.set_points_async(POINTS_RESIDUAL, pinned[(i + 1) % 2], counts)
+        if i > 0:   # the losses of step i - 1
+            lev[(i - 1) % 2].synchronize()
+            out = lbuf[(i - 1) % 2].numpy().copy()
+            losses_read += 1
+            if not np.all(np.isfinite(out)):
+                raise FloatingPointError(f"non-finite loss at end-to-end step {i - 1}")
     torch.cuda.synchronize()
+    assert losses_read == e2e_steps
     e2e_s = time.perf_counter() - t0
     if dist:
         (e2e_s,) = max_over_ranks(dist, [e2e_s], "cuda")

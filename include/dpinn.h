@@ -266,6 +266,17 @@ int dpinn_set_params(dpinn_t* h, const float* params);
  * filled), TIMEOUT (a device wait gave up), CUDA. */
 int dpinn_loss(dpinn_t* h, float* host_out);
 
+/* Asynchronous form of dpinn_loss for pipelined training loops: enqueue on
+ * `stream`, after the work already queued there, a copy of the loss record
+ * [n_nets][6] into host_out and return without waiting.  The caller owns
+ * host_out (pinned host memory, else the copy is synchronous); its contents
+ * are valid once `stream` has reached this point (an event recorded after
+ * the call).  Call it on the stream the step ran on, before the next step
+ * is queued there, which overwrites the record.  The device error flags are
+ * not read: NONFINITE and TIMEOUT stay set and are reported by the next
+ * dpinn_loss / dpinn_loss_ext.  Errors: INVALID_ARG, CUDA. */
+int dpinn_loss_async(dpinn_t* h, float* host_out, dpinn_stream_t stream);
+
 /* As dpinn_loss with the 8-entry record [n_nets][8]: the 6 entries above
  * (the total includes the interface terms), then L_gh_r and L_gh_c1. */
 int dpinn_loss_ext(dpinn_t* h, float* host_out);

@@ -30,7 +30,7 @@ EXPORTS = (
     "dpinn_eval_loss", "dpinn_set_params", "dpinn_set_schedule", "dpinn_get_schedule",
     "dpinn_qctx_create", "dpinn_qctx_destroy", "dpinn_qctx_query", "dpinn_qctx_status",
     "dpinn_set_resampling", "dpinn_get_points", "dpinn_set_partial_budget", "dpinn_loss_ext",
-    "dpinn_set_points_async", "dpinn_selftest_wait",
+    "dpinn_set_points_async", "dpinn_selftest_wait", "dpinn_loss_async",
 )
 
 
@@ -109,6 +109,7 @@ def load_library(path: str = LIB_PATH):
         "dpinn_loss_ext": ([vp, vp], i32),
         "dpinn_set_points_async": ([vp, i32, vp, vp, i32, vp], i32),
         "dpinn_selftest_wait": ([vp], i32),
+        "dpinn_loss_async": ([vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -300,6 +301,18 @@ class Dpinn:
         if check:
             self._check(rc)
         return out
+
+    def loss_async(self, out, stream=None):
+        """Queue a copy of the loss record [n_nets][6] into ``out`` (a pinned
+        float32 host tensor or array owned by the caller) on ``stream`` and
+        return at once; ``out`` is valid once the stream reaches this point."""
+        p, keep = _ptr(out)
+        if keep is not out or tuple(out.shape) != (self.n_nets, 6) or str(out.dtype) not in ("float32",
+                                                                                               "torch.float32"):
+            raise ValueError("loss_async needs a contiguous float32 [n_nets][6] host buffer")
+        if getattr(out, "is_cuda", False):
+            raise ValueError("loss_async writes host memory")
+        self._check(self.lib.dpinn_loss_async(self.h, p, _stream(stream)))
 
     def loss_ext(self, check=True):
         """Loss record with the interface terms: [n_nets][8] (L_obs, L_PDE,

@@ -108,12 +108,20 @@ struct dpinn {
   int grid_eval = 0, grid_jet = 0, grid_val = 0, grid_jf = 0;
   // interface residual / C1 terms on (face items train with jets)
   bool iface = false;
-  DevBuf<float> grad_part, stash, nbr_val, nbr_anc, nbr_res, nbr_grd, loss_rec;
+  // stash: the jet kernel's per-CTA activation stash; stash_side: the same for
+  // the kernels of the step's side branch (face jets, values), which run
+  // concurrently with the jet kernel
+  DevBuf<float> grad_part, stash, stash_side, nbr_val, nbr_anc, nbr_res, nbr_grd, loss_rec;
   DevBuf<double> loss_part;
   float* loss_host = nullptr;
   bool plan_ok = false;
   int sched_jet = 0, sched_val = 0, sched_order = 0;   // 0 = automatic / longest first
   cudaStream_t cap = nullptr;
+  // second capture stream: exchange, face-jet and value items fork off the
+  // residual-point jet kernel (which needs no neighbour messages) and join
+  // before the gradient reduction
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   // asynchronous residual-point upload: host -> staging buffer on copy_st
   // (overlapping the running step), staging -> res_pts at the next launch
   cudaStream_t copy_st = nullptr;
@@ -134,19 +142,22 @@ struct dpinn {
     if (g_loss) cudaGraphExecDestroy(g_loss);
     if (done) cudaEventDestroy(done);
     if (cap) cudaStreamDestroy(cap);
+    if (side) cudaStreamDestroy(side);
+    if (fork_ev) cudaEventDestroy(fork_ev);
+    if (join_ev) cudaEventDestroy(join_ev);
     if (stage_ready) cudaEventDestroy(stage_ready);
     if (stage_free) cudaEventDestroy(stage_free);
     if (copy_st) cudaStreamDestroy(copy_st);
     res_stage.free_();
     if (loss_host) cudaFreeHost(loss_host);
     for (auto* b : {&theta, &thetaT, &m, &v, &grad, &norm_part, &coef, &res_pts, &obs_pts, &obs_vals, &face_pts,
-                    &grad_part, &stash, &nbr_val, &nbr_anc, &nbr_res, &nbr_grd, &loss_rec})
+                    &grad_part, &stash, &stash_side, &nbr_val, &nbr_anc, &nbr_res, &nbr_grd, &loss_rec})
       b->free_();
     step_d.free_(); nets_d.free_(); loss_part.free_();
     for (auto* b : {&face_info_d, &err_d, &counters, &n_items_d, &slot_begin_d, &iota_d, &q_net, &q_perm,
                     &q_counts, &q_off, &q_cursor, &q_nitems})
       b->free_();
-    items_eval.free_(); items_jet.free_(); items_val.free_(); q_items.free_();
+    items_eval.free_(); items_jet.free_(); items_val.free_(); items_jf.free_(); q_items.free_();
   }
 };
 
@@ -244,44 +255,65 @@ cudaError_t enqueue_step(dpinn* h, int mode, cudaStream_t s, int* n_launch, cuda
     ++launches;
     mark("sample");
   }
+  b.no_reverse = (mode == RUN_LOSS) ? 1 : 0;
+  // The residual-point jet items need no neighbour messages: without timing
+  // events the exchange, face-jet and value items run on a side branch
+  // (stream `side`, own stash) concurrently with them.  Timed runs keep
+  // the kernels in sequence so that each gets its own interval.
+  const bool fork = (ev == nullptr) && h->n_jet > 0 && (h->n_eval + h->n_val + h->n_jf) > 0;
+  cudaStream_t s2 = fork ? h->side : s;
+  if (e == cudaSuccess && fork) {
+    e = cudaEventRecord(h->fork_ev, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, h->fork_ev, 0);
+  }
+  auto run_jet = [&]() {
+    if (e == cudaSuccess && h->n_jet) {
+      dk::Bufs bb = b;
+      bb.counter = h->counters.p + 1;
+      bb.stash_per_cta = h->ks.stash_train_jet;
+      e = launch_pinn(h->ks.train_jet_run, h->grid_jet, h->ks.smem_train_jet, h->shape, bb, h->items_jet.p,
+                      h->n_items_d.p + 1, s, h->ks.threads_train_jet);
+      ++launches;
+      mark("train_jet");
+    }
+  };
+  if (fork) run_jet();
   if (e == cudaSuccess && h->n_eval) {
     dk::Bufs bb = b;
     bb.counter = h->counters.p + 0;
+    bb.no_reverse = 0;
     if (h->iface)   // the messages include the residual and first derivatives
       e = launch_pinn(h->ks.eval_jet, h->grid_eval, h->ks.smem_jet, h->shape, bb, h->items_eval.p, h->n_items_d.p + 0,
-                      s);
+                      s2);
     else
       e = launch_pinn(h->ks.eval_val_run, h->grid_eval, h->ks.smem_val_run, h->shape, bb, h->items_eval.p,
-                      h->n_items_d.p + 0, s, h->ks.threads_val_run);
+                      h->n_items_d.p + 0, s2, h->ks.threads_val_run);
     ++launches;
     mark("exchange");
   }
-  b.no_reverse = (mode == RUN_LOSS) ? 1 : 0;
-  if (e == cudaSuccess && h->n_jet) {
-    dk::Bufs bb = b;
-    bb.counter = h->counters.p + 1;
-    bb.stash_per_cta = h->ks.stash_train_jet;
-    e = launch_pinn(h->ks.train_jet_run, h->grid_jet, h->ks.smem_train_jet, h->shape, bb, h->items_jet.p,
-                    h->n_items_d.p + 1, s, h->ks.threads_train_jet);
-    ++launches;
-    mark("train_jet");
-  }
+  if (!fork) run_jet();
   if (e == cudaSuccess && h->n_jf) {   // face items with the interface jet terms (FP32 jet kernel)
     dk::Bufs bb = b;
     bb.counter = h->counters.p + 3;
+    bb.stash = fork ? h->stash_side.p : h->stash.p;
     bb.stash_per_cta = h->ks.stash_jet;
-    e = launch_pinn(h->ks.train_jet, h->grid_jf, h->ks.smem_jet, h->shape, bb, h->items_jf.p, h->n_items_d.p + 3, s);
+    e = launch_pinn(h->ks.train_jet, h->grid_jf, h->ks.smem_jet, h->shape, bb, h->items_jf.p, h->n_items_d.p + 3, s2);
     ++launches;
     mark("train_face_jets");
   }
   if (e == cudaSuccess && h->n_val) {
     dk::Bufs bb = b;
     bb.counter = h->counters.p + 2;
+    bb.stash = fork ? h->stash_side.p : h->stash.p;
     bb.stash_per_cta = h->ks.stash_val_run;
     e = launch_pinn(h->ks.train_val_run, h->grid_val, h->ks.smem_val_run, h->shape, bb, h->items_val.p,
-                    h->n_items_d.p + 2, s, h->ks.threads_val_run);
+                    h->n_items_d.p + 2, s2, h->ks.threads_val_run);
     ++launches;
     mark("train_val");
+  }
+  if (e == cudaSuccess && fork) {
+    e = cudaEventRecord(h->join_ev, s2);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->join_ev, 0);
   }
   const int nblk = (h->n_params + dk::NT - 1) / dk::NT;
   if (e == cudaSuccess && mode != RUN_LOSS) {
@@ -306,7 +338,7 @@ cudaError_t enqueue_step(dpinn* h, int mode, cudaStream_t s, int* n_launch, cuda
     mark("adam");
   }
   if (e == cudaSuccess) {
-    dk::k_loss_record<<<(h->n_nets + 127) / 128, 128, 0, s>>>(h->shape, h->loss_part.p, h->slot_begin_d.p,
+    dk::k_loss_record<<<(h->n_nets + 3) / 4, 128, 0, s>>>(h->shape, h->loss_part.p, h->slot_begin_d.p,
                                                              h->nets_d.p, h->n_nets, h->loss_rec.p, h->err_d.p,
                                                              h->step_d.p, with_adam ? 1 : 0);
     e = cudaGetLastError();
@@ -493,9 +525,10 @@ int build_plan(dpinn* h) {
   CK(h, h->grad_part.ensure((size_t)std::max(slot, 1) * h->npp));
   CK(h, h->loss_part.ensure((size_t)std::max(slot, 1) * dk::LP));
   CK(h, cudaMemset(h->loss_part.p, 0, (size_t)std::max(slot, 1) * dk::LP * sizeof(double)));
-  const size_t st = std::max({(size_t)h->grid_jet * h->ks.stash_train_jet, (size_t)h->grid_val * h->ks.stash_val_run,
-                              (size_t)h->grid_jf * h->ks.stash_jet});
+  const size_t st = (size_t)h->grid_jet * h->ks.stash_train_jet;
+  const size_t st_side = std::max((size_t)h->grid_val * h->ks.stash_val_run, (size_t)h->grid_jf * h->ks.stash_jet);
   CK(h, h->stash.ensure(std::max<size_t>(st, 4)));
+  CK(h, h->stash_side.ensure(std::max<size_t>(st_side, 4)));
   CK(h, h->nbr_val.ensure((size_t)std::max<int64_t>(n_face_pts, 1) * 2 * h->dout));
   CK(h, h->nbr_anc.ensure((size_t)std::max<int64_t>(n_face_pts, 1) * 2));
   if (h->iface) {
@@ -834,6 +867,9 @@ int dpinn_create(const dpinn_config* cfg, dpinn_t** out) {
   int rc = refresh_transpose(hp);
   if (rc) { g_create_err = h->err; return rc; }
   CK(hp, cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  CK(hp, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+  CK(hp, cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+  CK(hp, cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming));
   CK(hp, cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming));
   CK(hp, cudaStreamCreateWithFlags(&h->copy_st, cudaStreamNonBlocking));
   CK(hp, cudaEventCreateWithFlags(&h->stage_ready, cudaEventDisableTiming));
@@ -1195,6 +1231,14 @@ int dpinn_loss(dpinn_t* h, float* host_out) {
   CK(h, cudaMemcpy2D(host_out, 6 * sizeof(float), h->loss_rec.p, 8 * sizeof(float), 6 * sizeof(float), h->n_nets,
                      cudaMemcpyDeviceToHost));
   return check_errors(h);
+}
+
+int dpinn_loss_async(dpinn_t* h, float* host_out, dpinn_stream_t stream) {
+  if (!h || !host_out) return DPINN_ERR_INVALID_ARG;
+  // the first 6 of the 8 entries per net, in stream order after the step
+  CK(h, cudaMemcpy2DAsync(host_out, 6 * sizeof(float), h->loss_rec.p, 8 * sizeof(float), 6 * sizeof(float),
+                          h->n_nets, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  return DPINN_OK;
 }
 
 int dpinn_loss_ext(dpinn_t* h, float* host_out) {

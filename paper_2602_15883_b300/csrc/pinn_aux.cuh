@@ -102,12 +102,21 @@ __global__ void k_transpose(const Shape sh, const float* __restrict__ theta, flo
 __global__ void k_loss_record(const Shape sh, const double* __restrict__ loss_part, const int* __restrict__ slot_begin,
                               const NetInfo* __restrict__ nets, int n_nets, float* __restrict__ rec, int* err,
                               long long* step, int bump) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k == 0 && bump) *step += 1;
+  // one warp per net: lane j sums slots j, j + 32, ... in order, then a
+  // fixed shuffle tree; lane 0's total is the recorded value
+  const int lane = threadIdx.x & 31;
+  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && bump) *step += 1;
   if (k >= n_nets) return;
   double s[LP] = {0, 0, 0, 0, 0, 0, 0};
-  for (int i = slot_begin[k]; i < slot_begin[k + 1]; ++i)
+  for (int i = slot_begin[k] + lane; i < slot_begin[k + 1]; i += 32)
+#pragma unroll
     for (int q = 0; q < LP; ++q) s[q] += loss_part[(size_t)i * LP + q];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int q = 0; q < LP; ++q) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
+  if (lane != 0) return;
   const NetInfo ni = nets[k];
   const double lo = s[0] * ni.inv_nobs, lp = s[1] * ni.inv_npde, lu = s[2] * ni.inv_ngh,
                ls = s[3] * ni.inv_ngh, lt = s[4] * ni.inv_ngh, lr = s[5] * ni.inv_ngh, lc = s[6] * ni.inv_ngh;

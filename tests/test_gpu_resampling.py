@@ -154,3 +154,26 @@ def test_async_upload_equals_synchronous_upload():
     for x, y in zip(a.get_state()[:3], b.get_state()[:3]):
         np.testing.assert_array_equal(x, y)
     np.testing.assert_array_equal(b.get_points(RESIDUAL, int(pb.res_counts.sum())), sets[2])
+
+
+def test_async_loss_read_equals_synchronous_read():
+    """Loss records queued with loss_async while later steps are already
+    queued on the same stream equal the synchronous reads step by step."""
+    import torch
+    Dpinn = _gpu()
+    cfg, pb = small_case("tgv")
+    a = Dpinn(cfg)
+    a.set_problem(pb)
+    b = Dpinn(cfg)
+    b.set_problem(pb)
+    bufs = [torch.full((b.n_nets, 6), -1.0, dtype=torch.float32).pin_memory() for _ in range(3)]
+    s = torch.cuda.Stream()
+    for i in range(3):
+        b.step(1, s)
+        b.loss_async(bufs[i], s)
+    s.synchronize()
+    for i in range(3):
+        a.step(1)
+        np.testing.assert_array_equal(bufs[i].numpy(), a.loss())
+    with pytest.raises(ValueError):
+        b.loss_async(np.zeros((b.n_nets, 6)), s)    # float64
