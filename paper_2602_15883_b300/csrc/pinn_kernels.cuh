@@ -95,18 +95,20 @@ struct Bufs {
 };
 
 // ------------------------------------------------------------ tiling ---
-// Register tiles.  Shared memory delivers 128 B per clock per SM whatever
-// the broadcast, against 128 FFMA per clock, so a thread tile needs >= 4 FMA
-// per float it loads: TM neurons x (TP points x C channels) gives
-// TM*NCOL / (TM + NCOL).  W = 64 uses 8 neurons per thread; W = 128 is held
-// to 4 by the shared-memory capacity of its activation buffers.
+// Register tiles.  Shared memory reads at most 128 distinct bytes per clock
+// per SM, against 128 FFMA per clock, so a thread tile wants about 4 FMA per
+// float it loads: TM neurons x (TP points x C channels) gives
+// TM*NCOL / (TM + NCOL).  W = 64 uses 8 neurons per thread (and 8 points per
+// thread for values: 256-point value tiles, measured 11 % faster than 128 on
+// the TGV value and exchange items); W = 128 is held to 4 neurons by the
+// shared-memory capacity of its activation buffers.
 template <int W, int C>
 struct Tile {
   static constexpr int TM = (W == 64) ? 8 : 4;    // neurons per thread
   static constexpr int NG = W / TM;               // neuron groups
   static constexpr int PG = NT / NG;              // point groups
   static constexpr int TP = (W == 128) ? (C == 1 ? 8 : (C == 4 ? 4 : 2))
-                          : (W == 64) ? (C == 1 ? 4 : (C == 6 ? 1 : 2))
+                          : (W == 64) ? (C == 1 ? 8 : (C == 6 ? 1 : 2))
                           : 2;                    // points per thread
   static constexpr int P = PG * TP;               // points per tile
   static constexpr int NCOL = TP * C;             // columns per thread
@@ -118,7 +120,7 @@ struct Tile {
   // shared-memory phase store (8 rows apart when TM = 8).  Chosen with a
   // wavefront model of every access pattern of the kernel.
   static constexpr int RS0 = ((PC + 27) / 32) * 32 + 4;
-  static constexpr int SK = (W == 64) ? (C == 1 ? 16 : (C == 4 ? 4 : 8)) : 0;
+  static constexpr int SK = (W == 64) ? ((C == 1 || C == 4) ? 4 : 8) : 0;
   static constexpr int SKM = (W == 64) ? ((C == 1 || C == 4) ? 2 : 4) : 1;
   static constexpr int RS = (RS0 >= PC + SK * (SKM - 1)) ? RS0 : RS0 + 32 * ((PC + SK * (SKM - 1) - RS0 + 31) / 32);
   __host__ __device__ static constexpr int row(int i) { return i * RS + SK * ((i / TM) % SKM); }
