@@ -101,7 +101,10 @@ typedef struct dpinn_config {
   double lo[4], hi[4];    /* global box per input axis */
   int splits[4];          /* cells per input axis */
   int depth;              /* hidden layers L (2..16) */
-  int width;              /* neurons per hidden layer: 32, 64 or 128 */
+  int width;              /* neurons per hidden layer: 32, 64, or 128..224
+                             (32, 64, 128: register-tiled kernels; 129..224, e.g.
+                             the cylinder networks' 150 and 200 of Sec. 5: the
+                             streamed-weight kernel, padded to 160 or 224) */
   int activation;         /* DPINN_ACT_TANH or DPINN_ACT_SIN */
   double nu;              /* kinematic viscosity = 1/Re */
   double anchor_x[3];     /* x_anc (spatial) */

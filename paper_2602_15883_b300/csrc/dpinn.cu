@@ -31,6 +31,8 @@ bool pick_kernels(int W, int ds, int unst, int L, int act, KernelSet* k) {
   if (W == 32) return sn ? dk::kernels_w32_sin(ds, unst, L, k) : dk::kernels_w32_tanh(ds, unst, L, k);
   if (W == 64) return sn ? dk::kernels_w64_sin(ds, unst, L, k) : dk::kernels_w64_tanh(ds, unst, L, k);
   if (W == 128) return sn ? dk::kernels_w128_sin(ds, unst, L, k) : dk::kernels_w128_tanh(ds, unst, L, k);
+  if (W > 128 && W <= 160) return sn ? dk::kernels_wide160_sin(ds, unst, L, k) : dk::kernels_wide160_tanh(ds, unst, L, k);
+  if (W > 160 && W <= 224) return sn ? dk::kernels_wide224_sin(ds, unst, L, k) : dk::kernels_wide224_tanh(ds, unst, L, k);
   return false;
 }
 
@@ -233,6 +235,12 @@ int build_plan(dpinn* h);
 // Step modes: the training step, gradients without the update, losses only.
 enum { RUN_STEP = 0, RUN_GRAD = 1, RUN_LOSS = 2 };
 
+// A training launch writes grid x stash_per_cta floats of its stash buffer:
+// refuse (host side) any launch that the buffer does not cover.
+static bool stash_fits(const DevBuf<float>& buf, int grid, long long per_cta) {
+  return (size_t)std::max(grid, 0) * (size_t)std::max<long long>(per_cta, 0) <= buf.n;
+}
+
 cudaError_t enqueue_step(dpinn* h, int mode, cudaStream_t s, int* n_launch, cudaEvent_t* ev = nullptr,
                          const char** names = nullptr) {
   const bool with_adam = (mode == RUN_STEP);
@@ -271,6 +279,7 @@ cudaError_t enqueue_step(dpinn* h, int mode, cudaStream_t s, int* n_launch, cuda
       dk::Bufs bb = b;
       bb.counter = h->counters.p + 1;
       bb.stash_per_cta = h->ks.stash_train_jet;
+      if (!stash_fits(h->stash, h->grid_jet, bb.stash_per_cta)) { e = cudaErrorInvalidValue; return; }
       e = launch_pinn(h->ks.train_jet_run, h->grid_jet, h->ks.smem_train_jet, h->shape, bb, h->items_jet.p,
                       h->n_items_d.p + 1, s, h->ks.threads_train_jet);
       ++launches;
@@ -295,25 +304,30 @@ cudaError_t enqueue_step(dpinn* h, int mode, cudaStream_t s, int* n_launch, cuda
   if (e == cudaSuccess && h->n_jf) {   // face items with the interface jet terms (FP32 jet kernel)
     dk::Bufs bb = b;
     bb.counter = h->counters.p + 3;
-    bb.stash = fork ? h->stash_side.p : h->stash.p;
+    bb.stash = h->stash_side.p;   // sized for the side kernels, forked or in sequence
     bb.stash_per_cta = h->ks.stash_jet;
-    e = launch_pinn(h->ks.train_jet, h->grid_jf, h->ks.smem_jet, h->shape, bb, h->items_jf.p, h->n_items_d.p + 3, s2);
+    e = stash_fits(h->stash_side, h->grid_jf, bb.stash_per_cta) ? cudaSuccess : cudaErrorInvalidValue;
+    if (e == cudaSuccess)
+      e = launch_pinn(h->ks.train_jet, h->grid_jf, h->ks.smem_jet, h->shape, bb, h->items_jf.p, h->n_items_d.p + 3, s2);
     ++launches;
     mark("train_face_jets");
   }
   if (e == cudaSuccess && h->n_val) {
     dk::Bufs bb = b;
     bb.counter = h->counters.p + 2;
-    bb.stash = fork ? h->stash_side.p : h->stash.p;
+    bb.stash = h->stash_side.p;
     bb.stash_per_cta = h->ks.stash_val_run;
-    e = launch_pinn(h->ks.train_val_run, h->grid_val, h->ks.smem_val_run, h->shape, bb, h->items_val.p,
+    e = stash_fits(h->stash_side, h->grid_val, bb.stash_per_cta) ? cudaSuccess : cudaErrorInvalidValue;
+    if (e == cudaSuccess)
+      e = launch_pinn(h->ks.train_val_run, h->grid_val, h->ks.smem_val_run, h->shape, bb, h->items_val.p,
                     h->n_items_d.p + 2, s2, h->ks.threads_val_run);
     ++launches;
     mark("train_val");
   }
-  if (e == cudaSuccess && fork) {
-    e = cudaEventRecord(h->join_ev, s2);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->join_ev, 0);
+  if (fork) {   // joined even after an error, so that a capture ends cleanly
+    cudaError_t ej = cudaEventRecord(h->join_ev, s2);
+    if (ej == cudaSuccess) ej = cudaStreamWaitEvent(s, h->join_ev, 0);
+    if (e == cudaSuccess) e = ej;
   }
   const int nblk = (h->n_params + dk::NT - 1) / dk::NT;
   if (e == cudaSuccess && mode != RUN_LOSS) {
@@ -671,7 +685,8 @@ int dpinn_create(const dpinn_config* cfg, dpinn_t** out) {
   const dpinn_config& c = *cfg;
   if (c.d_space != 2 && c.d_space != 3) return fail(nullptr, DPINN_ERR_INVALID_ARG, "d_space must be 2 or 3");
   if (c.unsteady != 0 && c.unsteady != 1) return fail(nullptr, DPINN_ERR_INVALID_ARG, "unsteady must be 0 or 1");
-  if (c.width != 32 && c.width != 64 && c.width != 128) return fail(nullptr, DPINN_ERR_INVALID_ARG, "width must be 32, 64 or 128");
+  if (c.width != 32 && c.width != 64 && !(c.width >= 128 && c.width <= 224))
+    return fail(nullptr, DPINN_ERR_INVALID_ARG, "width must be 32, 64 or in [128, 224]");
   if (c.depth < 1 || c.depth > dk::MAXL) return fail(nullptr, DPINN_ERR_INVALID_ARG, "depth must be in [1, 16]");
   if (c.activation != DPINN_ACT_TANH && c.activation != DPINN_ACT_SIN)
     return fail(nullptr, DPINN_ERR_INVALID_ARG, "activation must be tanh or sin");

@@ -59,5 +59,11 @@ bool kernels_w128_tanh(int ds, int unst, int L, KernelSet* k);
 bool kernels_w32_sin(int ds, int unst, int L, KernelSet* k);
 bool kernels_w64_sin(int ds, int unst, int L, KernelSet* k);
 bool kernels_w128_sin(int ds, int unst, int L, KernelSet* k);
+// other widths (the cylinder networks: 150, 200): the streamed-weight kernel
+// k_pinn_w, padded to 160 (widths 129-160) or 224 (161-224)
+bool kernels_wide160_tanh(int ds, int unst, int L, KernelSet* k);
+bool kernels_wide160_sin(int ds, int unst, int L, KernelSet* k);
+bool kernels_wide224_tanh(int ds, int unst, int L, KernelSet* k);
+bool kernels_wide224_sin(int ds, int unst, int L, KernelSet* k);
 
 }  // namespace dk

@@ -432,6 +432,152 @@ __device__ __forceinline__ float pde_seed(const float (&Y)[DS + 1][C], float nu,
   return r2;
 }
 
+// Per-point epilogue of the grouped kernels for point p (tile row sub + p of
+// `item`) with output jets Y[j][c]: TRAIN returns the point's loss terms in
+// l0..l3 and the output-jet adjoints in Yb; EVAL writes the neighbour
+// messages; QUERY writes the output row (masters: pass 0 keeps the raw
+// pressure in pkeep, pass 1 subtracts the anchor value, Eq. (15)).
+template <int DS, int UNST, bool JETS, int MODE, int C>
+__device__ __forceinline__ void point_epilogue(const Shape& sh, const Bufs& b, const Item& item, const NetInfo& ni,
+                                               int sub, int p, bool valid, int pass, int npass, int other_master,
+                                               int is_time, const float (&Y)[DS + 1][C], float (&Yb)[DS + 1][C],
+                                               float& l0, float& l1, float& l2, float& l3, float& pkeep) {
+  constexpr int DIN = DS + UNST;
+  constexpr int DOUT = DS + 1;
+  if constexpr (MODE == M_TRAIN) {
+#pragma unroll
+    for (int j = 0; j < DOUT; ++j)
+#pragma unroll
+      for (int c = 0; c < C; ++c) Yb[j][c] = 0.f;
+    if constexpr (JETS) {
+      if (item.kind == K_PDE) {
+        const float r2 = pde_seed<DS, UNST, C>(Y, sh.nu, valid ? 2.f * sh.lam_pde * ni.inv_npde : 0.f, Yb);
+        l0 = valid ? r2 : 0.f;
+      } else if (valid) {   // K_FACE with the interface terms: C0 on the value channel, r and C1 matching
+        const size_t pt = (size_t)(item.begin + sub + p);
+        const int o = 1 - item.side;
+        const float* nv = b.nbr_val + (pt * 2 + o) * DOUT;
+        float su = 0.f;
+#pragma unroll
+        for (int c = 0; c < DS; ++c) {
+          const float e = Y[c][0] - nv[c];
+          su = fmaf(sh.comp_w[c] * e, e, su);
+          Yb[c][0] = 2.f * sh.lam_gh_u * sh.comp_w[c] * e * ni.inv_ngh;
+        }
+        float Pn = nv[DS];
+        if (other_master) Pn = Pn - b.nbr_anc[pt * 2 + o];   // Eq. (15)
+        const float ep = Y[DS][0] - Pn;
+        const float lam = is_time ? sh.lam_time : ni.lam_space;
+        Yb[DS][0] = 2.f * lam * ep * ni.inv_ngh;
+        l0 = su;
+        l1 = ep * ep;
+        const float* rt = b.nbr_res + (pt * 2 + o) * (DS + 1);
+        l2 = pde_seed<DS, UNST, C>(Y, sh.nu, 2.f * sh.lam_gh_r * ni.inv_ngh, Yb, rt);
+        const float* gt = b.nbr_grd + (pt * 2 + o) * DOUT * DIN;
+        float sc1 = 0.f;
+#pragma unroll
+        for (int c = 0; c < DOUT; ++c)
+#pragma unroll
+          for (int q = 0; q < DIN; ++q) {
+            const float e = Y[c][1 + q] - gt[c * DIN + q];
+            sc1 = fmaf(e, e, sc1);
+            Yb[c][1 + q] = fmaf(2.f * sh.lam_gh_c1 * ni.inv_ngh, e, Yb[c][1 + q]);
+          }
+        l3 = sc1;
+      }
+    } else if (item.kind == K_OBS) {
+      float e[DS];
+#pragma unroll
+      for (int c = 0; c < DS; ++c) e[c] = 0.f;
+      if (valid) {
+        const float* ov = b.obs_vals + (size_t)(item.begin + sub + p) * DS;
+#pragma unroll
+        for (int c = 0; c < DS; ++c) e[c] = Y[c][0] - ov[c];
+      }
+      float s = 0.f;
+#pragma unroll
+      for (int c = 0; c < DS; ++c) {
+        s = fmaf(sh.comp_w[c] * e[c], e[c], s);
+        Yb[c][0] = 2.f * sh.lam_obs * sh.comp_w[c] * e[c] * ni.inv_nobs;
+      }
+      l0 = s;
+    } else {   // K_FACE: own side item.side, neighbour 1 - side
+      float e[DS];
+      float ep = 0.f;
+#pragma unroll
+      for (int c = 0; c < DS; ++c) e[c] = 0.f;
+      if (valid) {
+        const size_t pt = (size_t)(item.begin + sub + p);
+        const int o = 1 - item.side;
+        const float* nv = b.nbr_val + (pt * 2 + o) * DOUT;
+#pragma unroll
+        for (int c = 0; c < DS; ++c) e[c] = Y[c][0] - nv[c];
+        float Pn = nv[DS];
+        if (other_master) Pn = Pn - b.nbr_anc[pt * 2 + o];   // Eq. (15)
+        ep = Y[DS][0] - Pn;
+      }
+      float su = 0.f;
+#pragma unroll
+      for (int c = 0; c < DS; ++c) {
+        su = fmaf(sh.comp_w[c] * e[c], e[c], su);
+        Yb[c][0] = 2.f * sh.lam_gh_u * sh.comp_w[c] * e[c] * ni.inv_ngh;
+      }
+      const float lam = is_time ? sh.lam_time : ni.lam_space;
+      Yb[DS][0] = 2.f * lam * ep * ni.inv_ngh;
+      l0 = su;
+      l1 = ep * ep;
+    }
+  } else if constexpr (MODE == M_EVAL) {
+    if (valid) {
+      const size_t pt = (size_t)(item.begin + sub + p);
+      if (item.kind == K_EVAL) {
+#pragma unroll
+        for (int j = 0; j < DOUT; ++j) b.nbr_val[(pt * 2 + item.side) * DOUT + j] = Y[j][0];
+        if constexpr (JETS) {   // the interface terms' messages: residual and first derivatives
+          float r[DS + 1];
+          ns_residual<DS, UNST, C>(Y, sh.nu, r);
+#pragma unroll
+          for (int j = 0; j <= DS; ++j) b.nbr_res[(pt * 2 + item.side) * (DS + 1) + j] = r[j];
+#pragma unroll
+          for (int c = 0; c < DOUT; ++c)
+#pragma unroll
+            for (int q = 0; q < DIN; ++q)
+              b.nbr_grd[((pt * 2 + item.side) * DOUT + c) * DIN + q] = Y[c][1 + q];
+        }
+      } else {
+        b.nbr_anc[pt * 2 + item.side] = Y[DS][0];
+      }
+    }
+  } else {   // M_QUERY
+    if (valid) {
+      float* o = b.q_out + (size_t)b.q_perm[item.begin + sub + p] * b.q_w;
+      if (pass == 0) {
+#pragma unroll
+        for (int j = 0; j < DS; ++j) o[j] = Y[j][0];
+        if (npass == 1) o[DS] = Y[DS][0] + sh.p_ref;
+        else pkeep = Y[DS][0];
+        if constexpr (JETS) {
+#pragma unroll
+          for (int j = 0; j < DS; ++j) {
+            float v = UNST ? Y[j][1 + DS] : 0.f;
+#pragma unroll
+            for (int i = 0; i < DS; ++i) v = fmaf(Y[i][0], Y[j][1 + i], v);
+            v += Y[DS][1 + j];
+            v = fmaf(-sh.nu, Y[j][C - 1], v);
+            o[DOUT + j] = v;
+          }
+          float dv = 0.f;
+#pragma unroll
+          for (int i = 0; i < DS; ++i) dv += Y[i][1 + i];
+          o[DOUT + DS] = dv;
+        }
+      } else {
+        o[DS] = (pkeep - Y[DS][0]) + sh.p_ref;
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------ the kernel ---
 template <int W, int DS, int UNST, bool JETS, int MODE, int ACT>
 __global__ void __launch_bounds__(NT, 1)
@@ -668,142 +814,14 @@ __global__ void __launch_bounds__(NT, 1)
           for (int j = 0; j < DOUT; ++j)
 #pragma unroll
             for (int c = 0; c < C; ++c) Y[j][c] = ysm[j * RS + p * C + c];
+          float Yb[DOUT][C];
+          point_epilogue<DS, UNST, JETS, MODE, C>(sh, b, item, ni, sub, p, valid, pass, npass, s_other_master,
+                                                  s_is_time, Y, Yb, l0, l1, l2, l3, pkeep);
           if constexpr (MODE == M_TRAIN) {
-            float Yb[DOUT][C];
-#pragma unroll
-            for (int j = 0; j < DOUT; ++j)
-#pragma unroll
-              for (int c = 0; c < C; ++c) Yb[j][c] = 0.f;
-            if constexpr (JETS) {
-             if (item.kind == K_PDE) {
-              const float r2 = pde_seed<DS, UNST, C>(Y, sh.nu, valid ? 2.f * sh.lam_pde * ni.inv_npde : 0.f, Yb);
-              l0 = valid ? r2 : 0.f;
-             } else if (valid) {   // K_FACE with the interface terms: C0 on the value channel, r and C1 matching
-                const size_t pt = (size_t)(item.begin + sub + p);
-                const int o = 1 - item.side;
-                const float* nv = b.nbr_val + (pt * 2 + o) * DOUT;
-                float su = 0.f;
-#pragma unroll
-                for (int c = 0; c < DS; ++c) {
-                  const float e = Y[c][0] - nv[c];
-                  su = fmaf(sh.comp_w[c] * e, e, su);
-                  Yb[c][0] = 2.f * sh.lam_gh_u * sh.comp_w[c] * e * ni.inv_ngh;
-                }
-                float Pn = nv[DS];
-                if (s_other_master) Pn = Pn - b.nbr_anc[pt * 2 + o];   // Eq. (15)
-                const float ep = Y[DS][0] - Pn;
-                const float lam = s_is_time ? sh.lam_time : ni.lam_space;
-                Yb[DS][0] = 2.f * lam * ep * ni.inv_ngh;
-                l0 = su;
-                l1 = ep * ep;
-                const float* rt = b.nbr_res + (pt * 2 + o) * (DS + 1);
-                l2 = pde_seed<DS, UNST, C>(Y, sh.nu, 2.f * sh.lam_gh_r * ni.inv_ngh, Yb, rt);
-                const float* gt = b.nbr_grd + (pt * 2 + o) * DOUT * DIN;
-                float sc1 = 0.f;
-#pragma unroll
-                for (int c = 0; c < DOUT; ++c)
-#pragma unroll
-                  for (int q = 0; q < DIN; ++q) {
-                    const float e = Y[c][1 + q] - gt[c * DIN + q];
-                    sc1 = fmaf(e, e, sc1);
-                    Yb[c][1 + q] = fmaf(2.f * sh.lam_gh_c1 * ni.inv_ngh, e, Yb[c][1 + q]);
-                  }
-                l3 = sc1;
-             }
-            } else if (item.kind == K_OBS) {
-              float e[DS];
-#pragma unroll
-              for (int c = 0; c < DS; ++c) e[c] = 0.f;
-              if (valid) {
-                const float* ov = b.obs_vals + (size_t)(item.begin + sub + p) * DS;
-#pragma unroll
-                for (int c = 0; c < DS; ++c) e[c] = Y[c][0] - ov[c];
-              }
-              float s = 0.f;
-#pragma unroll
-              for (int c = 0; c < DS; ++c) {
-                s = fmaf(sh.comp_w[c] * e[c], e[c], s);
-                Yb[c][0] = 2.f * sh.lam_obs * sh.comp_w[c] * e[c] * ni.inv_nobs;
-              }
-              l0 = s;
-            } else {   // K_FACE: own side item.side, neighbour 1 - side
-              float e[DS];
-              float ep = 0.f;
-#pragma unroll
-              for (int c = 0; c < DS; ++c) e[c] = 0.f;
-              if (valid) {
-                const size_t pt = (size_t)(item.begin + sub + p);
-                const int o = 1 - item.side;
-                const float* nv = b.nbr_val + (pt * 2 + o) * DOUT;
-#pragma unroll
-                for (int c = 0; c < DS; ++c) e[c] = Y[c][0] - nv[c];
-                float Pn = nv[DS];
-                if (s_other_master) Pn = Pn - b.nbr_anc[pt * 2 + o];   // Eq. (15)
-                ep = Y[DS][0] - Pn;
-              }
-              float su = 0.f;
-#pragma unroll
-              for (int c = 0; c < DS; ++c) {
-                su = fmaf(sh.comp_w[c] * e[c], e[c], su);
-                Yb[c][0] = 2.f * sh.lam_gh_u * sh.comp_w[c] * e[c] * ni.inv_ngh;
-              }
-              const float lam = s_is_time ? sh.lam_time : ni.lam_space;
-              Yb[DS][0] = 2.f * lam * ep * ni.inv_ngh;
-              l0 = su;
-              l1 = ep * ep;
-            }
 #pragma unroll
             for (int j = 0; j < DOUT; ++j)
 #pragma unroll
               for (int c = 0; c < C; ++c) ybsm[j * RS + p * C + c] = Yb[j][c];
-          } else if constexpr (MODE == M_EVAL) {
-            if (valid) {
-              const size_t pt = (size_t)(item.begin + sub + p);
-              if (item.kind == K_EVAL) {
-#pragma unroll
-                for (int j = 0; j < DOUT; ++j) b.nbr_val[(pt * 2 + item.side) * DOUT + j] = Y[j][0];
-                if constexpr (JETS) {   // the interface terms' messages: residual and first derivatives
-                  float r[DS + 1];
-                  ns_residual<DS, UNST, C>(Y, sh.nu, r);
-#pragma unroll
-                  for (int j = 0; j <= DS; ++j) b.nbr_res[(pt * 2 + item.side) * (DS + 1) + j] = r[j];
-#pragma unroll
-                  for (int c = 0; c < DOUT; ++c)
-#pragma unroll
-                    for (int q = 0; q < DIN; ++q)
-                      b.nbr_grd[((pt * 2 + item.side) * DOUT + c) * DIN + q] = Y[c][1 + q];
-                }
-              } else {
-                b.nbr_anc[pt * 2 + item.side] = Y[DS][0];
-              }
-            }
-          } else {   // M_QUERY
-            if (valid) {
-              float* o = b.q_out + (size_t)b.q_perm[item.begin + sub + p] * b.q_w;
-              if (pass == 0) {
-#pragma unroll
-                for (int j = 0; j < DS; ++j) o[j] = Y[j][0];
-                if (npass == 1) o[DS] = Y[DS][0] + sh.p_ref;
-                else pkeep = Y[DS][0];
-                if constexpr (JETS) {
-#pragma unroll
-                  for (int j = 0; j < DS; ++j) {
-                    float v = UNST ? Y[j][1 + DS] : 0.f;
-#pragma unroll
-                    for (int i = 0; i < DS; ++i) v = fmaf(Y[i][0], Y[j][1 + i], v);
-                    v += Y[DS][1 + j];
-                    v = fmaf(-sh.nu, Y[j][C - 1], v);
-                    o[DOUT + j] = v;
-                  }
-                  float dv = 0.f;
-#pragma unroll
-                  for (int i = 0; i < DS; ++i) dv += Y[i][1 + i];
-                  o[DOUT + DS] = dv;
-                }
-              } else {
-                o[DS] = (pkeep - Y[DS][0]) + sh.p_ref;
-              }
-            }
           }
         }
         if constexpr (TRAIN) {

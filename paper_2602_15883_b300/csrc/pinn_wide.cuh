@@ -1,0 +1,516 @@
+// Grouped kernel for the widths that the register-tiled kernel does not
+// tile: the cylinder networks of Sec. 5 (6 x 150 and 8 x 200 neurons).  It
+// computes exactly what k_pinn computes (Eqs. (5)-(16), Algorithm 1; the
+// per-point epilogue is the same function), with a layout that takes any
+// width W <= WP (WP a multiple of 32):
+//   * lane l of every warp owns neurons l, l + 32, ... (TMG = WP / 32 of them)
+//     and warp w owns the tile's points w TPG ... w TPG + TPG - 1 (its column
+//     group), so the activation jets of a (neuron, point) stay in one thread;
+//   * a W x W weight matrix does not fit in shared memory next to the
+//     activations (200 x 200 fp32 = 160 KB), so it is streamed through two
+//     buffers of 32 rows (16 above width 160) with cp.async while the
+//     previous chunk is contracted;
+//   * the weight gradient is accumulated per block of 4 output neurons per
+//     warp and written with coalesced read-modify-writes (lanes = input
+//     neurons).
+// Rows of the activation buffers are 2 (mod 32) floats apart, so the
+// lane-strided 8-byte row loads of the weight gradient are conflict-free.
+#pragma once
+#include "pinn_kernels.cuh"
+
+namespace dk {
+
+constexpr int NTW = 256;   // threads per CTA of the wide kernel
+static_assert(NTW == NT, "the block sums and launches assume NT threads");
+
+template <int WP, int C>
+struct WideTile {
+  static_assert(WP % 32 == 0, "padded width");
+  static constexpr int TMG = WP / 32;                                              // neurons per thread
+  static constexpr int TPG = (C == 1) ? 8 : 2;                                    // points per column group
+  static constexpr int P = 8 * TPG;                                                // points per tile
+  static constexpr int NCOL = TPG * C;                                             // columns per thread
+  static constexpr int PC = P * C;
+  static constexpr int RS = ((PC + 29) / 32) * 32 + 2;                            // row stride, 2 (mod 32)
+  static constexpr int KC = (WP > 160) ? 16 : 32;                                 // streamed weight rows
+  static constexpr int IB = 4;                                                     // dW neurons per block
+  static constexpr int NQ = TMG * NCOL;                                            // stashed floats per thread
+  static_assert(RS >= PC && RS % 2 == 0 && P <= NTW && PC % 2 == 0, "wide tile");
+};
+
+template <int WP, int C, int DOUT>
+constexpr size_t smem_floats_wide(int L) {
+  using T = WideTile<WP, C>;
+  return (size_t)2 * WP * T::RS + (size_t)2 * T::KC * WP + (size_t)2 * DOUT * T::RS + (size_t)T::P * 4 +
+         (size_t)WP * 4 + WP + 4 + (size_t)(L > 1 ? L - 1 : 0) * WP;
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <int WP, int VW>
+__device__ __forceinline__ void wide_chunk_copy(float* dst, const float* __restrict__ src, int nr, int ncols) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nv = ncols / VW;
+  for (int r = warp; r < nr; r += NTW / 32)
+    for (int v = lane; v < nv; v += 32) cp_async<4 * VW>(dst + r * WP + v * VW, src + (size_t)r * ncols + v * VW);
+}
+
+// Rows [r0, r0 + nr) of a row-major matrix (row length ncols) into a
+// streamed-weight buffer of KC rows x WP columns (columns >= ncols untouched):
+// warp w copies rows w, w + 8, ..., its lanes 16-, 8- or 4-byte pieces (the
+// widest that the row length and the addresses allow).
+template <int WP>
+__device__ __forceinline__ void wide_chunk_issue(float* dst, const float* __restrict__ src, int r0, int nr, int ncols) {
+  const float* s0 = src + (size_t)r0 * ncols;
+  const uintptr_t a = reinterpret_cast<uintptr_t>(s0);
+  if (ncols % 4 == 0 && a % 16 == 0) wide_chunk_copy<WP, 4>(dst, s0, nr, ncols);
+  else if (ncols % 2 == 0 && a % 8 == 0) wide_chunk_copy<WP, 2>(dst, s0, nr, ncols);
+  else wide_chunk_copy<WP, 1>(dst, s0, nr, ncols);
+  cp_async_commit();
+}
+
+// acc[m][j] += sum_{k < K} M[k][lane + 32 m] * X[k * RS + col0 + j], M a
+// row-major K x ncols matrix in global memory streamed in chunks of KC rows.
+// Ends with a barrier (the buffers and X may be rewritten afterwards).
+template <int WP, int C, int NCOL>
+__device__ __forceinline__ void wide_contract(float (&acc)[WP / 32][NCOL], const float* __restrict__ M, int K,
+                                              int ncols, float* wch, const float* X, int col0) {
+  using T = WideTile<WP, C>;
+  constexpr int KC = T::KC, TMG = T::TMG, RS = T::RS;
+  const int lane = threadIdx.x & 31;
+  const int nch = (K + KC - 1) / KC;
+  wide_chunk_issue<WP>(wch, M, 0, min(KC, K), ncols);
+  for (int ch = 0; ch < nch; ++ch) {
+    float* const buf = wch + (ch & 1) * KC * WP;
+    if (ch + 1 < nch) {
+      wide_chunk_issue<WP>(wch + ((ch + 1) & 1) * KC * WP, M, (ch + 1) * KC, min(KC, K - (ch + 1) * KC), ncols);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const int k0 = ch * KC, nk = min(KC, K - k0);
+#pragma unroll 4
+    for (int k = 0; k < nk; ++k) {
+      float w[TMG];
+#pragma unroll
+      for (int m = 0; m < TMG; ++m) w[m] = buf[k * WP + lane + 32 * m];
+      const float* xr = X + (k0 + k) * RS + col0;
+      if constexpr (NCOL % 2 == 0) {
+#pragma unroll
+        for (int j = 0; j < NCOL; j += 2) {
+          const float2 x = *reinterpret_cast<const float2*>(xr + j);
+#pragma unroll
+          for (int m = 0; m < TMG; ++m) {
+            const float2 r = __ffma2_rn(make_float2(w[m], w[m]), x, make_float2(acc[m][j], acc[m][j + 1]));
+            acc[m][j] = r.x;
+            acc[m][j + 1] = r.y;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < NCOL; ++j) {
+          const float x = xr[j];
+#pragma unroll
+          for (int m = 0; m < TMG; ++m) acc[m][j] = fmaf(w[m], x, acc[m][j]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int WP, int DS, int UNST, bool JETS, int MODE, int ACT>
+__global__ void __launch_bounds__(NTW, 1)
+    k_pinn_w(const Shape sh, const Bufs b, const Item* __restrict__ items, const int* __restrict__ n_items_ptr) {
+  constexpr int DIN = DS + UNST;
+  constexpr int C = JETS ? DIN + 2 : 1;
+  constexpr int DOUT = DS + 1;
+  using T = WideTile<WP, C>;
+  constexpr int P = T::P, RS = T::RS, TPG = T::TPG, NCOL = T::NCOL, PC = T::PC, TMG = T::TMG, KC = T::KC;
+  constexpr bool TRAIN = (MODE == M_TRAIN);
+
+  extern __shared__ float4 sm4[];
+  float* const sm = reinterpret_cast<float*>(sm4);
+  float* const bufA = sm;
+  float* const bufB = bufA + WP * RS;
+  float* const wch = bufB + WP * RS;        // [2][KC][WP]
+  float* const ysm = wch + 2 * KC * WP;
+  float* const ybsm = ysm + DOUT * RS;
+  float* const xh = ybsm + DOUT * RS;       // [P][4]
+  float* const w0s = xh + P * 4;            // [WP][4]
+  float* const b0s = w0s + WP * 4;          // [WP]
+  float* const bLs = b0s + WP;              // [4]
+  float* const bls = bLs + 4;               // [L-1][WP]
+  __shared__ int s_item;
+  __shared__ float s_red[NTW / 32];
+  __shared__ float s_scale[4];
+  __shared__ int s_other_master, s_is_time;
+
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int W = sh.W, L = sh.L;
+  const int col0 = warp * NCOL;             // the warp's points warp * TPG + [0, TPG)
+  const int n_items = *n_items_ptr;
+  if (MODE == M_EVAL && b.comm_interval > 1 && (*b.step % b.comm_interval) != 0) return;
+
+  // padded neurons (>= W) see zero weights and biases, so every value stays finite
+  for (int e = t; e < 2 * KC * WP; e += NTW) wch[e] = 0.f;
+  for (int e = t; e < WP * 4; e += NTW) w0s[e] = 0.f;
+  for (int e = t; e < WP; e += NTW) b0s[e] = 0.f;
+  for (int e = t; e < (L - 1) * WP; e += NTW) bls[e] = 0.f;
+  __syncthreads();
+  float* const stash = b.stash + (TRAIN ? (size_t)blockIdx.x * b.stash_per_cta : 0);
+
+  auto stash_st = [&](int l, const float (&z)[TMG][NCOL]) {
+#pragma unroll
+    for (int m = 0; m < TMG; ++m)
+#pragma unroll
+      for (int j = 0; j < NCOL; ++j) stash[((size_t)l * T::NQ + m * NCOL + j) * NTW + t] = z[m][j];
+  };
+  auto stash_ld = [&](int l, float (&z)[TMG][NCOL]) {
+#pragma unroll
+    for (int m = 0; m < TMG; ++m)
+#pragma unroll
+      for (int j = 0; j < NCOL; ++j) z[m][j] = stash[((size_t)l * T::NQ + m * NCOL + j) * NTW + t];
+  };
+  auto to_stash_form = [&](float (&z)[TMG][NCOL]) {
+#pragma unroll
+    for (int m = 0; m < TMG; ++m)
+#pragma unroll
+      for (int pp = 0; pp < TPG; ++pp) z[m][pp * C] = stash_value<ACT>(z[m][pp * C]);
+  };
+  auto act_store = [&](float* buf, const float (&h)[TMG][NCOL]) {
+#pragma unroll
+    for (int m = 0; m < TMG; ++m) {
+      float a[NCOL];
+#pragma unroll
+      for (int pp = 0; pp < TPG; ++pp) act_from_stash<C, DS, DIN, ACT>(&h[m][pp * C], &a[pp * C]);
+      float* row = buf + (lane + 32 * m) * RS + col0;
+#pragma unroll
+      for (int j = 0; j < NCOL; ++j) row[j] = a[j];
+    }
+  };
+  auto zero_acc = [&](float (&z)[TMG][NCOL]) {
+#pragma unroll
+    for (int m = 0; m < TMG; ++m)
+#pragma unroll
+      for (int j = 0; j < NCOL; ++j) z[m][j] = 0.f;
+  };
+
+  for (;;) {
+    if (t == 0) s_item = atomicAdd(b.counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= n_items) break;
+    const Item item = items[it];
+    const int net = item.net;
+    const float* const th = b.theta + (size_t)net * sh.npp;
+    const float* const thT = b.thetaT + (size_t)net * sh.nTp;
+    const NetInfo ni = b.nets[net];
+    for (int e = t; e < W * DIN; e += NTW) w0s[(e / DIN) * 4 + e % DIN] = th[sh.woff[0] + e];
+    for (int e = t; e < W; e += NTW) b0s[e] = th[sh.boff[0] + e];
+    for (int e = t; e < (L - 1) * W; e += NTW) bls[(e / W) * WP + e % W] = th[sh.boff[1 + e / W] + e % W];
+    if (t < DOUT) bLs[t] = th[sh.boff[L] + t];
+    if (t < 4) s_scale[t] = t < DIN ? ni.scale[t] : 0.f;
+    if (t == 0) {
+      if (item.kind == K_FACE) {
+        const int other = b.face_info[item.face * 3 + (1 - item.side)];
+        s_other_master = b.nets[other].master;
+        s_is_time = b.face_info[item.face * 3 + 2];
+      } else {
+        s_other_master = 0;
+        s_is_time = 0;
+      }
+    }
+    double lsum0 = 0.0, lsum1 = 0.0, lsum2 = 0.0, lsum3 = 0.0;
+    const int npass = (MODE == M_QUERY && ni.master) ? 2 : 1;
+
+    for (int sub = 0; sub < item.count; sub += P) {
+      const int npts = min(P, item.count - sub);
+      const bool first = (sub == 0);
+      float pkeep = 0.f;
+      float* cur = bufA;
+      float* oth = bufB;
+      for (int pass = 0; pass < npass; ++pass) {
+        if (t < P) {
+          float x[4] = {0.f, 0.f, 0.f, 0.f};
+          const bool valid = t < npts;
+          if (valid) {
+            const float* src;
+            if (MODE == M_QUERY) src = b.q_pts + (size_t)b.q_perm[item.begin + sub + t] * DIN;
+            else if (item.kind == K_PDE) src = b.res_pts + (size_t)(item.begin + sub + t) * DIN;
+            else if (item.kind == K_OBS) src = b.obs_pts + (size_t)(item.begin + sub + t) * DIN;
+            else src = b.face_pts + (size_t)(item.begin + sub + t) * DIN;
+#pragma unroll
+            for (int q = 0; q < DIN; ++q) x[q] = src[q];
+            if (pass == 1 || item.kind == K_EVAL_ANC) {
+#pragma unroll
+              for (int q = 0; q < DS; ++q) x[q] = sh.anchor[q];
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) xh[t * 4 + q] = (valid && q < DIN) ? (x[q] - ni.center[q]) * ni.scale[q] : 0.f;
+        }
+        __syncthreads();
+        // ---- first affine map: z = W0 xh + b0, d_q z = s_q W0[:, q], lap z = 0
+        {
+          float z[TMG][NCOL];
+#pragma unroll
+          for (int m = 0; m < TMG; ++m) {
+            const int i = lane + 32 * m;
+#pragma unroll
+            for (int pp = 0; pp < TPG; ++pp) {
+              const int p = warp * TPG + pp;
+              float v = b0s[i];
+#pragma unroll
+              for (int q = 0; q < DIN; ++q) v = fmaf(w0s[i * 4 + q], xh[p * 4 + q], v);
+              z[m][pp * C] = v;
+              if constexpr (JETS) {
+#pragma unroll
+                for (int q = 0; q < DIN; ++q) z[m][pp * C + 1 + q] = w0s[i * 4 + q] * s_scale[q];
+                z[m][pp * C + C - 1] = 0.f;
+              }
+            }
+          }
+          to_stash_form(z);
+          if (TRAIN) stash_st(0, z);
+          act_store(bufA, z);
+        }
+        cur = bufA;
+        oth = bufB;
+        // ---- hidden layers (the contraction's first barrier orders the stores above)
+        for (int l = 1; l < L; ++l) {
+          float z[TMG][NCOL];
+          zero_acc(z);
+          wide_contract<WP, C, NCOL>(z, thT + (size_t)(l - 1) * W * W, W, W, wch, cur, col0);
+#pragma unroll
+          for (int m = 0; m < TMG; ++m)
+#pragma unroll
+            for (int pp = 0; pp < TPG; ++pp) z[m][pp * C] += bls[(l - 1) * WP + lane + 32 * m];
+          to_stash_form(z);
+          if (TRAIN) stash_st(l, z);
+          act_store(oth, z);
+          float* tmp = cur; cur = oth; oth = tmp;
+        }
+        __syncthreads();
+        // ---- output layer: Y[j][p][c] = W_L[j] . A[.][p][c] (+ b_L on values)
+        {
+          const float* const wL = th + sh.woff[L];
+          constexpr int PAIRS = DOUT * P;
+          constexpr int KS0 = NTW / PAIRS;
+          constexpr int KS = KS0 >= 8 ? 8 : (KS0 >= 4 ? 4 : (KS0 >= 2 ? 2 : 1));
+          for (int pr = t / KS; pr < PAIRS; pr += NTW / KS) {
+            const int j = pr / P, p = pr % P, lk = t % KS;
+            float acc[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) acc[c] = 0.f;
+            for (int k = lk; k < W; k += KS) {
+              const float w = wL[j * W + k];
+#pragma unroll
+              for (int c = 0; c < C; ++c) acc[c] = fmaf(w, cur[k * RS + p * C + c], acc[c]);
+            }
+#pragma unroll
+            for (int o = KS / 2; o > 0; o >>= 1)
+#pragma unroll
+              for (int c = 0; c < C; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+            if (lk == 0) {
+#pragma unroll
+              for (int c = 0; c < C; ++c) ysm[j * RS + p * C + c] = acc[c] + (c == 0 ? bLs[j] : 0.f);
+            }
+          }
+        }
+        __syncthreads();
+        // ---- per-point epilogue
+        float l0 = 0.f, l1 = 0.f, l2 = 0.f, l3 = 0.f;
+        if (t < P) {
+          const int p = t;
+          const bool valid = p < npts;
+          float Y[DOUT][C];
+#pragma unroll
+          for (int j = 0; j < DOUT; ++j)
+#pragma unroll
+            for (int c = 0; c < C; ++c) Y[j][c] = ysm[j * RS + p * C + c];
+          float Yb[DOUT][C];
+          point_epilogue<DS, UNST, JETS, MODE, C>(sh, b, item, ni, sub, p, valid, pass, npass, s_other_master,
+                                                  s_is_time, Y, Yb, l0, l1, l2, l3, pkeep);
+          if constexpr (MODE == M_TRAIN) {
+#pragma unroll
+            for (int j = 0; j < DOUT; ++j)
+#pragma unroll
+              for (int c = 0; c < C; ++c) ybsm[j * RS + p * C + c] = Yb[j][c];
+          }
+        }
+        if constexpr (TRAIN) {
+          const float s0 = block_sum(l0, s_red);
+          if (t == 0) lsum0 += (double)s0;
+          if (item.kind == K_FACE) {
+            const float s1 = block_sum(l1, s_red);
+            if (t == 0) lsum1 += (double)s1;
+            if constexpr (JETS) {
+              const float s2 = block_sum(l2, s_red);
+              if (t == 0) lsum2 += (double)s2;
+              const float s3 = block_sum(l3, s_red);
+              if (t == 0) lsum3 += (double)s3;
+            }
+          }
+        }
+        __syncthreads();
+      }   // pass
+      if constexpr (!TRAIN) continue;
+      if (b.no_reverse) continue;
+
+      // ================= reverse pass =================
+      float* const g = b.grad_part + (size_t)item.slot * sh.npp;
+      // output layer: dW_L, db_L
+      for (int e = t; e < DOUT * W; e += NTW) {
+        const int j = e / W, k = e % W;
+        float s = 0.f;
+        for (int pc = 0; pc < PC; ++pc) s = fmaf(ybsm[j * RS + pc], cur[k * RS + pc], s);
+        grad_rmw(g + sh.woff[L] + e, s, first);
+      }
+      if (t < DOUT) {
+        float s = 0.f;
+        for (int p = 0; p < P; ++p) s += ybsm[t * RS + p * C];
+        grad_rmw(g + sh.boff[L] + t, s, first);
+      }
+      float* zb = oth;
+      float* ab = cur;
+      {   // A_{L-1} adjoints = W_L^T Yb, then through the activation
+        const float* const wL = th + sh.woff[L];
+        float a[TMG][NCOL];
+        zero_acc(a);
+#pragma unroll
+        for (int jo = 0; jo < DOUT; ++jo) {
+          float yb[NCOL];
+#pragma unroll
+          for (int j = 0; j < NCOL; ++j) yb[j] = ybsm[jo * RS + col0 + j];
+#pragma unroll
+          for (int m = 0; m < TMG; ++m) {
+            const int k = lane + 32 * m;
+            const float w = k < W ? wL[jo * W + k] : 0.f;
+#pragma unroll
+            for (int j = 0; j < NCOL; ++j) a[m][j] = fmaf(w, yb[j], a[m][j]);
+          }
+        }
+        float z[TMG][NCOL];
+        stash_ld(L - 1, z);
+        __syncthreads();   // the dW_L loop above reads cur, which the first reverse layer overwrites
+#pragma unroll
+        for (int m = 0; m < TMG; ++m) {
+          float zz[NCOL];
+#pragma unroll
+          for (int pp = 0; pp < TPG; ++pp) act_bwd<C, DS, DIN, ACT>(&z[m][pp * C], &a[m][pp * C], &zz[pp * C]);
+          float* row = zb + (lane + 32 * m) * RS + col0;
+#pragma unroll
+          for (int j = 0; j < NCOL; ++j) row[j] = zz[j];
+        }
+      }
+      for (int l = L - 1; l >= 1; --l) {
+        {   // A_{l-1} into ab
+          float z[TMG][NCOL];
+          stash_ld(l - 1, z);
+          act_store(ab, z);
+        }
+        __syncthreads();
+        // dW_l[i][k] += sum_pc Zb[i][pc] A_{l-1}[k][pc]: lanes take the input
+        // neurons k = lane + 32 m, warp w the output neurons w + 8 r in blocks
+        // of IB; column pairs in order (a fixed summation order).
+        {
+          constexpr int IB = T::IB;
+          float* const gw = g + sh.woff[l];
+          const int nr = (W + 7) / 8;
+          for (int r0 = 0; r0 < nr; r0 += IB) {
+            float2 acc[TMG][IB];   // .x the even, .y the odd columns
+#pragma unroll
+            for (int m = 0; m < TMG; ++m)
+#pragma unroll
+              for (int q = 0; q < IB; ++q) acc[m][q] = make_float2(0.f, 0.f);
+            int irow[IB];
+#pragma unroll
+            for (int q = 0; q < IB; ++q) irow[q] = min(warp + 8 * (r0 + q), WP - 1) * RS;
+            for (int pc = 0; pc < PC; pc += 2) {
+              float2 zv[IB], av[TMG];
+#pragma unroll
+              for (int q = 0; q < IB; ++q) zv[q] = *reinterpret_cast<const float2*>(zb + irow[q] + pc);
+#pragma unroll
+              for (int m = 0; m < TMG; ++m) av[m] = *reinterpret_cast<const float2*>(ab + (lane + 32 * m) * RS + pc);
+#pragma unroll
+              for (int m = 0; m < TMG; ++m)
+#pragma unroll
+                for (int q = 0; q < IB; ++q) acc[m][q] = __ffma2_rn(zv[q], av[m], acc[m][q]);
+            }
+#pragma unroll
+            for (int q = 0; q < IB; ++q) {
+              const int i = warp + 8 * (r0 + q);
+              if (i >= W) continue;
+#pragma unroll
+              for (int m = 0; m < TMG; ++m) {
+                const int k = lane + 32 * m;
+                if (k < W) grad_rmw(gw + (size_t)i * W + k, acc[m][q].x + acc[m][q].y, first);
+              }
+            }
+          }
+        }
+        for (int e = t; e < W; e += NTW) {
+          float s = 0.f;
+          for (int p = 0; p < P; ++p) s += zb[e * RS + p * C];
+          grad_rmw(g + sh.boff[l] + e, s, first);
+        }
+        // A_{l-1} adjoint = W_l^T Zb_l (rows of W_l streamed: i, entries k);
+        // the stash of layer l - 1 is loaded first, its latency under the
+        // contraction
+        float z[TMG][NCOL];
+        stash_ld(l - 1, z);
+        float a[TMG][NCOL];
+        zero_acc(a);
+        wide_contract<WP, C, NCOL>(a, th + sh.woff[l], W, W, wch, zb, col0);
+#pragma unroll
+        for (int m = 0; m < TMG; ++m) {
+          float zz[NCOL];
+#pragma unroll
+          for (int pp = 0; pp < TPG; ++pp) act_bwd<C, DS, DIN, ACT>(&z[m][pp * C], &a[m][pp * C], &zz[pp * C]);
+          float* row = zb + (lane + 32 * m) * RS + col0;
+#pragma unroll
+          for (int j = 0; j < NCOL; ++j) row[j] = zz[j];
+        }
+      }
+      __syncthreads();
+      // first affine map: dW_0[i][q] += sum_p (Zb_val xh_q + s_q Zb_q), db_0
+      for (int e = t; e < W * DIN; e += NTW) {
+        const int i = e / DIN, q = e % DIN;
+        float s = 0.f;
+        for (int p = 0; p < P; ++p) {
+          s = fmaf(zb[i * RS + p * C], xh[p * 4 + q], s);
+          if constexpr (JETS) s = fmaf(s_scale[q], zb[i * RS + p * C + 1 + q], s);
+        }
+        grad_rmw(g + sh.woff[0] + e, s, first);
+      }
+      for (int e = t; e < W; e += NTW) {
+        float s = 0.f;
+        for (int p = 0; p < P; ++p) s += zb[e * RS + p * C];
+        grad_rmw(g + sh.boff[0] + e, s, first);
+      }
+      __syncthreads();
+    }   // sub-tiles
+    if (TRAIN && t == 0) {
+      double* lp = b.loss_part + (size_t)item.slot * LP;
+      for (int q = 0; q < LP; ++q) lp[q] = 0.0;
+      if (item.kind == K_PDE) lp[1] = lsum0;
+      else if (item.kind == K_OBS) lp[0] = lsum0;
+      else {
+        lp[2] = lsum0;
+        lp[s_is_time ? 4 : 3] = lsum1;
+        lp[5] = lsum2;
+        lp[6] = lsum3;
+      }
+    }
+  }   // items
+}
+
+}  // namespace dk

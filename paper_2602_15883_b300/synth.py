@@ -94,6 +94,25 @@ CONFIGS = {
         anchor=[-0.75, -0.75, -0.5], lambda_obs=10.0, lambda_pde=10.0,
         flow="beltrami", res_dist=("powerlaw", 2048, 65536, 1.2), n_obs=2048,
         noise=0.02, n_face=1024),
+    # The network shapes and point budgets of the paper's cylinder cases
+    # (Sec. 5, Table B1) on analytic stand-in flows (the CFD data are not
+    # available): 2-D, 6 x 150 sin, 5e5 residual and 1e4 observation points,
+    # 1,000 points per interface, 4 x 2 (space x time) subdomains on the TGV
+    # domain; 3-D, 8 x 200 sin, 6e5 residual and 1e5 observation points,
+    # 5,000 points per interface, 2 x 2 x 1 x 2 subdomains on the Beltrami
+    # domain.
+    "cylinder2d": _base(
+        d_space=2, unsteady=1, lo=[0.0, 0.0, 0.0, 0], hi=[2 * math.pi, 2 * math.pi, 1.0, 0],
+        splits=[4, 1, 2, 1], depth=6, width=150, activation=1, nu=0.01,
+        anchor=[math.pi / 4, math.pi / 4, 0.0], lambda_obs=10.0, lambda_pde=5.0,
+        flow="tgv", res_dist=("const", 62500), n_obs=1250, noise=0.01,
+        n_face=1000),
+    "cylinder3d": _base(
+        d_space=3, unsteady=1, lo=[-1.0, -1.0, -1.0, 0.0], hi=[1.0, 1.0, 1.0, 1.0],
+        splits=[2, 2, 1, 2], depth=8, width=200, activation=1, nu=1.0,
+        anchor=[-0.5, -0.5, -0.5], lambda_obs=10.0, lambda_pde=10.0,
+        flow="beltrami", res_dist=("const", 75000), n_obs=12500, noise=0.02,
+        n_face=5000),
 }
 
 LIB_KEYS = (

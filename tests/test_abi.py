@@ -42,7 +42,8 @@ def test_config_default_is_host_only(lib):
     assert c.width == 32 and c.depth == 4 and list(c.splits) == [1, 1, 1, 1]
 
 
-@pytest.mark.parametrize("field,value", [("width", 48), ("depth", 0), ("d_space", 4), ("activation", 2),
+@pytest.mark.parametrize("field,value", [("width", 48), ("width", 100), ("width", 225), ("depth", 0),
+                                         ("d_space", 4), ("activation", 2),
                                          ("precision", 2), ("precision", 1)])
 def test_create_rejects_bad_configs_before_touching_a_device(lib, field, value):
     c = binding.Config()

@@ -36,7 +36,7 @@ def _compare(loss, oloss, tol=LOSS_TOL):
 
 
 @pytest.mark.parametrize("name,precision", [("tgv", 0), ("steady3d_w64", 0), ("beltrami32", 0), ("beltrami32", 1),
-                                            ("tgv_ghost", 0), ("beltrami_sin", 0)])
+                                            ("tgv_ghost", 0), ("beltrami_sin", 0), ("cyl2d_w150", 0)])
 def test_interface_terms_losses_and_gradients_match_oracle(name, precision):
     Dpinn = _gpu()
     cfg, pb = _case(name, precision)

@@ -70,6 +70,13 @@ def small_case(name):
     elif name == "unsteady2d_w128_deep":
         cfg = synth.config("tgv", width=128, depth=3, splits=[1, 2, 3, 1], anchor=[3.0, 1.0, 0.0])
         res, obs, face = (90, 30), (20, 8), (20, 8)
+    elif name == "cyl2d_w150":   # the 2-D cylinder network shape of Sec. 5: 6 x 150 sin, d_in = 3
+        cfg = synth.config("tgv", width=150, depth=6, activation=1, splits=[2, 1, 2, 1], anchor=[0.5, 2.0, 0.0])
+        res, obs, face = (150, 40), (40, 12), (30, 9)
+    elif name == "cyl3d_w200":   # the 3-D cylinder network shape of Sec. 5: 8 x 200 sin, d_in = 4
+        cfg = synth.config("beltrami32", width=200, depth=8, activation=1, splits=[2, 1, 1, 2],
+                           anchor=[-0.4, 0.2, 0.3])
+        res, obs, face = (90, 25), (40, 12), (30, 9)
     elif name in ("tgv_ghost", "beltrami_ghost"):
         cfg, pb = small_case(name[:-6] if name.startswith("tgv") else "beltrami32")
         d = (0.4, 0.2) if name.startswith("tgv") else (0.3, 0.15)
@@ -90,7 +97,8 @@ def small_case(name):
 
 
 CASES = ["kovasznay", "tgv", "beltrami32", "beltrami128", "steady3d_w64", "unsteady3d_w32",
-         "unsteady3d_w64", "unsteady2d_w128_deep", "tgv_sin", "beltrami_sin", "tgv_ghost", "beltrami_ghost"]
+         "unsteady3d_w64", "unsteady2d_w128_deep", "tgv_sin", "beltrami_sin", "tgv_ghost", "beltrami_ghost",
+         "cyl2d_w150", "cyl3d_w200"]
 
 
 def compare_losses(gpu, ref, tol=LOSS_TOL):
@@ -122,7 +130,7 @@ def test_losses_and_gradients_match_oracle(name):
         assert g[0, -1] == 0.0 and og[0, -1] == 0.0
 
 
-@pytest.mark.parametrize("name", ["kovasznay", "tgv", "beltrami32", "beltrami_sin"])
+@pytest.mark.parametrize("name", ["kovasznay", "tgv", "beltrami32", "beltrami_sin", "cyl2d_w150"])
 def test_one_step_matches_oracle(name):
     Dpinn = _gpu()
     cfg, pb = small_case(name)
@@ -313,3 +321,23 @@ def test_ghost_layers_then_back_to_faces():
     e.eval_grad()
     np.testing.assert_array_equal(lf, e.loss())
     np.testing.assert_array_equal(gf, e.grad())
+
+
+@pytest.mark.parametrize("name", ["tgv", "cyl3d_w200"])
+def test_timed_step_equals_graph_step(name):
+    """dpinn_step_timed runs the step's kernels one after another (the graph
+    forks the exchange and value items beside the jet items); both give the
+    same parameters bit for bit.  The W = 200 case has a larger value-kernel
+    stash than jet-kernel stash."""
+    Dpinn = _gpu()
+    cfg, pb = small_case(name)
+    a = Dpinn(cfg)
+    a.set_problem(pb)
+    b = Dpinn(cfg)
+    b.set_problem(pb)
+    for _ in range(2):
+        a.step(1)
+        ms = b.step_timed()
+        assert "train_jet" in ms and all(v >= 0 for v in ms.values())
+    np.testing.assert_array_equal(a.loss(), b.loss())
+    np.testing.assert_array_equal(a.get_state()[0], b.get_state()[0])

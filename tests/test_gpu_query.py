@@ -22,7 +22,8 @@ def _torch():
     return torch
 
 
-@pytest.mark.parametrize("name", ["kovasznay", "tgv", "beltrami32", "steady3d_w64", "unsteady3d_w32", "tgv_sin"])
+@pytest.mark.parametrize("name", ["kovasznay", "tgv", "beltrami32", "steady3d_w64", "unsteady3d_w32", "tgv_sin",
+                                  "cyl2d_w150", "cyl3d_w200"])
 @pytest.mark.parametrize("want_res", [False, True])
 def test_query_matches_oracle(name, want_res):
     Dpinn = _gpu()
