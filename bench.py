@@ -239,7 +239,13 @@ def serving_leg(seconds=5.0, rate=200.0, train_steps=20, seed=0, precision="tf32
     d.loss()
     srv = Server(d, slots=4, mem_cap_bytes=8 << 30, max_batch_points=1 << 21).start()
     try:
-        poisson_load(srv, cfg, rate_hz=20.0, duration_s=0.5, seed=seed + 1)     # warm-up
+        # warm-up: every slot serves small and large requests, values and
+        # residuals (first launches load their kernels), then a light load
+        warm = [srv.submit(synth.query_points(cfg, n, seed=seed + 10 + i), res)
+                for i, (n, res) in enumerate([(n, res) for res in (False, True) for n in (1000, 1 << 20)] * 4)]
+        for r in warm:
+            r.done.wait()
+        poisson_load(srv, cfg, rate_hz=20.0, duration_s=0.5, seed=seed + 1)
         reqs = poisson_load(srv, cfg, rate_hz=rate, duration_s=seconds, seed=seed + 2)
     finally:
         srv.stop()
