@@ -15,6 +15,7 @@ from pinned host memory and the loss record copied back every step.
 from __future__ import annotations
 
 import argparse
+import glob
 import json
 import os
 import subprocess
@@ -146,6 +147,41 @@ def whole_job_value(world, n_res_per_rank, steps, total_ms_max):
     """Whole-job residual points per second: every replica's points over the
     slowest replica's time (weak scaling: each rank runs its own problem)."""
     return world * n_res_per_rank * steps / (total_ms_max / 1e3)
+
+
+TRAFFIC_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2602_15883_b300", "ncu_traffic.json")
+
+
+def kernel_source_sha256():
+    """SHA-256 over the CUDA sources and the C header (the build the ncu
+    traffic captures were taken on must be the one that runs)."""
+    import hashlib
+    root = os.path.dirname(os.path.abspath(__file__))
+    files = sorted(glob.glob(os.path.join(root, "paper_2602_15883_b300", "csrc", "*")))
+    files.append(os.path.join(root, "include", "dpinn.h"))
+    h = hashlib.sha256()
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def captured_traffic(workload, precision):
+    """DRAM bytes (read + write) per launch of the jet kernel from an ncu
+    capture of this workload, or None when there is none or the kernel
+    sources changed since it was taken."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_sha256") != kernel_source_sha256():
+        return None
+    for c in rec.get("captures", []):
+        if c["workload"] == workload and c["precision"] == precision:
+            return c["dram_bytes_per_launch"]
+    return None
 
 
 def tf32_tensor_peak_tflops(pk):
@@ -354,14 +390,18 @@ def main():
     if args.precision == "fp32":
         peak = fp32_alu_peak_tflops(sm_mhz)
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None, "kernel": "k_pinn train (jets)",
+                    "frac": achieved / peak, "traffic": captured_traffic(args.workload, "fp32"),
+                    "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+                    "kernel": "k_pinn train (jets)" if cfg["width"] in (32, 64, 128) else "k_pinn_w train (jets)",
                     "peak_source": f"148 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (max SM clock, {pk_kind})",
                     "kernel_ms": kms}
     else:
         peak = tf32_tensor_peak_tflops(pk)
         hidden = 3 * 2 * (synth.d_in(cfg) + 2) * cfg["width"] ** 2 * (cfg["depth"] - 1) * pb.n_res
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None, "kernel": "k_pinn_tc train (jets, tcgen05 3xTF32)",
+                    "frac": achieved / peak, "traffic": captured_traffic(args.workload, "tf32x3"),
+                    "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+                    "kernel": "k_pinn_tc train (jets, tcgen05 3xTF32)",
                     "peak_source": f"dense TF32 = measured bf16 burst x 1.1/2.25 (nominal ratio, {pk_kind})",
                     "hw_tflops_3x": 3 * hidden / (jet_ms / 1e3) / 1e12,
                     "note": "achieved counts every product once; the tensor cores execute three per product",

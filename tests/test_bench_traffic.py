@@ -1,0 +1,21 @@
+"""bench.py reports an ncu DRAM-traffic figure only for the kernel sources it
+was captured on."""
+import json
+
+import bench
+
+
+def test_traffic_only_for_matching_sources(tmp_path, monkeypatch):
+    rec = {"source_sha256": bench.kernel_source_sha256(),
+           "captures": [{"workload": "tgv", "precision": "fp32", "dram_bytes_per_launch": 123}]}
+    f = tmp_path / "t.json"
+    f.write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(f))
+    assert bench.captured_traffic("tgv", "fp32") == 123
+    assert bench.captured_traffic("tgv", "tf32x3") is None
+    assert bench.captured_traffic("beltrami32", "fp32") is None
+    rec["source_sha256"] = "0" * 64          # sources changed since the capture
+    f.write_text(json.dumps(rec))
+    assert bench.captured_traffic("tgv", "fp32") is None
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(tmp_path / "missing.json"))
+    assert bench.captured_traffic("tgv", "fp32") is None
