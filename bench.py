@@ -389,7 +389,14 @@ def main():
     achieved = jet_flops / (jet_ms / 1e3) / 1e12
     if args.precision == "fp32":
         peak = fp32_alu_peak_tflops(sm_mhz)
+        # context: the attainable FP32 FMA rate measured now by the library's
+        # packed-FMA chain probe (a ~20 ms burst)
+        from paper_2602_15883_b300.binding import probe_fp32
+        cal_ms, _ = probe_fp32(2000)
+        p_ms, p_flop = probe_fp32(max(1, int(2000 * 20.0 / max(cal_ms, 1e-3))))
+        probe_tflops = p_flop / (p_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "probe_tflops": probe_tflops, "frac_of_probe": achieved / probe_tflops,
                     "frac": achieved / peak, "traffic": captured_traffic(args.workload, "fp32"),
                     "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                     "kernel": "k_pinn train (jets)" if cfg["width"] in (32, 64, 128) else "k_pinn_w train (jets)",

@@ -374,6 +374,16 @@ int dpinn_launches_per_step(dpinn_t* h);
 int dpinn_step_timed(dpinn_t* h, dpinn_stream_t stream, float* ms, int max_kernels, int* n_kernels,
                      const char** names);
 
+/* Measurement aid (not part of the training path): time one launch of a
+ * kernel in which every thread runs 8 independent chains of packed dual
+ * FP32 FMAs (blocks_per_sm x 256-thread CTAs per SM, `iters` iterations of
+ * 32 packed FMAs per thread) on `device`, after a short warm-up launch.
+ * Returns the launch time in *ms (CUDA events) and its FLOP count in *flop;
+ * *flop / *ms is the attainable FP32 FMA rate at the clocks the GPU ran.
+ * Synchronises.  Errors: INVALID_ARG (blocks_per_sm outside 1..8, iters
+ * outside 1..2^40, null outputs), CUDA. */
+int dpinn_probe_fp32(int device, int blocks_per_sm, long long iters, float* ms, double* flop);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,7 @@ EXPORTS = (
     "dpinn_eval_loss", "dpinn_set_params", "dpinn_set_schedule", "dpinn_get_schedule",
     "dpinn_qctx_create", "dpinn_qctx_destroy", "dpinn_qctx_query", "dpinn_qctx_status",
     "dpinn_set_resampling", "dpinn_get_points", "dpinn_set_partial_budget", "dpinn_loss_ext",
-    "dpinn_set_points_async", "dpinn_selftest_wait", "dpinn_loss_async",
+    "dpinn_set_points_async", "dpinn_selftest_wait", "dpinn_loss_async", "dpinn_probe_fp32",
 )
 
 
@@ -110,6 +110,7 @@ def load_library(path: str = LIB_PATH):
         "dpinn_set_points_async": ([vp, i32, vp, vp, i32, vp], i32),
         "dpinn_selftest_wait": ([vp], i32),
         "dpinn_loss_async": ([vp, vp, vp], i32),
+        "dpinn_probe_fp32": ([i32, i32, i64, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -146,6 +147,17 @@ def make_config(cfg: dict) -> Config:
     c.lambda_gh_r = float(cfg.get("lambda_gh_r", 0.0))
     c.lambda_gh_c1 = float(cfg.get("lambda_gh_c1", 0.0))
     return c
+
+
+def probe_fp32(iters, blocks_per_sm=4, device=0):
+    """(milliseconds, FLOP) of one launch of the library's packed-FMA chain
+    probe (dpinn_probe_fp32): the attainable FP32 FMA rate is FLOP / time."""
+    lib = load_library()
+    ms, flop = C.c_float(), C.c_double()
+    rc = lib.dpinn_probe_fp32(int(device), int(blocks_per_sm), int(iters), C.byref(ms), C.byref(flop))
+    if rc:
+        raise DpinnError(rc, "dpinn_probe_fp32 failed")
+    return ms.value, flop.value
 
 
 def _ptr(a):

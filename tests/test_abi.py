@@ -18,7 +18,7 @@ HEADER = os.path.join(ROOT, "include", "dpinn.h")
 def declared():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(dpinn_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(dpinn_[a-z0-9_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
