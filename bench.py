@@ -152,35 +152,35 @@ def whole_job_value(world, n_res_per_rank, steps, total_ms_max):
 TRAFFIC_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2602_15883_b300", "ncu_traffic.json")
 
 
-def kernel_source_sha256():
-    """SHA-256 over the CUDA sources and the C header (the build the ncu
-    traffic captures were taken on must be the one that runs)."""
+def kernel_source_sha256(files):
+    """SHA-256 over the named source files (paths relative to the repository
+    root): the sources that define a captured kernel."""
     import hashlib
     root = os.path.dirname(os.path.abspath(__file__))
-    files = sorted(glob.glob(os.path.join(root, "paper_2602_15883_b300", "csrc", "*")))
-    files.append(os.path.join(root, "include", "dpinn.h"))
     h = hashlib.sha256()
     for f in files:
-        h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
+        h.update(f.encode())
+        with open(os.path.join(root, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
 def captured_traffic(workload, precision):
     """DRAM bytes (read + write) per launch of the jet kernel from an ncu
-    capture of this workload, or None when there is none or the kernel
-    sources changed since it was taken."""
+    capture of this workload, or None when there is none or the sources that
+    define the kernel changed since it was taken."""
     try:
         with open(TRAFFIC_FILE) as fh:
             rec = json.load(fh)
     except (OSError, ValueError):
         return None
-    if rec.get("source_sha256") != kernel_source_sha256():
-        return None
     for c in rec.get("captures", []):
         if c["workload"] == workload and c["precision"] == precision:
-            return c["dram_bytes_per_launch"]
+            try:
+                same = c.get("sources_sha256") == kernel_source_sha256(c.get("sources", []))
+            except OSError:
+                return None
+            return c["dram_bytes_per_launch"] if same and c.get("sources") else None
     return None
 
 
