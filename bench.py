@@ -281,8 +281,9 @@ def serving_leg(seconds=5.0, rate=200.0, train_steps=20, seed=0, precision="tf32
                 for i, (n, res) in enumerate([(n, res) for res in (False, True) for n in (1000, 1 << 20)] * 4)]
         for r in warm:
             r.done.wait()
+        del warm, r
         poisson_load(srv, cfg, rate_hz=20.0, duration_s=0.5, seed=seed + 1)
-        reqs = poisson_load(srv, cfg, rate_hz=rate, duration_s=seconds, seed=seed + 2)
+        reqs = poisson_load(srv, cfg, rate_hz=rate, duration_s=seconds, seed=seed + 2, client_buffers=True)
     finally:
         srv.stop()
     out = latency_summary(reqs)

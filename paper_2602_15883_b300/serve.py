@@ -41,6 +41,7 @@ class Request:
     rid: int = 0
     retries: int = 0
     cancelled: bool = False
+    out: np.ndarray | None = None   # caller-owned result rows, filled in place
     done: threading.Event = field(default_factory=threading.Event)
 
     @property
@@ -115,9 +116,18 @@ class Server:
         self._thread = None
 
     # -- client side ------------------------------------------------------
-    def submit(self, pts: np.ndarray, want_residual: bool = False) -> Request:
+    def submit(self, pts: np.ndarray, want_residual: bool = False, out: np.ndarray | None = None) -> Request:
+        """Queue a query of ``pts`` ([n][d_in]).  ``out``, if given, is a
+        caller-owned float32 array [n][width] (width 4 or 8 as for the result)
+        that receives the result in place (and becomes ``result``), so that a
+        client can reuse its buffers instead of receiving a new array."""
         pts = np.ascontiguousarray(pts, np.float32).reshape(-1, self.d_in)
         r = Request(pts=pts, want_residual=bool(want_residual), t_arrival=time.perf_counter())
+        if out is not None:
+            if (not isinstance(out, np.ndarray) or out.dtype != np.float32 or
+                    out.shape != (r.n, self._width(r))):
+                raise ValueError(f"out must be a float32 array of shape ({r.n}, {self._width(r)})")
+            r.out = out
         with self.lock:
             r.rid = self._next_id
             self._next_id += 1
@@ -260,7 +270,11 @@ class Server:
                     if r.cancelled:
                         r.error = "cancelled"
                     elif st == 0:
-                        r.result = h[off:off + r.n].copy()
+                        if r.out is not None:
+                            np.copyto(r.out, h[off:off + r.n])
+                            r.result = r.out
+                        else:
+                            r.result = h[off:off + r.n].copy()
                     elif (st == ERR_INVALID_ARG and r.retries == 0 and
                           np.all((r.pts >= self.lo) & (r.pts <= self.hi))):
                         r.retries += 1       # an innocent neighbour of an outside point: run it again
@@ -289,10 +303,14 @@ class Server:
 
 
 def poisson_load(server: Server, cfg: dict, rate_hz: float, duration_s: float, seed: int = 0,
-                 n_min: int = 1000, n_max: int = 1_000_000, residual_fraction: float = 0.1, pool=None):
+                 n_min: int = 1000, n_max: int = 1_000_000, residual_fraction: float = 0.1, pool=None,
+                 client_buffers: bool = False):
     """Open-loop Poisson arrivals; each request a uniform space-time point cloud
     of log-uniform size (a slice of a pre-generated uniform pool, so that
     producing a request costs nothing), a fraction asking for residuals.
+    With ``client_buffers`` every request gets its own rows of two result
+    arrays allocated and touched before the first arrival (a client with its
+    own output memory), so that results are written in place.
     Returns the requests once all are done."""
     from . import synth
     rng = np.random.default_rng(seed)
@@ -307,12 +325,22 @@ def poisson_load(server: Server, cfg: dict, rate_hz: float, duration_s: float, s
         n = int(np.exp(rng.uniform(np.log(n_min), np.log(n_max))))
         off = int(rng.integers(0, len(pool) - n + 1))
         sched.append((t, off, n, bool(rng.random() < residual_fraction)))
+    outs = [None] * len(sched)
+    if client_buffers:
+        rows = {w: sum(n for (_, _, n, want) in sched if want == w) for w in (False, True)}
+        ring = {w: np.empty((max(rows[w], 1), server.w_res if w else server.w_val), np.float32) for w in rows}
+        pos = {False: 0, True: 0}
+        for w in ring:
+            ring[w].fill(0.0)   # touch every page now, not while serving
+        for i, (_, _, n, want) in enumerate(sched):
+            outs[i] = ring[want][pos[want]:pos[want] + n]
+            pos[want] += n
     t0 = time.perf_counter()
     reqs = []
-    for (ta, off, n, want) in sched:
+    for i, (ta, off, n, want) in enumerate(sched):
         while time.perf_counter() - t0 < ta:
             time.sleep(max(0.0, min(0.0005, ta - (time.perf_counter() - t0))))
-        reqs.append(server.submit(pool[off:off + n], want))
+        reqs.append(server.submit(pool[off:off + n], want, out=outs[i]))
     for r in reqs:
         r.done.wait()
     return reqs

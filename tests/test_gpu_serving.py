@@ -109,3 +109,27 @@ def test_cancelled_requests_end_alone():
         assert not srv.cancel(other)          # already finished
     finally:
         srv.stop()
+
+
+def test_caller_buffers_receive_the_same_results():
+    cfg, pb, d, srv = _server(slots=2)
+    try:
+        pts_v = synth.query_points(cfg, 5000, seed=21)
+        pts_r = synth.query_points(cfg, 3000, seed=22)
+        a = srv.submit(pts_v)
+        b = srv.submit(pts_r, True)
+        ov = np.full((5000, 4), -7.0, np.float32)
+        orr = np.full((3000, 8), -7.0, np.float32)
+        c = srv.submit(pts_v, out=ov)
+        e = srv.submit(pts_r, True, out=orr)
+        for r in (a, b, c, e):
+            r.done.wait()
+        assert c.result is ov and e.result is orr
+        np.testing.assert_array_equal(ov, a.result)
+        np.testing.assert_array_equal(orr, b.result)
+        with pytest.raises(ValueError):
+            srv.submit(pts_v, out=np.zeros((5000, 8), np.float32))   # residual width for a value query
+        with pytest.raises(ValueError):
+            srv.submit(pts_v, out=np.zeros((5000, 4), np.float64))
+    finally:
+        srv.stop()
