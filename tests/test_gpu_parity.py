@@ -77,9 +77,9 @@ def small_case(name):
         cfg = synth.config("beltrami32", width=200, depth=8, activation=1, splits=[2, 1, 1, 2],
                            anchor=[-0.4, 0.2, 0.3])
         res, obs, face = (90, 25), (40, 12), (30, 9)
-    elif name in ("tgv_ghost", "beltrami_ghost"):
-        cfg, pb = small_case(name[:-6] if name.startswith("tgv") else "beltrami32")
-        d = (0.4, 0.2) if name.startswith("tgv") else (0.3, 0.15)
+    elif name in ("tgv_ghost", "beltrami_ghost", "cyl2d_w150_ghost"):
+        cfg, pb = small_case({"tgv_ghost": "tgv", "beltrami_ghost": "beltrami32"}.get(name, "cyl2d_w150"))
+        d = (0.3, 0.15) if name.startswith("beltrami") else (0.4, 0.2)
         return cfg, synth.with_ghost_layers(pb, 70, delta_space=d[0], delta_time=d[1], seed=5)
     else:
         raise ValueError(name)
@@ -98,7 +98,7 @@ def small_case(name):
 
 CASES = ["kovasznay", "tgv", "beltrami32", "beltrami128", "steady3d_w64", "unsteady3d_w32",
          "unsteady3d_w64", "unsteady2d_w128_deep", "tgv_sin", "beltrami_sin", "tgv_ghost", "beltrami_ghost",
-         "cyl2d_w150", "cyl3d_w200"]
+         "cyl2d_w150", "cyl3d_w200", "cyl2d_w150_ghost"]
 
 
 def compare_losses(gpu, ref, tol=LOSS_TOL):
@@ -277,12 +277,12 @@ def test_redelivering_points_keeps_plan():
     assert not np.array_equal(g1, g2)
 
 
-@pytest.mark.parametrize("interval", [1, 3])
-def test_comm_interval_and_lr_decay_trajectory(interval):
+@pytest.mark.parametrize("name,interval", [("tgv", 1), ("tgv", 3), ("cyl2d_w150", 3)])
+def test_comm_interval_and_lr_decay_trajectory(name, interval):
     """Algorithm 1 with I_comm > 1 (stale messages between refreshes) and a
     step decay of the learning rate, 6 steps against the oracle."""
     Dpinn = _gpu()
-    cfg, pb = small_case("tgv")
+    cfg, pb = small_case(name)
     cfg = dict(cfg, comm_interval=interval, lr=3e-3, lr_decay_factor=0.5, lr_decay_interval=2)
     d = Dpinn(cfg)
     d.set_problem(pb)

@@ -57,7 +57,7 @@ def test_sampled_points_match_the_oracle_bit_for_bit():
     np.testing.assert_array_equal(d.get_points(RESIDUAL, n), ora.sample(seed, 5, counts))
 
 
-@pytest.mark.parametrize("name,precision", [("tgv", 0), ("beltrami32", 0), ("beltrami32", 1)])
+@pytest.mark.parametrize("name,precision", [("tgv", 0), ("beltrami32", 0), ("beltrami32", 1), ("cyl2d_w150", 0)])
 def test_losses_and_gradients_on_resampled_points_match_oracle(name, precision):
     d, cfg, pb, counts = _setup(name, precision)
     seed = 99
