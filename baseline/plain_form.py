@@ -94,6 +94,8 @@ class PlainForm:
         self.comm_interval = int(cfg.get("comm_interval", 1))
         self.t = 0
         self.msgs = None
+        self.anchor_t = torch.tensor(np.float32(cfg["anchor"][: self.ds]), dtype=dtype, device=self.dev)
+        self.graph = None
 
     def _cell(self, a, x):
         import numpy as np
@@ -137,7 +139,7 @@ class PlainForm:
         if self.master[k]:
             import numpy as np
             xa = x.clone()
-            xa[:, : self.ds] = torch.tensor(np.float32(self.cfg["anchor"][: self.ds]), dtype=self.dt, device=self.dev)
+            xa[:, : self.ds] = self.anchor_t
             P = P - self.net(k, xa)[:, self.ds]
         return y[:, : self.ds], P
 
@@ -157,7 +159,7 @@ class PlainForm:
                     P = y[:, self.ds]
                     if self.master[k]:
                         xa = x.clone()
-                        xa[:, : self.ds] = torch.tensor(np.float32(self.cfg["anchor"][: self.ds]), dtype=self.dt, device=self.dev)
+                        xa[:, : self.ds] = self.anchor_t
                         P = P - self.net(k, xa)[:, self.ds]
                     sides.append((y[:, : self.ds], P))
                 msgs.append(sides)
@@ -224,6 +226,45 @@ class PlainForm:
             self.sched.step()
         self.t += 1
         return rec
+
+    def capture(self, warmup=3):
+        """Capture one whole training step (exchange, per-net losses, double
+        backward, Adam) in a CUDA graph, the way the paper's pipeline replays
+        its step (Sec. 2.3); then ``replay()`` runs a step.  Needs a CUDA
+        device, I_comm = 1, no learning-rate schedule and no clipping."""
+        if self.dev.type != "cuda" or self.comm_interval != 1 or self.sched is not None or self.cfg["clip_norm"] > 0:
+            raise ValueError("graph capture needs CUDA, I_comm = 1, no LR schedule and no clipping")
+        params = [p for ps in self.params for p in ps]
+        self.opt = torch.optim.Adam(params, lr=self.cfg["lr"], betas=(self.cfg["beta1"], self.cfg["beta2"]),
+                                    eps=self.cfg["eps"], capturable=True)
+        snap = [p.detach().clone() for p in params]
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(warmup):
+                self.msgs = None
+                self.losses_and_grads()
+                self.opt.step()
+        torch.cuda.current_stream().wait_stream(side)
+        # the warm-up steps are undone: parameters and Adam state as before
+        with torch.no_grad():
+            for p, p0 in zip(params, snap):
+                p.copy_(p0)
+            for st in self.opt.state.values():
+                for v in st.values():
+                    if torch.is_tensor(v):
+                        v.zero_()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.msgs = None
+            self.rec_static = self.losses_and_grads()
+            self.opt.step()
+        return self
+
+    def replay(self):
+        self.graph.replay()
+        self.t += 1
+        return self.rec_static
 
     def flat(self, grads=False):
         out = []

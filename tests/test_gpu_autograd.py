@@ -139,3 +139,19 @@ def test_autotuned_schedule_keeps_parity(tmp_path, monkeypatch):
         og, _ = ora.grad(np.asarray(pb.theta0, np.float64))
         for k in range(d.n_nets):
             assert rel_l2(g[k], og[k]) <= GRAD_TOL
+
+
+def test_graph_captured_plain_form_matches_eager():
+    """The CUDA-graph-captured plain form (the benchmark's paper-form arm)
+    takes the same steps as the eager one."""
+    import torch
+    _gpu()
+    from baseline.plain_form import PlainForm
+    cfg, pb = small_case("tgv")
+    a = PlainForm(pb, device="cuda", dtype=torch.float32)
+    b = PlainForm(pb, device="cuda", dtype=torch.float32).capture()
+    for _ in range(3):
+        ra = a.step()
+        rb = b.replay()
+        torch.testing.assert_close(rb, ra, rtol=1e-4, atol=1e-6)
+    torch.testing.assert_close(b.flat(), a.flat(), rtol=1e-4, atol=1e-6)
