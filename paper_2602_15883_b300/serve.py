@@ -41,6 +41,7 @@ class Request:
     rid: int = 0
     retries: int = 0
     cancelled: bool = False
+    final: bool = False             # its outcome is being delivered: too late to cancel
     out: np.ndarray | None = None   # caller-owned result rows, filled in place
     done: threading.Event = field(default_factory=threading.Event)
 
@@ -152,7 +153,7 @@ class Server:
         with error "cancelled" (True); a finished request is left as it is
         (False)."""
         with self.lock:
-            if r.done.is_set():
+            if r.done.is_set() or r.final:
                 return False
             r.cancelled = True
             if r in self.pending:
@@ -267,7 +268,10 @@ class Server:
                 finished, retry = [], []
                 off = 0
                 for r in b[key_reqs]:
-                    if r.cancelled:
+                    with self.lock:   # decided once: a later cancel() returns False
+                        cancelled = r.cancelled
+                        r.final = True
+                    if cancelled:
                         r.error = "cancelled"
                     elif st == 0:
                         if r.out is not None:
@@ -278,6 +282,8 @@ class Server:
                     elif (st == ERR_INVALID_ARG and r.retries == 0 and
                           np.all((r.pts >= self.lo) & (r.pts <= self.hi))):
                         r.retries += 1       # an innocent neighbour of an outside point: run it again
+                        with self.lock:
+                            r.final = False
                         retry.append(r)
                         off += r.n
                         continue
