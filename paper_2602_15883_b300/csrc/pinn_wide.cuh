@@ -35,7 +35,9 @@ struct WideTile {
   static constexpr int KC = (WP > 160) ? 16 : 32;                                 // streamed weight rows
   static constexpr int IB = 4;                                                     // dW neurons per block
   static constexpr int NQ = TMG * NCOL;                                            // stashed floats per thread
+  static constexpr uint32_t STASH_LAYER_BYTES = (uint32_t)NQ * NTW * 4;           // one layer of a CTA's stash
   static_assert(RS >= PC && RS % 2 == 0 && P <= NTW && PC % 2 == 0, "wide tile");
+  static_assert(STASH_LAYER_BYTES % 128 == 0, "stash blocks are whole 128-byte lines");
 };
 
 template <int WP, int C, int DOUT>
@@ -52,6 +54,16 @@ __device__ __forceinline__ void cp_async(float* dst, const float* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// L2 residency of the stash: a block is prefetched into L2 (one bulk
+// prefetch, two reverse layers ahead of its reads) and discarded from L2
+// after its last read (no write-back of dead lines).
+__device__ __forceinline__ void wide_l2_prefetch(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void wide_l2_discard(const void* p) {
+  asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+}
 
 template <int WP, int VW>
 __device__ __forceinline__ void wide_chunk_copy(float* dst, const float* __restrict__ src, int nr, int ncols) {
@@ -195,6 +207,13 @@ __global__ void __launch_bounds__(NTW, 1)
 #pragma unroll
       for (int j = 0; j < NCOL; ++j) row[j] = a[j];
     }
+  };
+  auto stash_prefetch = [&](int l) {
+    if (t == 0) wide_l2_prefetch(stash + (size_t)l * T::NQ * NTW, T::STASH_LAYER_BYTES);
+  };
+  auto stash_discard = [&](int l) {   // after a barrier that follows the block's last reads
+    for (uint32_t o = (uint32_t)t * 128; o < T::STASH_LAYER_BYTES; o += NTW * 128)
+      wide_l2_discard(reinterpret_cast<const char*>(stash + (size_t)l * T::NQ * NTW) + o);
   };
   auto zero_acc = [&](float (&z)[TMG][NCOL]) {
 #pragma unroll
@@ -398,6 +417,7 @@ __global__ void __launch_bounds__(NTW, 1)
             for (int j = 0; j < NCOL; ++j) a[m][j] = fmaf(w, yb[j], a[m][j]);
           }
         }
+        if (L >= 2) stash_prefetch(L - 2);
         float z[TMG][NCOL];
         stash_ld(L - 1, z);
         __syncthreads();   // the dW_L loop above reads cur, which the first reverse layer overwrites
@@ -412,6 +432,7 @@ __global__ void __launch_bounds__(NTW, 1)
         }
       }
       for (int l = L - 1; l >= 1; --l) {
+        if (l >= 2) stash_prefetch(l - 2);
         {   // A_{l-1} into ab
           float z[TMG][NCOL];
           stash_ld(l - 1, z);
@@ -470,6 +491,7 @@ __global__ void __launch_bounds__(NTW, 1)
         float a[TMG][NCOL];
         zero_acc(a);
         wide_contract<WP, C, NCOL>(a, th + sh.woff[l], W, W, wch, zb, col0);
+        stash_discard(l);   // last read in the layer above, before this contraction's barriers
 #pragma unroll
         for (int m = 0; m < TMG; ++m) {
           float zz[NCOL];
@@ -481,6 +503,7 @@ __global__ void __launch_bounds__(NTW, 1)
         }
       }
       __syncthreads();
+      stash_discard(0);
       // first affine map: dW_0[i][q] += sum_p (Zb_val xh_q + s_q Zb_q), db_0
       for (int e = t; e < W * DIN; e += NTW) {
         const int i = e / DIN, q = e % DIN;
