@@ -11,7 +11,8 @@
 //
 // What it follows (equation numbers count the paper's numbered equations in
 // order of appearance):
-//   * network (u, p) = NN(x, t; theta), fully connected tanh MLP  - Sec. 2.1, Eq. (2)
+//   * network (u, p) = NN(x, t; theta), fully connected tanh MLP,
+//     or sin for the cylinder cases                               - Sec. 2.1, Eq. (2); Sec. 5
 //   * L_obs, mean over points of ||u_obs - u_NN||_2^2             - Eq. (3)
 //   * L_PDE, mean over points of ||r||_2^2                         - Eq. (5)
 //   * incompressible Navier-Stokes residuals r_1..r_4, 1/Re = nu   - Eqs. (6)-(10)
@@ -26,6 +27,13 @@
 //   * local objective L_{k,m}                                      - Eq. (16)
 //   * one optimiser step per iteration (Adam)                      - Algorithm 1
 //   * anchored pressure for output of master cells                 - Sec. 3, Eq. (18)
+//   * volumetric ghost layers of thickness delta (ghost points of A
+//     evaluated by the net whose cell holds them)                  - Sec. 2.2
+//   * interface residual and C1 matching terms on ghost points     - Remark, Sec. 2.2
+//   * messages refreshed every I_comm iterations, stale between    - Algorithm 1
+//   * step decay of the learning rate (factor, interval)           - Table B1
+//   * per-step uniform resampling of collocation points from
+//     counter-based SplitMix64 streams                             - Sec. 3 (epochs)
 //
 // Readings where the paper is silent (each listed in the design notes):
 //   * inputs are mapped from the net's own interior box to [-1, 1];
