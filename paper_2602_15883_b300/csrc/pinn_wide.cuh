@@ -65,6 +65,15 @@ __device__ __forceinline__ void wide_l2_discard(const void* p) {
   asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
 }
 
+// Gradient-slot accumulation: the first tile of an item stores, later ones
+// add in L2 without a read-back (fire and forget).  Each address has one
+// owning thread, whose operations on it stay in program order, so the sum
+// order is the tile order (deterministic).
+__device__ __forceinline__ void grad_acc(float* g, float v, bool first) {
+  if (first) *g = v;
+  else asm volatile("red.global.add.f32 [%0], %1;" ::"l"(g), "f"(v) : "memory");
+}
+
 template <int WP, int VW>
 __device__ __forceinline__ void wide_chunk_copy(float* dst, const float* __restrict__ src, int nr, int ncols) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -473,7 +482,7 @@ __global__ void __launch_bounds__(NTW, 1)
 #pragma unroll
               for (int m = 0; m < TMG; ++m) {
                 const int k = lane + 32 * m;
-                if (k < W) grad_rmw(gw + (size_t)i * W + k, acc[m][q].x + acc[m][q].y, first);
+                if (k < W) grad_acc(gw + (size_t)i * W + k, acc[m][q].x + acc[m][q].y, first);
               }
             }
           }
