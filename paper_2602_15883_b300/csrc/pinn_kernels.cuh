@@ -376,6 +376,15 @@ __device__ __forceinline__ void grad_rmw(float* g, float v, bool first) {
   *g = first ? v : (*g + v);
 }
 
+// Gradient-slot accumulation: the first tile of an item stores, later ones
+// add in L2 without a read-back (fire and forget).  Each address has one
+// owning thread, whose operations on it stay in program order, so the sum
+// order is the tile order (deterministic).
+__device__ __forceinline__ void grad_acc(float* g, float v, bool first) {
+  if (first) *g = v;
+  else asm volatile("red.global.add.f32 [%0], %1;" ::"l"(g), "f"(v) : "memory");
+}
+
 // Navier-Stokes residuals of one point from its output jets Y[j][c]
 // (c = value, d/dx_q for every input, spatial Laplacian; j = velocity
 // components then pressure), Eqs. (7)-(10):
@@ -890,11 +899,11 @@ __global__ void __launch_bounds__(NT, 1)
         // rows ig + NTI a and columns kg + NTI c; its KS lanes take interleaved
         // float4 chunks of pc.  The lanes' partial tiles are combined by a
         // shuffle reduce-scatter in a fixed order (lane ks ends with flat
-        // entries [NE ks, NE ks + NE) of the tile), and the read-modify-write of
-        // the entries into the item's gradient slot is software-pipelined into
-        // the next contraction so that its L2 latency overlaps the FMAs.  With
-        // KS > 1 the chunk offset moves the bank group, so kg is permuted to keep
-        // a quarter-warp's rows 4 groups apart.
+        // entries [NE ks, NE ks + NE) of the tile), which go into the item's
+        // gradient slot between the chunks of the next contraction: stored by
+        // the item's first tile, added by later ones with L2 reductions (no
+        // read-back).  With KS > 1 the chunk offset moves the bank group, so kg
+        // is permuted to keep a quarter-warp's rows 4 groups apart.
         constexpr int D = T::D, NTI = T::NTI, KS = T::KS, NE = D * D / KS;
         const int ks = t % KS, tile = t / KS;
         const int kq = tile % NTI;
@@ -954,7 +963,8 @@ __global__ void __launch_bounds__(NT, 1)
           const int e = NE * ks + i;
           return gw + (ig + NTI * (e / D)) * W + kg + NTI * (e % D);
         };
-        // A_{l-1} adjoint = W_l^T Zb_l, with the pipelined dW read-modify-write
+        // A_{l-1} adjoint = W_l^T Zb_l; the dW entries go out between its
+        // chunks (stores for the item's first tile, then L2 reductions)
         mbar_wait(&mbar, phase & 1, b.err);
         ++phase;
         float a[TM][NCOL];
@@ -964,29 +974,14 @@ __global__ void __launch_bounds__(NT, 1)
           for (int j = 0; j < NCOL; ++j) a[m][j] = 0.f;
         {
           constexpr int NCH = 8, NEH = (NE + NCH - 1) / NCH;
-          float ld[NEH];
 #pragma unroll
           for (int ch = 0; ch < NCH; ++ch) {
             contract_range<TM, NCOL, VEC>(a, wbuf, W, n0, zb, ROW, col0, ch * (W / NCH), (ch + 1) * (W / NCH));
-            if (ch > 0) {
 #pragma unroll
-              for (int q = 0; q < NEH; ++q) {
-                const int i = (ch - 1) * NEH + q;
-                if (i < NE) *waddr(i) = first ? dwv[i] : ld[q] + dwv[i];
-              }
+            for (int q = 0; q < NEH; ++q) {
+              const int i = ch * NEH + q;
+              if (i < NE) grad_acc(waddr(i), dwv[i], first);
             }
-            if (!first) {
-#pragma unroll
-              for (int q = 0; q < NEH; ++q) {
-                const int i = ch * NEH + q;
-                if (i < NE) ld[q] = *waddr(i);
-              }
-            }
-          }
-#pragma unroll
-          for (int q = 0; q < NEH; ++q) {
-            const int i = (NCH - 1) * NEH + q;
-            if (i < NE) *waddr(i) = first ? dwv[i] : ld[q] + dwv[i];
           }
         }
         __syncthreads();

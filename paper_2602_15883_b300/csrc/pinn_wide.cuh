@@ -65,15 +65,6 @@ __device__ __forceinline__ void wide_l2_discard(const void* p) {
   asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
 }
 
-// Gradient-slot accumulation: the first tile of an item stores, later ones
-// add in L2 without a read-back (fire and forget).  Each address has one
-// owning thread, whose operations on it stay in program order, so the sum
-// order is the tile order (deterministic).
-__device__ __forceinline__ void grad_acc(float* g, float v, bool first) {
-  if (first) *g = v;
-  else asm volatile("red.global.add.f32 [%0], %1;" ::"l"(g), "f"(v) : "memory");
-}
-
 template <int WP, int VW>
 __device__ __forceinline__ void wide_chunk_copy(float* dst, const float* __restrict__ src, int nr, int ncols) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
