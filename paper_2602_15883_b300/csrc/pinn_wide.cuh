@@ -391,12 +391,12 @@ __global__ void __launch_bounds__(NTW, 1)
         const int j = e / W, k = e % W;
         float s = 0.f;
         for (int pc = 0; pc < PC; ++pc) s = fmaf(ybsm[j * RS + pc], cur[k * RS + pc], s);
-        grad_rmw(g + sh.woff[L] + e, s, first);
+        grad_acc(g + sh.woff[L] + e, s, first);
       }
       if (t < DOUT) {
         float s = 0.f;
         for (int p = 0; p < P; ++p) s += ybsm[t * RS + p * C];
-        grad_rmw(g + sh.boff[L] + t, s, first);
+        grad_acc(g + sh.boff[L] + t, s, first);
       }
       float* zb = oth;
       float* ab = cur;
@@ -481,7 +481,7 @@ __global__ void __launch_bounds__(NTW, 1)
         for (int e = t; e < W; e += NTW) {
           float s = 0.f;
           for (int p = 0; p < P; ++p) s += zb[e * RS + p * C];
-          grad_rmw(g + sh.boff[l] + e, s, first);
+          grad_acc(g + sh.boff[l] + e, s, first);
         }
         // A_{l-1} adjoint = W_l^T Zb_l (rows of W_l streamed: i, entries k);
         // the stash of layer l - 1 is loaded first, its latency under the
@@ -512,12 +512,12 @@ __global__ void __launch_bounds__(NTW, 1)
           s = fmaf(zb[i * RS + p * C], xh[p * 4 + q], s);
           if constexpr (JETS) s = fmaf(s_scale[q], zb[i * RS + p * C + 1 + q], s);
         }
-        grad_rmw(g + sh.woff[0] + e, s, first);
+        grad_acc(g + sh.woff[0] + e, s, first);
       }
       for (int e = t; e < W; e += NTW) {
         float s = 0.f;
         for (int p = 0; p < P; ++p) s += zb[e * RS + p * C];
-        grad_rmw(g + sh.boff[0] + e, s, first);
+        grad_acc(g + sh.boff[0] + e, s, first);
       }
       __syncthreads();
     }   // sub-tiles
