@@ -23,12 +23,25 @@ def cache_path() -> str:
     return os.environ.get("DPINN_AUTOTUNE_CACHE", DEFAULT_CACHE)
 
 
-def schedule_key(cfg: dict, n_res: int, n_val: int, n_nets: int, device: str) -> str:
-    """Architecture, log2 buckets of the residual / value point totals, GPU."""
+def build_id() -> str:
+    """Identity of the loaded library build (size and modification time of
+    libdpinn.so): schedules tuned on another build are not reused."""
+    from .binding import LIB_PATH
+    try:
+        st = os.stat(LIB_PATH)
+        return f"{st.st_size}-{st.st_mtime_ns}"
+    except OSError:
+        return "nobuild"
+
+
+def schedule_key(cfg: dict, n_res: int, n_val: int, n_nets: int, device: str, build: str = "") -> str:
+    """Architecture, precision, activation, log2 buckets of the residual /
+    value point totals, GPU and library build."""
     din = cfg["d_space"] + cfg["unsteady"]
     b = lambda n: int(math.floor(math.log2(max(n, 1))))
     return (f"W{cfg['width']}-L{cfg['depth']}-din{din}-ds{cfg['d_space']}-nets{n_nets}"
-            f"-res2^{b(n_res)}-val2^{b(n_val)}-{device}")
+            f"-prec{cfg.get('precision', 0)}-act{cfg.get('activation', 0)}"
+            f"-res2^{b(n_res)}-val2^{b(n_val)}-{device}-{build}")
 
 
 def load_cache(path: str | None = None) -> dict:
@@ -72,7 +85,7 @@ def autotune(handle, n_res: int, n_val: int, reps: int = 3, use_cache: bool = Tr
     import torch
     stream = torch.cuda.current_stream()
     dev = torch.cuda.get_device_name(handle.cfg.get("device", 0)).replace(" ", "_")
-    key = schedule_key(handle.cfg, n_res, n_val, handle.n_nets, dev)
+    key = schedule_key(handle.cfg, n_res, n_val, handle.n_nets, dev, build_id())
     if use_cache:
         hit = load_cache().get(key)
         if hit:

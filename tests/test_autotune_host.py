@@ -23,3 +23,13 @@ def test_cache_roundtrip(tmp_path, monkeypatch):
     assert data["k1"]["jet_tiles"] == 8 and data["k2"]["order"] == 1
     p.write_text("not json")
     assert autotune.load_cache() == {}
+
+
+def test_key_separates_precision_activation_and_build():
+    from paper_2602_15883_b300 import autotune, synth
+    base = synth.config("beltrami32")
+    k = lambda cfg, build="b1": autotune.schedule_key(cfg, 262144, 65536, 32, "B300", build)
+    assert k(base) != k(dict(base, precision=1))
+    assert k(base) != k(dict(base, activation=1))
+    assert k(base) != k(base, "b2")
+    assert k(base) == k(dict(base))
