@@ -10,6 +10,14 @@ Prints one JSON line (rank 0).  `value` is device-timed with CUDA events
 around each step, L2 flushed (a 512 MiB buffer is written) between steps;
 `e2e` is the same metric through the C ABI with the residual points copied
 from pinned host memory and the loss record copied back every step.
+`roofline.traffic` is the DRAM traffic per launch of the same kernel from an
+ncu capture of the same workload (paper_2602_15883_b300/ncu_traffic.json),
+reported only while the kernel's sources are the captured ones;
+`roofline.probe_tflops` is the FP32 FMA rate measured now by the library's
+probe kernel.  `plain_form` also times the per-net loop captured in one CUDA
+graph.  Other workloads: kovasznay, beltrami32, beltrami128 (width 128, the
+tensor-core kernels by default), cylinder2d and cylinder3d (the paper's
+cylinder network shapes).
 --impl reference times the FP64 CPU oracle on a bounded sample instead.
 """
 from __future__ import annotations
