@@ -112,12 +112,24 @@ __device__ __forceinline__ void gacc(float* p, float v, bool first) {
   if (first) *p = v;
   else asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
 }
-__device__ __forceinline__ void gacc4(float* p, float4 v, bool first) {
-  if (first) *reinterpret_cast<float4*>(p) = v;
-  else
-    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+// A whole weight-gradient tile staged row-major in shared memory goes to the
+// item's slot in one asynchronous bulk operation issued by one thread: a store
+// for the item's first tile, an add performed at L2 for later ones.  The
+// issuing thread waits for each operation to complete (its global writes
+// included) before the staging region is reused, so the operations on an
+// address are applied one at a time in tile order (deterministic sums).
+// Both addresses are 16-byte aligned and `bytes` is a multiple of 16.
+__device__ __forceinline__ void bulk_flush(float* gdst, uint32_t ssrc, uint32_t bytes, bool first) {
+  if (first)
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(ssrc), "r"(bytes)
                  : "memory");
+  else
+    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(gdst), "r"(ssrc),
+                 "r"(bytes)
+                 : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
+__device__ __forceinline__ void bulk_flush_wait() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // L2 residency of the per-CTA stash: a bulk prefetch of a contiguous block
 // into L2 ahead of its loads, and a discard of its lines after their last
@@ -561,6 +573,7 @@ __global__ void __launch_bounds__(NTC, 1)
         for (int c = 0; c < C; ++c)
 #pragma unroll
           for (int u = 0; u < HP; ++u) put_row(c, u, zb[c][u]);   // zbar_l as [n][out]
+        if (t == 0) bulk_flush_wait();   // the previous layer's tile has left the staging region
         publish();
         issue(tm + TD, tm + TG, sX, sXl, NC * 128, W / 8, IDN);   // abar_{l-1} = W_l^T zbar_l
         stash_discard(l);   // its last reads (hsn) precede the barrier above
@@ -630,16 +643,20 @@ __global__ void __launch_bounds__(NTC, 1)
               }
             }
           }
-          // lane (8 gr + j) now holds chunk j of the rows of lanes 8 gr + c
+          // lane (8 gr + j) now holds chunk j of the rows of lanes 8 gr + c:
+          // the 8 lanes of a group store one 128-byte row segment (one
+          // wavefront) of the row-major tile, staged in the [neuron][n]
+          // operand region (idle until the next layer's activation operand)
           const int row0 = qd * 32 + (lane & ~7);
-          float* const gw = g + sh.woff[l] + (size_t)row0 * W + hq * KQ + 4 * (lane & 7);
+          float* const sw = reinterpret_cast<float*>(gA) + row0 * W + hq * KQ + 4 * (lane & 7);
 #pragma unroll
-          for (int c = 0; c < 8; ++c) gacc4(gw + (size_t)c * W, q[c], first);
+          for (int c = 0; c < 8; ++c) *reinterpret_cast<float4*>(sw + c * W) = q[c];
+          tc::fence_smem_async();
         }
-        if (l > 1) {   // the weight-gradient MMA (A operand zbar_l) has completed
-          put_w_staged(reinterpret_cast<const float*>(gX));
-          __syncthreads();   // all reads of the staged copy precede the next zbar rows
-        }
+        // the weight-gradient MMA (A operand zbar_l) has completed
+        if (l > 1) put_w_staged(reinterpret_cast<const float*>(gX));
+        __syncthreads();   // the staged tile is whole; reads of the staged weights precede the next zbar rows
+        if (t == 0) bulk_flush(g + sh.woff[l], sA, W * W * 4, first);
       }
       // first affine map: dW_0[i][q] += sum_p (zbar_val xh_q + s_q zbar_q), db_0
       __syncthreads();
@@ -668,6 +685,7 @@ __global__ void __launch_bounds__(NTC, 1)
 #pragma unroll
         for (int q = 0; q <= DIN; ++q) xpart[(hq * W + nrn) * 8 + q] = part[q];
       }
+      if (t == 0) bulk_flush_wait();   // layer 1's tile has left the staging region
       __syncthreads();
       if (hq == 0) {
 #pragma unroll

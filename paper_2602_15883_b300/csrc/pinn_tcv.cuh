@@ -426,6 +426,7 @@ __global__ void __launch_bounds__(NTC, 1)
         }
 #pragma unroll
         for (int u = 0; u < HP; ++u) put_row(u, zb[u]);
+        if (t == 0) bulk_flush_wait();   // the previous layer's tile has left the staging region
         publish();
         issue(tm + TD, tm + TG, sX, sXl, P * 128, W / 8, IDN);   // abar_{l-1} = W_l^T zbar_l
         stash_ld(l - 1, hsn);
@@ -480,15 +481,17 @@ __global__ void __launch_bounds__(NTC, 1)
               }
             }
           }
+          // staged row-major in the idle [neuron][n] operand region, one
+          // 128-byte row segment per group of 8 lanes
           const int row0 = qd * 32 + (lane & ~7);
-          float* const gw = g + sh.woff[l] + (size_t)row0 * W + hq * KQ + 4 * (lane & 7);
+          float* const sw = reinterpret_cast<float*>(gA) + row0 * W + hq * KQ + 4 * (lane & 7);
 #pragma unroll
-          for (int c = 0; c < 8; ++c) gacc4(gw + (size_t)c * W, q[c], first);
+          for (int c = 0; c < 8; ++c) *reinterpret_cast<float4*>(sw + c * W) = q[c];
+          tc::fence_smem_async();
         }
-        if (l > 1) {
-          put_w_staged(reinterpret_cast<const float*>(gX));
-          __syncthreads();
-        }
+        if (l > 1) put_w_staged(reinterpret_cast<const float*>(gX));
+        __syncthreads();
+        if (t == 0) bulk_flush(g + sh.woff[l], sA, W * W * 4, first);
       }
       // first affine map: dW_0[i][q] += sum_p zbar_p xh_{p,q}, db_0
       {
@@ -506,6 +509,7 @@ __global__ void __launch_bounds__(NTC, 1)
 #pragma unroll
         for (int q = 0; q <= DIN; ++q) xpart[(hq * W + nrn) * 8 + q] = part[q];
       }
+      if (t == 0) bulk_flush_wait();   // layer 1's tile has left the staging region
       __syncthreads();
       if (hq == 0) {
 #pragma unroll
