@@ -24,9 +24,11 @@ def _threads():
 
 
 @pytest.mark.parametrize("name,precision", [("tgv", 0), ("beltrami32", 0), ("beltrami128", 0),
-                                            ("beltrami32", 1), ("beltrami128", 1)])
+                                            ("beltrami32", 1), ("beltrami128", 1),
+                                            ("cylinder2d", 0), ("cylinder3d", 0)])
 def test_full_size_sampled_nets(name, precision):
-    """precision 1 = the tensor-core (3xTF32) jet kernel."""
+    """precision 1 = the tensor-core (3xTF32) jet kernel; the cylinder
+    workloads (6 x 150 and 8 x 200 sin nets) run the streamed-weight kernel."""
     Dpinn = _gpu()
     import torch
     cfg = synth.config(name)
