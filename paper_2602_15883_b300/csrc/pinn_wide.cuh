@@ -10,9 +10,9 @@
 //     activations (200 x 200 fp32 = 160 KB), so it is streamed through two
 //     buffers of 32 rows (16 above width 160) with cp.async while the
 //     previous chunk is contracted;
-//   * the weight gradient is accumulated per block of 4 output neurons per
-//     warp and written with coalesced read-modify-writes (lanes = input
-//     neurons).
+//   * the weight gradient is accumulated per block of 8 output neurons per
+//     warp (4 for the last rows) and added to the item's slot with
+//     coalesced L2 reductions (lanes = input neurons).
 // Rows of the activation buffers are 2 (mod 32) floats apart, so the
 // lane-strided 8-byte row loads of the weight gradient are conflict-free.
 #pragma once
@@ -21,6 +21,7 @@
 namespace dk {
 
 constexpr int NTW = 256;   // threads per CTA of the wide kernel
+template <int N> struct IntC { static constexpr int value = N; };   // a block size as a type
 static_assert(NTW == NT, "the block sums and launches assume NT threads");
 
 template <int WP, int C>
@@ -33,7 +34,6 @@ struct WideTile {
   static constexpr int PC = P * C;
   static constexpr int RS = ((PC + 29) / 32) * 32 + 2;                            // row stride, 2 (mod 32)
   static constexpr int KC = (WP > 160) ? 16 : 32;                                 // streamed weight rows
-  static constexpr int IB = 4;                                                     // dW neurons per block
   static constexpr int NQ = TMG * NCOL;                                            // stashed floats per thread
   static constexpr uint32_t STASH_LAYER_BYTES = (uint32_t)NQ * NTW * 4;           // one layer of a CTA's stash
   static_assert(RS >= PC && RS % 2 == 0 && P <= NTW && PC % 2 == 0, "wide tile");
@@ -441,12 +441,15 @@ __global__ void __launch_bounds__(NTW, 1)
         __syncthreads();
         // dW_l[i][k] += sum_pc Zb[i][pc] A_{l-1}[k][pc]: lanes take the input
         // neurons k = lane + 32 m, warp w the output neurons w + 8 r in blocks
-        // of IB; column pairs in order (a fixed summation order).
+        // of IB; column pairs in order (a fixed summation order).  Per column
+        // pair a block loads IB broadcast and TMG lane-strided 8-byte rows
+        // (IB + 2 TMG shared-memory wavefronts) for IB TMG packed FMAs: with
+        // IB = 8 that stays under the SM's half a wavefront per packed FMA.
         {
-          constexpr int IB = T::IB;
           float* const gw = g + sh.woff[l];
           const int nr = (W + 7) / 8;
-          for (int r0 = 0; r0 < nr; r0 += IB) {
+          auto dw_block = [&](auto ibc, int r0) {
+            constexpr int IB = decltype(ibc)::value;
             float2 acc[TMG][IB];   // .x the even, .y the odd columns
 #pragma unroll
             for (int m = 0; m < TMG; ++m)
@@ -476,7 +479,10 @@ __global__ void __launch_bounds__(NTW, 1)
                 if (k < W) grad_acc(gw + (size_t)i * W + k, acc[m][q].x + acc[m][q].y, first);
               }
             }
-          }
+          };
+          int r0 = 0;
+          for (; r0 + 8 <= nr; r0 += 8) dw_block(IntC<8>(), r0);
+          for (; r0 < nr; r0 += 4) dw_block(IntC<4>(), r0);
         }
         for (int e = t; e < W; e += NTW) {
           float s = 0.f;
