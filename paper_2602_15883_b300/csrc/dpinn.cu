@@ -803,6 +803,12 @@ int dpinn_create(const dpinn_config* cfg, dpinn_t** out) {
   }
   h->n_params = off;
   h->npp = ((off + 63) / 64) * 64;
+  // the tensor-core kernels move each hidden-layer weight-gradient tile of a
+  // slot with one bulk operation, which needs a 16-byte aligned address (true
+  // for W = 128: every woff[l], l >= 1, is a multiple of 128 floats)
+  if (c.precision == DPINN_PREC_TF32X3)
+    for (int l = 1; l < h->L; ++l)
+      if (sh.woff[l] % 4 != 0) return fail(nullptr, DPINN_ERR_INVALID_ARG, "weight-gradient tile not 16-byte aligned");
   h->nTp = std::max(1, (h->L - 1) * h->W * h->W);
   sh.npp = h->npp; sh.nTp = h->nTp;
   sh.act = (c.activation == DPINN_ACT_SIN) ? dk::ACT_SIN : dk::ACT_TANH;
