@@ -113,7 +113,7 @@ typedef struct dpinn_config {
   double lambda_gh_p_space; /* base value; masters use 0 */
   double lambda_gh_p_time;
   double comp_w[3];       /* velocity component weights in L_obs, L_gh_u */
-  double lr, beta1, beta2, eps;
+  double lr, beta1, beta2, eps; /* Adam (PyTorch's rule); beta1, beta2 in [0, 1), else INVALID_ARG */
   double clip_norm;       /* per-net gradient-norm clip, 0 = off */
   uint64_t seed;          /* Xavier-normal initialisation seed */
   int precision;          /* DPINN_PREC_FP32 or DPINN_PREC_TF32X3 */

@@ -209,6 +209,14 @@ dk::Bufs make_bufs(dpinn* h) {
   return b;
 }
 
+// Adam's arguments; the logarithms feed the FP32 bias corrections of k_adam
+dk::AdamArgs adam_args(const dpinn* h) {
+  const dpinn_config& c = h->cfg;
+  return dk::AdamArgs{c.lr, c.beta1, c.beta2, c.eps, c.clip_norm > 0 ? 1 : 0, c.lr_decay_factor,
+                      c.lr_decay_interval, (float)std::log(c.beta1), (float)std::log(c.beta2),
+                      (float)std::log(c.lr_decay_factor)};
+}
+
 cudaError_t launch_pinn(const void* fn, int grid, size_t smem, const dk::Shape& sh, const dk::Bufs& b,
                         const dk::Item* items, const int* n_items, cudaStream_t s, int threads = dk::NT) {
   void* args[] = {(void*)&sh, (void*)&b, (void*)&items, (void*)&n_items};
@@ -343,8 +351,7 @@ cudaError_t enqueue_step(dpinn* h, int mode, cudaStream_t s, int* n_launch, cuda
       ++launches;
       mark("clip");
     }
-    dk::AdamArgs ar{h->cfg.lr, h->cfg.beta1, h->cfg.beta2, h->cfg.eps, h->cfg.clip_norm > 0 ? 1 : 0,
-                   h->cfg.lr_decay_factor, h->cfg.lr_decay_interval};
+    const dk::AdamArgs ar = adam_args(h);
     dk::k_adam<<<dim3(nblk, h->n_nets), dk::NT, 0, s>>>(h->shape, ar, h->theta.p, h->thetaT.p, h->m.p, h->v.p,
                                                          h->grad.p, h->coef.p, h->step_d.p, h->n_params);
     e = cudaGetLastError();
@@ -698,6 +705,8 @@ int dpinn_create(const dpinn_config* cfg, dpinn_t** out) {
   if (c.comm_interval < 1) return fail(nullptr, DPINN_ERR_INVALID_ARG, "comm_interval must be >= 1");
   if (!(c.lambda_gh_r >= 0.0) || !(c.lambda_gh_c1 >= 0.0))
     return fail(nullptr, DPINN_ERR_INVALID_ARG, "interface weights must be >= 0");
+  if (!(c.beta1 >= 0 && c.beta1 < 1) || !(c.beta2 >= 0 && c.beta2 < 1))
+    return fail(nullptr, DPINN_ERR_INVALID_ARG, "Adam betas must be in [0, 1)");
   if (c.lr_decay_interval < 0 || !(c.lr_decay_factor > 0))
     return fail(nullptr, DPINN_ERR_INVALID_ARG, "bad learning-rate decay");
   const int din = c.d_space + c.unsteady;
@@ -1314,8 +1323,7 @@ int dpinn_apply_grad(dpinn_t* h, const float* host_grad) {
                                                         h->n_params);
   if (h->cfg.clip_norm > 0)
     dk::k_clip_coef<<<h->n_nets, dk::NT>>>(h->norm_part.p, nblk, (float)h->cfg.clip_norm, h->coef.p);
-  dk::AdamArgs ar{h->cfg.lr, h->cfg.beta1, h->cfg.beta2, h->cfg.eps, h->cfg.clip_norm > 0 ? 1 : 0,
-                   h->cfg.lr_decay_factor, h->cfg.lr_decay_interval};
+  const dk::AdamArgs ar = adam_args(h);
   dk::k_adam<<<dim3(nblk, h->n_nets), dk::NT>>>(h->shape, ar, h->theta.p, h->thetaT.p, h->m.p, h->v.p, h->grad.p,
                                                  h->coef.p, h->step_d.p, h->n_params);
   dk::k_loss_record<<<1, 32>>>(h->shape, h->loss_part.p, h->slot_begin_d.p, h->nets_d.p, 0, h->loss_rec.p,

@@ -43,6 +43,11 @@ struct AdamArgs {
   int use_clip;
   double decay_factor;   // lr * decay_factor^floor((t-1)/decay_interval)
   int decay_interval;    // 0: constant lr
+  // log(beta1), log(beta2), log(decay_factor), formed in double on the host:
+  // the bias corrections 1 - beta^t = -expm1(t log beta) then take a few FP32
+  // operations with about 1e-7 relative error (1 - 0.999^t included), where
+  // FP64 pow on every block cost more than the update itself
+  float log_beta1, log_beta2, log_decay;
 };
 // (1 - beta) factors are formed in double on the host and rounded once:
 // 1.f - 0.999f would carry a 1.3e-5 relative error into the second moment.
@@ -54,13 +59,16 @@ __global__ void k_adam(const Shape sh, AdamArgs ar, float* __restrict__ theta, f
                        const float* __restrict__ coef, const long long* __restrict__ step, int n_params) {
   __shared__ float s_c[4];
   if (threadIdx.x == 0) {
-    const double t = (double)(*step + 1);
-    const double bc1 = 1.0 - pow(ar.beta1, t);
-    const double bc2 = 1.0 - pow(ar.beta2, t);
-    double lr = ar.lr;
-    if (ar.decay_interval > 0) lr *= pow(ar.decay_factor, (double)((*step) / ar.decay_interval));
-    s_c[0] = (float)(lr / bc1);
-    s_c[1] = (float)(1.0 / sqrt(bc2));
+    const float t = (float)(*step + 1);
+    const float bc1 = -expm1f(t * ar.log_beta1);
+    const float bc2 = -expm1f(t * ar.log_beta2);
+    float lr = (float)ar.lr;
+    if (ar.decay_interval > 0) {
+      const long long n = (*step) / ar.decay_interval;
+      if (n > 0) lr *= expf((float)n * ar.log_decay);
+    }
+    s_c[0] = lr / bc1;
+    s_c[1] = 1.f / sqrtf(bc2);
   }
   __syncthreads();
   const int k = blockIdx.y;

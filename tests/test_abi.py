@@ -44,7 +44,8 @@ def test_config_default_is_host_only(lib):
 
 @pytest.mark.parametrize("field,value", [("width", 48), ("width", 100), ("width", 225), ("depth", 0),
                                          ("d_space", 4), ("activation", 2),
-                                         ("precision", 2), ("precision", 1)])
+                                         ("precision", 2), ("precision", 1),
+                                         ("beta1", 1.0), ("beta2", -0.1), ("beta2", float("nan"))])
 def test_create_rejects_bad_configs_before_touching_a_device(lib, field, value):
     c = binding.Config()
     lib.dpinn_config_default(C.addressof(c))
