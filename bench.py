@@ -393,8 +393,8 @@ def main():
     ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
     loss = d.loss()
     assert np.all(np.isfinite(loss)), "non-finite loss"
-    step_ms = float(np.median(ms))
     total_ms = float(ms.sum())
+    step_ms = total_ms / args.steps   # the mean, so that value = points / step time
     if dist:
         total_ms, step_ms = max_over_ranks(dist, [total_ms, step_ms], "cuda")
     value = whole_job_value(world, pb.n_res, args.steps, total_ms)
