@@ -184,6 +184,39 @@ def test_optimizer_update_matches_oracle_adam():
     assert rel_l2(gv, v) < 1e-5
 
 
+@pytest.mark.parametrize("beta1,beta2,t0,decay", [(0.9, 0.999, 0, None), (0.0, 0.5, 0, None),
+                                                  (0.9, 0.999, 997, None), (0.5, 0.9999, 20000, None),
+                                                  (0.9, 0.999, 41, (0.5, 10))])
+def test_adam_updates_match_oracle(beta1, beta2, t0, decay):
+    """The update itself (not the parameters, which it barely moves) against
+    the oracle's Adam: bias corrections 1 - beta^t at early and late steps,
+    beta1 = 0, and the learning-rate step decay."""
+    Dpinn = _gpu()
+    cfg, pb = small_case("tgv")
+    cfg = dict(cfg, beta1=beta1, beta2=beta2, lr=1e-3)
+    if decay:
+        cfg.update(lr_decay_factor=decay[0], lr_decay_interval=decay[1])
+    d = Dpinn(cfg)
+    d.set_problem(pb)
+    ora = oracle.Oracle(cfg, pb)
+    n = ora.n_nets * ora.n_params
+    rng = np.random.default_rng(t0 + 7)
+    # parameters of order 1e-3, so that the FP32 rounding of theta_1 stays far
+    # below the update (the decayed case moves them by lr / 16)
+    th0 = (1e-3 * rng.standard_normal(n)).astype(np.float32)
+    m0 = (0.01 * rng.standard_normal(n)).astype(np.float32)
+    v0 = (1e-4 * rng.random(n)).astype(np.float32)
+    d.set_state(th0, m0, v0, step=t0)
+    g = synth.random_grad(cfg, seed=3, scale=0.05).astype(np.float32)
+    d.apply_grad(g)
+    th1, m1, v1, t1 = d.get_state()
+    oth, om, ov, ot = ora.adam(th0, m0, v0, t0, g.astype(np.float64))
+    assert t1 == ot == t0 + 1
+    assert rel_l2(th1.astype(np.float64) - th0, oth - th0) < 1e-5
+    assert rel_l2(m1, om) < 1e-6
+    assert rel_l2(v1, ov) < 1e-6
+
+
 def test_multi_step_trajectory_tracks_oracle():
     Dpinn = _gpu()
     cfg, pb = small_case("tgv")
