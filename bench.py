@@ -26,6 +26,7 @@ import argparse
 import glob
 import json
 import os
+import platform
 import subprocess
 import sys
 import time
@@ -230,9 +231,21 @@ def cpu_baseline(cfg, pb, budget_s=15.0):
     for _ in range(reps):
         ora.step(th, np.zeros_like(th), np.zeros_like(th), 0)
     dt = (time.perf_counter() - t0) / reps
-    return {"value": sub.n_res / dt, "unit": "residual-points/s", "cores": cores, "kind": "oracle",
+    return {"value": sub.n_res / dt, "unit": "residual-points/s", "cores": cores, "cpu": cpu_model(), "kind": "oracle",
             "sample": f"all {synth.n_nets(cfg)} nets with 1/{f} of their points ({sub.n_res} residual pts), "
                       f"FP64 loss+gradient+Adam, {reps} steps"}
+
+
+def cpu_model():
+    """The host CPU's model name (read at run time), for the CPU baseline."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or None
 
 
 def run_reference(args):
