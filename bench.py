@@ -2,16 +2,21 @@
 subdomain networks (grouped jet forward + residuals + losses + reverse pass +
 Adam) on synthetic analytic-flow data.
 
-Default workload: the 2D unsteady Taylor-Green vortex, 4 x 4 x 2 = 32 nets
-of 6 x 64 tanh, 8,192 residual + 1,024 noisy velocity points per net and 512
-points per shared face (64 faces).  --workload picks another configuration.
+Default workload: the 3-D unsteady Beltrami flow decomposed into 4 x 4 x 2
+space x 4 time = 128 nets of 6 x 128 tanh, residual points per net drawn
+from a truncated power law n^-1.2 on [2,048, 65,536] (about 1.97 M in all),
+2,048 noisy velocity points per net and 1,024 points per shared face (352
+faces); the headline runs the FP32 kernels (the paper's arithmetic).  The
+same line carries the tcgen05 3xTF32 variant of that workload (key
+"tf32x3") and the 32-net Taylor-Green workload (key "tgv") measured the same
+way.  --workload picks another headline configuration.
 
 Prints one JSON line (rank 0).  `value` is device-timed with CUDA events
 around each step, L2 flushed (a 512 MiB buffer is written) between steps;
 `e2e` is the same metric through the C ABI with the residual points copied
 from pinned host memory and the loss record copied back every step.
 `roofline.traffic` is the DRAM traffic per launch of the same kernel from an
-ncu capture of the same workload (paper_2602_15883_b300/ncu_traffic.json),
+ncu capture of the same workload (profiles/ncu_traffic.json),
 reported only while the kernel's sources are the captured ones;
 `roofline.probe_tflops` is the FP32 FMA rate measured now by the library's
 probe kernel.  `plain_form` also times the per-net loop captured in one CUDA
@@ -158,7 +163,7 @@ def whole_job_value(world, n_res_per_rank, steps, total_ms_max):
     return world * n_res_per_rank * steps / (total_ms_max / 1e3)
 
 
-TRAFFIC_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2602_15883_b300", "ncu_traffic.json")
+TRAFFIC_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "ncu_traffic.json")
 
 
 def kernel_source_sha256(files):
@@ -334,54 +339,26 @@ def serving_leg(seconds=5.0, rate=200.0, train_steps=20, seed=0, precision="tf32
     return out
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="tgv", choices=list(synth.CONFIGS))
-    ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--no-baselines", action="store_true", help="skip the plain-form and CPU legs")
-    ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
-    ap.add_argument("--serving-seconds", type=float, default=5.0)
-    ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule")
-    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "tf32x3"],
-                    help="hidden-layer contractions of the jet kernel: FP32 FMA, or tcgen05 3xTF32 (width 128); "
-                         "auto = tf32x3 where the width allows it")
-    args = ap.parse_args()
-    args.warmup = max(args.warmup, 3)
-    if args.impl == "reference":
-        return run_reference(args)
-
+def measure(args, workload, precision, rank, world, local, dist, stream, clocks=True):
+    """Device-timed training steps, per-kernel times, roofline and the
+    end-to-end rate of one (workload, precision) on this rank's replica.
+    Returns the handle's problem and a dict of results."""
     import torch
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    from paper_2602_15883_b300 import build
-    build.build()
     from paper_2602_15883_b300.binding import POINTS_RESIDUAL, Dpinn
-
-    cfg, pb = make_problem(args, rank)
+    cfg = synth.config(workload)
+    pb = synth.make_problem(cfg, seed=args.seed + rank)
     cfg["device"] = local
-    if args.precision == "auto":
-        args.precision = "tf32x3" if cfg["width"] == 128 else "fp32"
-    cfg["precision"] = PRECISIONS[args.precision]
+    cfg["precision"] = PRECISIONS[precision]
     d = Dpinn(cfg)
     d.set_problem(pb)
-    stream = torch.cuda.current_stream()
     schedule = {"jet_tiles": 0, "val_tiles": 0, "order": 0, "tuned": False}
     if not args.no_autotune:
         from paper_2602_15883_b300 import autotune
         n_val = int(pb.obs_counts.sum() + 2 * pb.face_counts.sum())
         res = autotune.autotune(d, pb.n_res, n_val, reps=3)
         schedule = {k: res[k] for k in ("jet_tiles", "val_tiles", "order")}
-        schedule.update(tuned=True, cached=res.get("cached", False), tile_points=d.get_schedule()["tile_points"])
+        schedule.update(tuned=True, cached=res.get("cached", False))
+    schedule["tile_points"] = d.get_schedule()["tile_points"]
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     d.step(args.warmup, stream)
     d.loss()
@@ -389,7 +366,8 @@ def main():
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clk = Clocks(local)
-    clk.start()
+    if clocks:
+        clk.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -420,13 +398,13 @@ def main():
             kt.setdefault(k, []).append(v)
     kms = {k: float(np.mean(v)) for k, v in kt.items()}
     jet_ms = kms.get("train_jet", float("nan"))
-    clk.stop()
-    clocks = clk.summary()
+    if clocks:
+        clk.stop()
     pk, pk_kind = peaks()
     sm_mhz = float(pk.get("sm_max_mhz", 2032.0))
     jet_flops = flops_per_point(cfg, True) * pb.n_res
     achieved = jet_flops / (jet_ms / 1e3) / 1e12
-    if args.precision == "fp32":
+    if precision == "fp32":
         peak = fp32_alu_peak_tflops(sm_mhz)
         # context: the attainable FP32 FMA rate measured now by the library's
         # packed-FMA chain probe (a ~20 ms burst)
@@ -436,20 +414,23 @@ def main():
         probe_tflops = p_flop / (p_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "probe_tflops": probe_tflops, "frac_of_probe": achieved / probe_tflops,
-                    "frac": achieved / peak, "traffic": captured_traffic(args.workload, "fp32"),
+                    "frac": achieved / peak, "traffic": captured_traffic(workload, "fp32"),
                     "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                     "kernel": "k_pinn train (jets)" if cfg["width"] in (32, 64, 128) else "k_pinn_w train (jets)",
+                    "work_per_launch": f"{flops_per_point(cfg, True)} FLOP per residual point x {pb.n_res} points",
                     "peak_source": f"148 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (max SM clock, {pk_kind})",
                     "kernel_ms": kms}
     else:
         peak = tf32_tensor_peak_tflops(pk)
         hidden = 3 * 2 * (synth.d_in(cfg) + 2) * cfg["width"] ** 2 * (cfg["depth"] - 1) * pb.n_res
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": captured_traffic(args.workload, "tf32x3"),
+                    "frac": achieved / peak, "traffic": captured_traffic(workload, "tf32x3"),
                     "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                     "kernel": "k_pinn_tc train (jets, tcgen05 3xTF32)",
+                    "work_per_launch": f"{flops_per_point(cfg, True)} FLOP per residual point x {pb.n_res} points",
                     "peak_source": f"dense TF32 = measured bf16 burst x 1.1/2.25 (nominal ratio, {pk_kind})",
                     "hw_tflops_3x": 3 * hidden / (jet_ms / 1e3) / 1e12,
+                    "frac_3x": 3 * hidden / (jet_ms / 1e3) / 1e12 / peak,
                     "note": "achieved counts every product once; the tensor cores execute three per product",
                     "kernel_ms": kms}
 
@@ -490,20 +471,79 @@ def main():
         (e2e_s,) = max_over_ranks(dist, [e2e_s], "cuda")
     e2e = {"value": world * pb.n_res * e2e_steps / e2e_s, "unit": "residual-points/s",
            "h2d_bytes_per_step": int(pinned[0].numel() * 4), "d2h_bytes_per_step": int(out.nbytes)}
+    r = {"value": value, "ms_per_step": step_ms, "dtype": "f32" if precision == "fp32" else "tf32x3",
+         "config": {"workload": workload, "n_nets": d.n_nets, "width": cfg["width"], "depth": cfg["depth"],
+                    "residual_points": pb.n_res, "precision": precision,
+                    "obs_points": int(pb.obs_counts.sum()), "face_points": int(pb.face_counts.sum()),
+                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                    "l2": "flushed between steps (512 MiB write)", "schedule": schedule},
+         "roofline": roofline, "e2e": e2e, "gpu_launches": d.launches_per_step * args.steps,
+         "step_gflop": step_flops(cfg, pb) / 1e9}
+    if clocks:
+        r["clocks"] = clk.summary()
+    d.close()
+    del flush, pinned
+    torch.cuda.empty_cache()
+    return cfg, pb, r
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="beltrami128", choices=list(synth.CONFIGS))
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-baselines", action="store_true", help="skip the plain-form and CPU legs")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the extra measurements (the TF32x3 variant at width 128, the TGV workload)")
+    ap.add_argument("--serving-seconds", type=float, default=5.0)
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule")
+    ap.add_argument("--precision", default="fp32", choices=["auto", "fp32", "tf32x3"],
+                    help="hidden-layer contractions of the headline's jet kernel: FP32 FMA (the paper's "
+                         "arithmetic, default), or tcgen05 3xTF32 (width 128); auto = tf32x3 where the width "
+                         "allows it")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2602_15883_b300 import build
+    build.build()
+
+    width = synth.config(args.workload)["width"]
+    if args.precision == "auto":
+        args.precision = "tf32x3" if width == 128 else "fp32"
+    stream = torch.cuda.current_stream()
+    cfg, pb, head = measure(args, args.workload, args.precision, rank, world, local, dist, stream)
+    extras = {}
+    if not args.no_extras:
+        # the other arithmetic of the width-128 kernels, and the 32-net TGV workload
+        if width == 128:
+            other = "tf32x3" if args.precision == "fp32" else "fp32"
+            extras[other] = measure(args, args.workload, other, rank, world, local, dist, stream, clocks=False)[2]
+        if args.workload != "tgv":
+            extras["tgv"] = measure(args, "tgv", "fp32", rank, world, local, dist, stream, clocks=False)[2]
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "residual-points/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "tf32x3",
-                "data": "synthetic",
-                "config": {"workload": args.workload, "n_nets": d.n_nets, "width": cfg["width"],
-                           "depth": cfg["depth"], "residual_points": pb.n_res, "precision": args.precision,
-                           "obs_points": int(pb.obs_counts.sum()), "face_points": int(pb.face_counts.sum()),
-                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                           "l2": "flushed between steps (512 MiB write)", "schedule": schedule},
-                "roofline": roofline, "clocks": clocks, "e2e": e2e,
-                "gpu_launches": d.launches_per_step * args.steps,
-                "step_gflop": step_flops(cfg, pb) / 1e9}
+        line = {"metric": METRIC, "value": head["value"], "unit": "residual-points/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": head["dtype"],
+                "data": "synthetic", "config": head["config"], "roofline": head["roofline"],
+                "clocks": head["clocks"], "e2e": head["e2e"], "gpu_launches": head["gpu_launches"],
+                "step_gflop": head["step_gflop"]}
+        line.update(extras)
         if not args.no_baselines:
             try:
                 line["plain_form"] = plain_form_rate(cfg, pb)
@@ -518,7 +558,6 @@ def main():
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
-        dist.destroy_process_group()
 
 
 if __name__ == "__main__":

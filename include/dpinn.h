@@ -90,9 +90,12 @@ enum { DPINN_ACT_TANH = 0, DPINN_ACT_SIN = 1 };
  * contractions per layer (forward, input adjoint, weight gradient) run on the
  * tcgen05 tensor cores with every FP32 operand split into two TF32 parts and
  * the products accumulated as hi*lo + lo*hi + hi*hi in FP32 (relative error
- * per product ~2^-21, FP32-grade); everything else stays FP32.  Value
- * kernels (observations, ghost terms, messages) and queries are FP32 in both
- * modes.  The paper (Sec. 3) trains in FP32 and fixes no kernel arithmetic. */
+ * per product ~2^-21, FP32-grade); everything else stays FP32.  In TF32X3
+ * the value kernels (observations, ghost terms, messages) and the queries use
+ * the same tensor-core arithmetic for their hidden layers, except that the
+ * exchange and the face items run the FP32 jet kernels when the interface
+ * terms (lambda_gh_r, lambda_gh_c1) are on.  The paper (Sec. 3) trains in
+ * FP32 and fixes no kernel arithmetic. */
 enum { DPINN_PREC_FP32 = 0, DPINN_PREC_TF32X3 = 1 };
 
 typedef struct dpinn_config {
@@ -299,6 +302,19 @@ int dpinn_get_grad(dpinn_t* h, float* host_out);
  * (INVALID_ARG); its row is left untouched. */
 int dpinn_query(dpinn_t* h, const float* dev_pts, int64_t n, int want_residual,
                 float* dev_out, dpinn_stream_t stream);
+/* Output jets of the nets at routed points: for each point, the jets of the
+ * net whose cell holds it, row [j][c] of d_out x (d_in + 2) floats - outputs
+ * j = (u, v, [w], p), channels c = value, d/dx_q for every input q (spatial
+ * axes, then time), spatial Laplacian.  These are the forward jets the
+ * residuals of Eqs. (7)-(10) are assembled from (value, first derivatives and
+ * Laplacian carried through the network of Eq. (2), Sec. 2.1).  The pressure
+ * is the net's raw output (no anchoring, no p_ref).  Same kernels, routing,
+ * ownership, asynchrony and error reporting as dpinn_query with
+ * want_residual = 1; pts [n][d_in] and out [n][d_out][d_in + 2] are device
+ * pointers owned by the caller.  Errors: INVALID_ARG (n < 0 or > 2^30, null
+ * pointers), OOM, CUDA; points outside the domain as for dpinn_query. */
+int dpinn_query_jets(dpinn_t* h, const float* dev_pts, int64_t n, float* dev_out, dpinn_stream_t stream);
+
 /* Query contexts: dpinn_query shares one scratch per handle, so two of its
  * calls must not overlap on the GPU.  A context owns its own routing scratch
  * for up to max_points points per call (allocated once, here) and its own
@@ -328,7 +344,11 @@ int dpinn_qctx_status(dpinn_qctx_t* q, dpinn_stream_t stream);
  *     with a message; pts/out are device pointers owned by the caller.
  *   - The first call on a device looks up the array's device address (once
  *     per device, with that device made current); make that first call
- *     before any stream capture.
+ *     before any stream capture.  The address is kept for the life of the
+ *     process: it does not survive a device reset.
+ *   - A request whose work items would not fit the array is refused with
+ *     STATE before anything is launched (cannot happen with the kernels of
+ *     this library, whose query tiles have at least 16 points).
  *   - All calls share the one array and leave their contents in it; each
  *     call clears what must start at zero.  Calls that overlap on the GPU
  *     (different streams, or several handles on one device) race on it:

@@ -31,6 +31,7 @@ EXPORTS = (
     "dpinn_qctx_create", "dpinn_qctx_destroy", "dpinn_qctx_query", "dpinn_qctx_status",
     "dpinn_set_resampling", "dpinn_get_points", "dpinn_set_partial_budget", "dpinn_loss_ext",
     "dpinn_set_points_async", "dpinn_selftest_wait", "dpinn_loss_async", "dpinn_probe_fp32",
+    "dpinn_query_jets",
 )
 
 
@@ -88,6 +89,7 @@ def load_library(path: str = LIB_PATH):
         "dpinn_loss": ([vp, vp], i32),
         "dpinn_get_grad": ([vp, vp], i32),
         "dpinn_query": ([vp, vp, i64, i32, vp, vp], i32),
+        "dpinn_query_jets": ([vp, vp, i64, vp, vp], i32),
         "dpinn_query_status": ([vp, vp], i32),
         "dpinn_get_state": ([vp, vp, vp, vp, vp], i32),
         "dpinn_set_state": ([vp, vp, vp, vp, i64], i32),
@@ -400,6 +402,22 @@ class Dpinn:
         o, ko = _ptr(out)
         s = _stream(stream)
         self._check(self.lib.dpinn_query(self.h, p, n, int(bool(want_residual)), o, s))
+        if check:
+            self._check(self.lib.dpinn_query_status(self.h, s))
+        return out
+
+    def query_jets(self, pts, out=None, stream=None, check=True):
+        """Raw output jets of the routed nets at device points: [n][d_out][d_in + 2]
+        (channels: value, d/dx_q for every input, spatial Laplacian)."""
+        import torch
+        n = pts.shape[0]
+        C = self.d_in + 2
+        if out is None:
+            out = torch.empty((n, self.d_out, C), dtype=torch.float32, device=pts.device)
+        p, kp = _ptr(pts)
+        o, ko = _ptr(out)
+        s = _stream(stream)
+        self._check(self.lib.dpinn_query_jets(self.h, p, n, o, s))
         if check:
             self._check(self.lib.dpinn_query_status(self.h, s))
         return out

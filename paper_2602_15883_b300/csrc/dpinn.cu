@@ -603,16 +603,29 @@ int check_errors(dpinn* h) {
 struct QueryScratch {
   int *net_of, *perm, *counts, *offsets, *cursor, *nitems;
   dk::Item* items;
-  int* err;   // error words the route and query kernels report to
+  int* err;          // error words the route and query kernels report to
+  size_t items_cap;  // capacity of `items`
 };
+
+// Query modes: values, values + Navier-Stokes residuals, raw output jets.
+enum { Q_VALUES = 0, Q_RESIDUAL = 1, Q_JETS = 2 };
+
+// Points per work item of a query in `mode` (four tiles of its kernel).
+int64_t query_chunk(const dpinn* h, int mode) { return 4 * (int64_t)(mode == Q_VALUES ? h->ks.P_qval : h->ks.P_qjet); }
+
+// Upper bound of the work items of an n-point query: one per started chunk
+// of every net's segment.
+size_t query_max_items(const dpinn* h, int64_t n, int mode) {
+  return (size_t)(n / query_chunk(h, mode)) + h->n_nets + 1;
+}
 
 // Route n points to their nets, order them by net, build the work items and
 // launch the grouped query kernel, all on stream s.
-int enqueue_query(dpinn* h, const QueryScratch& q, const float* pts, int64_t n, int want_residual, float* out,
+int enqueue_query(dpinn* h, const QueryScratch& q, const float* pts, int64_t n, int mode, float* out,
                   cudaStream_t s) {
-  const int P = want_residual ? h->ks.P_qjet : h->ks.P_qval;
-  const int chunk = 4 * P;
-  const size_t max_items = (size_t)(n / chunk) + h->n_nets + 1;
+  const int chunk = (int)query_chunk(h, mode);
+  const size_t max_items = query_max_items(h, n, mode);
+  if (max_items > q.items_cap) return fail(h, DPINN_ERR_STATE, "query work-item scratch too small");
   dk::Route rt{};
   for (int a = 0; a < h->din; ++a) {
     rt.lo[a] = (float)h->cfg.lo[a];
@@ -636,16 +649,37 @@ int enqueue_query(dpinn* h, const QueryScratch& q, const float* pts, int64_t n, 
   b.q_pts = pts;
   b.q_perm = q.perm;
   b.q_out = out;
-  b.q_w = h->dout + (want_residual ? h->ds + 1 : 0);
-  const void* fn = want_residual ? h->ks.query_jet_run : h->ks.query_val_run;
-  const size_t smem = want_residual ? h->ks.smem_qjet : h->ks.smem_qval;
-  const int threads = want_residual ? h->ks.threads_qjet : h->ks.threads_qval;
+  b.q_jets = mode == Q_JETS ? 1 : 0;
+  b.q_w = mode == Q_JETS ? h->dout * (h->din + 2) : h->dout + (mode == Q_RESIDUAL ? h->ds + 1 : 0);
+  const bool jet = mode != Q_VALUES;
+  const void* fn = jet ? h->ks.query_jet_run : h->ks.query_val_run;
+  const size_t smem = jet ? h->ks.smem_qjet : h->ks.smem_qval;
+  const int threads = jet ? h->ks.threads_qjet : h->ks.threads_qval;
   // One CTA per work item rather than a persistent grid: CTAs retire as their
   // items finish, so the block scheduler can interleave the kernels of other
   // (higher-priority) streams with a large query.
   const int grid = (int)std::min<size_t>(max_items, (size_t)1 << 30);
   CK(h, launch_pinn(fn, grid, smem, h->shape, b, q.items, q.nitems, s, threads));
   return DPINN_OK;
+}
+
+// dpinn_query / dpinn_query_jets: routing scratch owned by the handle, grown
+// to the largest request so far.
+int handle_query(dpinn* h, const float* pts, int64_t n, int mode, float* out, cudaStream_t s) {
+  if (n < 0 || n > ((int64_t)1 << 30)) return fail(h, DPINN_ERR_INVALID_ARG, "bad point count");
+  if (n == 0) return DPINN_OK;
+  if (!pts || !out) return fail(h, DPINN_ERR_INVALID_ARG, "null pointer");
+  const size_t max_items = query_max_items(h, n, mode);
+  CK(h, h->q_net.ensure(n));
+  CK(h, h->q_perm.ensure(n));
+  CK(h, h->q_counts.ensure(h->n_nets));
+  CK(h, h->q_off.ensure(h->n_nets));
+  CK(h, h->q_cursor.ensure(h->n_nets));
+  CK(h, h->q_nitems.ensure(2));
+  CK(h, h->q_items.ensure(max_items));
+  QueryScratch qs{h->q_net.p, h->q_perm.p, h->q_counts.p, h->q_off.p, h->q_cursor.p, h->q_nitems.p,
+                  h->q_items.p, h->err_d.p, max_items};
+  return enqueue_query(h, qs, pts, n, mode, out, s);
 }
 
 }  // namespace
@@ -655,6 +689,7 @@ int enqueue_query(dpinn* h, const QueryScratch& q, const float* pts, int64_t n, 
 struct dpinn_qctx {
   dpinn* h = nullptr;
   int64_t cap = 0;
+  size_t items_cap = 0;
   DevBuf<int> net_of, perm, counts, offsets, cursor, nitems, err;
   DevBuf<dk::Item> items;
   ~dpinn_qctx() {
@@ -1335,21 +1370,12 @@ int dpinn_apply_grad(dpinn_t* h, const float* host_grad) {
 
 int dpinn_query(dpinn_t* h, const float* pts, int64_t n, int want_residual, float* out, dpinn_stream_t stream) {
   if (!h) return DPINN_ERR_INVALID_ARG;
-  if (n < 0 || n > ((int64_t)1 << 30)) return fail(h, DPINN_ERR_INVALID_ARG, "bad point count");
-  if (n == 0) return DPINN_OK;
-  if (!pts || !out) return fail(h, DPINN_ERR_INVALID_ARG, "null pointer");
-  const int P = want_residual ? h->ks.P_qjet : h->ks.P_qval;
-  const size_t max_items = (size_t)(n / (4 * P)) + h->n_nets + 1;
-  CK(h, h->q_net.ensure(n));
-  CK(h, h->q_perm.ensure(n));
-  CK(h, h->q_counts.ensure(h->n_nets));
-  CK(h, h->q_off.ensure(h->n_nets));
-  CK(h, h->q_cursor.ensure(h->n_nets));
-  CK(h, h->q_nitems.ensure(2));
-  CK(h, h->q_items.ensure(max_items));
-  QueryScratch qs{h->q_net.p, h->q_perm.p, h->q_counts.p, h->q_off.p, h->q_cursor.p, h->q_nitems.p,
-                  h->q_items.p, h->err_d.p};
-  return enqueue_query(h, qs, pts, n, want_residual, out, (cudaStream_t)stream);
+  return handle_query(h, pts, n, want_residual ? Q_RESIDUAL : Q_VALUES, out, (cudaStream_t)stream);
+}
+
+int dpinn_query_jets(dpinn_t* h, const float* pts, int64_t n, float* out, dpinn_stream_t stream) {
+  if (!h) return DPINN_ERR_INVALID_ARG;
+  return handle_query(h, pts, n, Q_JETS, out, (cudaStream_t)stream);
 }
 
 }  // extern "C"
@@ -1375,7 +1401,9 @@ constexpr size_t QS_BYTES = QS_OFF_ITEMS + (size_t)QS_MAX_ITEMS * sizeof(dk::Ite
 static __device__ __align__(256) unsigned char g_query_scratch[QS_BYTES];
 
 // Device address of g_query_scratch per device ordinal, looked up once per
-// device (the symbol's host-side name is not a device address).
+// device (the symbol's host-side name is not a device address).  The cache
+// lives as long as the process; it does not survive a device reset or a
+// teardown of the device's primary context (nor does the library's module).
 std::mutex g_qs_mu;
 void* g_qs_addr[256] = {nullptr};
 
@@ -1408,51 +1436,22 @@ int dpinn_query_static(dpinn_t* h, const float* pts, int64_t n, int want_residua
     return fail(h, DPINN_ERR_INVALID_ARG, "dpinn_query_static serves ensembles of at most 4096 nets");
   if (n == 0) return DPINN_OK;
   if (!pts || !out) return fail(h, DPINN_ERR_INVALID_ARG, "null pointer");
+  const int mode = want_residual ? Q_RESIDUAL : Q_VALUES;
+  // every work item must fit the fixed array (holds while query tiles have
+  // at least 16 points); refused before anything is launched
+  if (query_max_items(h, n, mode) > (size_t)QS_MAX_ITEMS)
+    return fail(h, DPINN_ERR_STATE, "dpinn_query_static: work items exceed the fixed array");
   void* base = nullptr;
   int rc = query_scratch_address(h, &base);
   if (rc) return rc;
   char* sb = static_cast<char*>(base);
-  int* net_of = reinterpret_cast<int*>(sb + QS_OFF_NET);
-  int* perm = reinterpret_cast<int*>(sb + QS_OFF_PERM);
-  int* counts = reinterpret_cast<int*>(sb + QS_OFF_COUNTS);
-  int* offsets = reinterpret_cast<int*>(sb + QS_OFF_OFFSETS);
-  int* cursor = reinterpret_cast<int*>(sb + QS_OFF_CURSOR);
-  int* nitems = reinterpret_cast<int*>(sb + QS_OFF_NITEMS);
-  dk::Item* items = reinterpret_cast<dk::Item*>(sb + QS_OFF_ITEMS);
-  cudaStream_t s = (cudaStream_t)stream;
-  const int P = want_residual ? h->ks.P_qjet : h->ks.P_qval;
-  const int chunk = 4 * P;   // >= 64, so at most QS_MAX_ITEMS items
-  const size_t max_items = (size_t)(n / chunk) + h->n_nets + 1;
-  dk::Route rt{};
-  for (int a = 0; a < h->din; ++a) {
-    rt.lo[a] = (float)h->cfg.lo[a];
-    rt.hi[a] = (float)h->cfg.hi[a];
-    rt.inv_h[a] = (float)((double)h->cfg.splits[a] / (h->cfg.hi[a] - h->cfg.lo[a]));
-    rt.splits[a] = h->cfg.splits[a];
-    rt.stride[a] = h->stride[a];
-  }
-  rt.din = h->din;
-  rt.n_nets = h->n_nets;
-  // the array keeps the previous call's contents: clear the counters
-  CK(h, cudaMemsetAsync(counts, 0, h->n_nets * sizeof(int), s));
-  CK(h, cudaMemsetAsync(nitems, 0, 2 * sizeof(int), s));
-  const int nb = (int)((n + 255) / 256);
-  dk::k_route<<<nb, 256, 0, s>>>(rt, pts, n, net_of, counts, h->err_d.p);
-  dk::k_route_plan<<<1, 32, 0, s>>>(counts, h->n_nets, chunk, offsets, cursor, items, nitems);
-  dk::k_route_scatter<<<nb, 256, 0, s>>>(net_of, n, cursor, perm);
-  CK(h, cudaGetLastError());
-  dk::Bufs b = make_bufs(h);
-  b.counter = nitems + 1;
-  b.q_pts = pts;
-  b.q_perm = perm;
-  b.q_out = out;
-  b.q_w = h->dout + (want_residual ? h->ds + 1 : 0);
-  const void* fn = want_residual ? h->ks.query_jet_run : h->ks.query_val_run;
-  const size_t smem = want_residual ? h->ks.smem_qjet : h->ks.smem_qval;
-  const int threads = want_residual ? h->ks.threads_qjet : h->ks.threads_qval;
-  const int grid = (int)std::min<size_t>(max_items, (size_t)h->n_sms * occupancy(fn, smem, threads));
-  CK(h, launch_pinn(fn, grid, smem, h->shape, b, items, nitems, s, threads));
-  return DPINN_OK;
+  // the array keeps the previous call's contents; enqueue_query clears the
+  // counters it accumulates into (per-net counts, item count) on the stream
+  QueryScratch qs{reinterpret_cast<int*>(sb + QS_OFF_NET),     reinterpret_cast<int*>(sb + QS_OFF_PERM),
+                  reinterpret_cast<int*>(sb + QS_OFF_COUNTS),  reinterpret_cast<int*>(sb + QS_OFF_OFFSETS),
+                  reinterpret_cast<int*>(sb + QS_OFF_CURSOR),  reinterpret_cast<int*>(sb + QS_OFF_NITEMS),
+                  reinterpret_cast<dk::Item*>(sb + QS_OFF_ITEMS), h->err_d.p, (size_t)QS_MAX_ITEMS};
+  return enqueue_query(h, qs, pts, n, mode, out, (cudaStream_t)stream);
 }
 
 int dpinn_qctx_create(dpinn_t* h, int64_t max_points, dpinn_qctx_t** out) {
@@ -1470,7 +1469,8 @@ int dpinn_qctx_create(dpinn_t* h, int64_t max_points, dpinn_qctx_t** out) {
   CK(h, q->cursor.ensure(h->n_nets));
   CK(h, q->nitems.ensure(2));
   CK(h, q->err.ensure(4));
-  CK(h, q->items.ensure((size_t)(max_points / (4 * Pmin)) + h->n_nets + 1));
+  q->items_cap = (size_t)(max_points / (4 * Pmin)) + h->n_nets + 1;
+  CK(h, q->items.ensure(q->items_cap));
   CK(h, cudaMemset(q->err.p, 0, 4 * sizeof(int)));
   *out = q.release();
   return DPINN_OK;
@@ -1491,8 +1491,8 @@ int dpinn_qctx_query(dpinn_qctx_t* q, const float* pts, int64_t n, int want_resi
   if (n == 0) return DPINN_OK;
   if (!pts || !out) return fail(h, DPINN_ERR_INVALID_ARG, "null pointer");
   QueryScratch qs{q->net_of.p, q->perm.p, q->counts.p, q->offsets.p, q->cursor.p, q->nitems.p, q->items.p,
-                  q->err.p};
-  return enqueue_query(h, qs, pts, n, want_residual, out, (cudaStream_t)stream);
+                  q->err.p, q->items_cap};
+  return enqueue_query(h, qs, pts, n, want_residual ? Q_RESIDUAL : Q_VALUES, out, (cudaStream_t)stream);
 }
 
 int dpinn_qctx_status(dpinn_qctx_t* q, dpinn_stream_t stream) {

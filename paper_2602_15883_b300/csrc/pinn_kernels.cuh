@@ -92,6 +92,7 @@ struct Bufs {
   const int* q_perm;       // query segment order -> point index
   float* q_out;            // query output rows
   int q_w;                 // query row width
+  int q_jets;              // jet queries: rows are the raw output jets [DOUT][C] (no residual, no anchoring)
 };
 
 // ------------------------------------------------------------ tiling ---
@@ -560,7 +561,12 @@ __device__ __forceinline__ void point_epilogue(const Shape& sh, const Bufs& b, c
   } else {   // M_QUERY
     if (valid) {
       float* o = b.q_out + (size_t)b.q_perm[item.begin + sub + p] * b.q_w;
-      if (pass == 0) {
+      if (JETS && b.q_jets) {   // the net's own output jets, row [j][c] (one pass)
+#pragma unroll
+        for (int j = 0; j < DOUT; ++j)
+#pragma unroll
+          for (int c = 0; c < C; ++c) o[j * C + c] = Y[j][c];
+      } else if (pass == 0) {
 #pragma unroll
         for (int j = 0; j < DS; ++j) o[j] = Y[j][0];
         if (npass == 1) o[DS] = Y[DS][0] + sh.p_ref;
@@ -716,7 +722,7 @@ __global__ void __launch_bounds__(NT, 1)
       }
     }
     double lsum0 = 0.0, lsum1 = 0.0, lsum2 = 0.0, lsum3 = 0.0;   // thread 0: loss numerators of this item
-    const int npass = (MODE == M_QUERY && ni.master) ? 2 : 1;
+    const int npass = (MODE == M_QUERY && ni.master && !b.q_jets) ? 2 : 1;
 
     for (int sub = 0; sub < item.count; sub += P) {
       const int npts = min(P, item.count - sub);

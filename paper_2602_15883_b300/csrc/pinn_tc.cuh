@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(NTC, 1)
     if (t < DOUT) bLs[t] = th[sh.boff[L] + t];
     if (t < 4) s_scale[t] = t < DIN ? ni.scale[t] : 0.f;
     double lsum0 = 0.0;   // thread 0: sum of r^2 over the item
-    const int npass = (!TRAIN && ni.master) ? 2 : 1;
+    const int npass = (!TRAIN && ni.master && !b.q_jets) ? 2 : 1;
 
     for (int sub = 0; sub < item.count; sub += P) {
       const int npts = min(P, item.count - sub);
@@ -469,7 +469,12 @@ __global__ void __launch_bounds__(NTC, 1)
 #pragma unroll
             for (int c = 0; c < C; ++c) Y[j][c] = ysm[j * NC + t * C + c];
           float* o = b.q_out + (size_t)b.q_perm[item.begin + sub + t] * b.q_w;
-          if (pass == 0) {
+          if (b.q_jets) {   // the net's own output jets, row [j][c] (one pass)
+#pragma unroll
+            for (int j = 0; j < DOUT; ++j)
+#pragma unroll
+              for (int c = 0; c < C; ++c) o[j * C + c] = Y[j][c];
+          } else if (pass == 0) {
 #pragma unroll
             for (int j = 0; j < DS; ++j) o[j] = Y[j][0];
             if (npass == 1) o[DS] = Y[DS][0] + sh.p_ref;

@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(NTW, 1)
       }
     }
     double lsum0 = 0.0, lsum1 = 0.0, lsum2 = 0.0, lsum3 = 0.0;
-    const int npass = (MODE == M_QUERY && ni.master) ? 2 : 1;
+    const int npass = (MODE == M_QUERY && ni.master && !b.q_jets) ? 2 : 1;
 
     for (int sub = 0; sub < item.count; sub += P) {
       const int npts = min(P, item.count - sub);

@@ -88,3 +88,49 @@ def query_jets(ora, th, pts, nets):
         sel = nets == k
         out[sel] = ora.forward(int(k), th[k * npar:(k + 1) * npar], pts[sel].astype(np.float64))
     return out
+
+
+def adam_step_bound(beta1, beta2, t):
+    """Largest |m_hat_t| / sqrt(v_hat_t) of Adam over all gradient histories
+    of length t (Cauchy-Schwarz on the two exponentially weighted sums):
+    sqrt(sum_k a_k^2 / b_k) with a_k, b_k the bias-corrected weights of g_k in
+    m_hat and of g_k^2 in v_hat.  One Adam update moves an element by at most
+    lr times this, whatever its gradients."""
+    k = np.arange(1, t + 1)
+    a = (1 - beta1) * beta1 ** (t - k) / (1 - beta1 ** t)
+    b = (1 - beta2) * beta2 ** (t - k) / (1 - beta2 ** t)
+    return float(np.sqrt(np.sum(a * a / b)))
+
+
+def free_run_envelope(cfg, steps):
+    """Bound on |theta_gpu - theta_oracle| per element after `steps` steps
+    of two independently integrated trajectories from the same start: each
+    step moves each side by at most lr * adam_step_bound (decayed lr is
+    smaller), so the two can differ by at most twice the sum.  Elements whose
+    gradient lies within FP32 rounding of zero can take such steps with
+    opposite signs on the two sides; this is the envelope, not an error."""
+    b1, b2, lr = cfg.get("beta1", 0.9), cfg.get("beta2", 0.999), cfg.get("lr", 1e-3)
+    return 2.0 * lr * sum(adam_step_bound(b1, b2, t) for t in range(1, steps + 1)) * 1.0001 + 1e-6
+
+
+def step_against_oracle(d, ora_step, loss_tol=1e-5, param_tol=1e-5):
+    """One training step on the GPU handle `d`, compared with the oracle's
+    step taken from the GPU's own pre-step state (parameters, Adam moments,
+    step count): the loss record at `loss_tol` per term (relative L2 over
+    nets) and the parameters after the update at `param_tol` (relative L2).
+    `ora_step(th, m, v, t)` returns (th, m, v, t, loss) as Oracle.step does.
+    Returns the GPU loss record."""
+    th, m, v, t = d.get_state()
+    d.step(1)
+    loss = d.loss()
+    th1, _, _, t1 = d.get_state()
+    oth, _, _, ot, oloss = ora_step(th.astype(np.float64), m.astype(np.float64), v.astype(np.float64), t)
+    assert t1 == ot == t + 1
+    for q in range(6):
+        r = oloss[:, q]
+        if np.linalg.norm(r) == 0:
+            assert np.all(loss[:, q] == 0), q
+        else:
+            assert rel_l2(loss[:, q], r) <= loss_tol, (t, q, rel_l2(loss[:, q], r))
+    assert rel_l2(th1, oth) <= param_tol, (t, rel_l2(th1, oth))
+    return loss

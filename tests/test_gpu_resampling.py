@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 from paper_2602_15883_b300 import synth
-from tests.helpers import rel_l2
+from tests.helpers import free_run_envelope, rel_l2, step_against_oracle
 from tests.test_gpu_parity import GRAD_TOL, _gpu, compare_losses, small_case
 
 pytestmark = pytest.mark.gpu
@@ -80,18 +80,10 @@ def test_training_steps_on_fresh_points_track_the_oracle():
     seed = 5
     d.set_resampling(counts, seed)
     ora = oracle.Oracle(cfg)
-    th = np.asarray(pb.theta0, np.float64)
-    m = np.zeros_like(th)
-    v = np.zeros_like(th)
-    t = 0
     for s in range(4):
-        d.step(1)
-        loss = d.loss()
         ora.set_problem(dataclasses.replace(pb, res_pts=ora.sample(seed, s, counts),
                                             res_counts=np.asarray(counts, np.int64)))
-        th, m, v, t, oloss = ora.step(th, m, v, t)
-        compare_losses(loss, oloss, tol=1e-4)
-    assert rel_l2(d.get_state()[0], th) < 1e-4
+        step_against_oracle(d, ora.step)
 
 
 def test_switching_off_keeps_the_last_points_and_set_points_takes_over():
