@@ -326,6 +326,7 @@ def serving_leg(seconds=5.0, rate=200.0, train_steps=20, seed=0, precision="tf32
             r.done.wait()
         del warm, r
         poisson_load(srv, cfg, rate_hz=20.0, duration_s=0.5, seed=seed + 1)
+        half = poisson_load(srv, cfg, rate_hz=rate / 2, duration_s=seconds, seed=seed + 3, client_buffers=True)
         reqs = poisson_load(srv, cfg, rate_hz=rate, duration_s=seconds, seed=seed + 2, client_buffers=True)
     finally:
         srv.stop()
@@ -333,8 +334,13 @@ def serving_leg(seconds=5.0, rate=200.0, train_steps=20, seed=0, precision="tf32
     out.update({"workload": "beltrami32 ensemble (32 nets of 8x128) after %d training steps" % train_steps,
                 "arrivals": f"Poisson {rate:g} req/s for {seconds:g} s", "points_per_request": "log-uniform 1e3..1e6",
                 "residual_fraction": 0.1, "mem_cap_gb": 8, "slots": 4, "precision": precision,
+                "slot_points": srv.max_points, "device_bytes": srv.device_bytes,
                 "max_concurrent_batches": srv.max_concurrent,
                 "offered_points_per_s": sum(r.n for r in reqs) / seconds})
+    h = latency_summary(half)
+    h.update({"arrivals": f"Poisson {rate / 2:g} req/s for {seconds:g} s",
+              "offered_points_per_s": sum(r.n for r in half) / seconds})
+    out["at_half_load"] = h
     d.close()
     return out
 
@@ -348,16 +354,28 @@ def measure(args, workload, precision, rank, world, local, dist, stream, clocks=
     cfg = synth.config(workload)
     pb = synth.make_problem(cfg, seed=args.seed + rank)
     cfg["device"] = local
-    cfg["precision"] = PRECISIONS[precision]
+    auto = precision == "auto"   # the autotuner picks the arithmetic (width 128: FP32 or 3xTF32)
+    if auto and cfg["width"] != 128:
+        precision, auto = "fp32", False
+    cfg["precision"] = 0 if auto else PRECISIONS[precision]
     d = Dpinn(cfg)
     d.set_problem(pb)
     schedule = {"jet_tiles": 0, "val_tiles": 0, "order": 0, "tuned": False}
     if not args.no_autotune:
         from paper_2602_15883_b300 import autotune
         n_val = int(pb.obs_counts.sum() + 2 * pb.face_counts.sum())
-        res = autotune.autotune(d, pb.n_res, n_val, reps=3)
+        res = autotune.autotune(d, pb.n_res, n_val, reps=3, precisions=(0, 1) if auto else None)
         schedule = {k: res[k] for k in ("jet_tiles", "val_tiles", "order")}
-        schedule.update(tuned=True, cached=res.get("cached", False))
+        schedule.update(tuned=True, cached=res.get("cached", False), trials=res.get("trials"),
+                        jet_tile_options=d.tile_options()[0], val_tile_options=d.tile_options()[1])
+        if auto:
+            schedule["variant_ms"] = {("tf32x3" if k == "1" else "fp32"): v
+                                      for k, v in res.get("precision_ms", {}).items()}
+    elif auto:
+        d.set_precision(1)
+    precision = "tf32x3" if d.get_precision() == 1 else "fp32"
+    cfg["precision"] = PRECISIONS[precision]
+    schedule["variant"] = precision + (" (autotuned)" if auto and not args.no_autotune else "")
     schedule["tile_points"] = d.get_schedule()["tile_points"]
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     d.step(args.warmup, stream)
@@ -531,8 +549,12 @@ def main():
     if not args.no_extras:
         # the other arithmetic of the width-128 kernels, and the 32-net TGV workload
         if width == 128:
-            other = "tf32x3" if args.precision == "fp32" else "fp32"
-            extras[other] = measure(args, args.workload, other, rank, world, local, dist, stream, clocks=False)[2]
+            # the autotuner's choice between the two kernel families (3xTF32
+            # measured faster); reported under the variant it picked
+            r = measure(args, args.workload, "auto", rank, world, local, dist, stream, clocks=False)[2]
+            key = "tf32x3" if r["dtype"] == "tf32x3" else "autotuned_f32"
+            if key != head["dtype"]:
+                extras[key] = r
         if args.workload != "tgv":
             extras["tgv"] = measure(args, "tgv", "fp32", rank, world, local, dist, stream, clocks=False)[2]
 

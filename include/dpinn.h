@@ -317,8 +317,9 @@ int dpinn_query_jets(dpinn_t* h, const float* dev_pts, int64_t n, float* dev_out
 
 /* Query contexts: dpinn_query shares one scratch per handle, so two of its
  * calls must not overlap on the GPU.  A context owns its own routing scratch
- * for up to max_points points per call (allocated once, here) and its own
- * error words, so queries through different contexts may run concurrently
+ * for up to max_points points per call (one device allocation made here, of
+ * about 8.5 bytes per point plus 44 bytes per net) and its own error words,
+ * so queries through different contexts may run concurrently
  * on different streams (the serving loop keeps one per in-flight batch).
  * dpinn_qctx_query: as dpinn_query (device pointers, asynchronous on
  * `stream`); n > max_points is INVALID_ARG.  dpinn_qctx_status: synchronise
@@ -379,6 +380,30 @@ int dpinn_apply_grad(dpinn_t* h, const float* host_grad);
  * the schedule beyond float rounding of the gradient sums (each schedule is
  * itself deterministic).  Used by the autotuner. */
 int dpinn_set_schedule(dpinn_t* h, int jet_tiles, int val_tiles, int order);
+/* Switch the arithmetic of the hidden-layer contractions (DPINN_PREC_FP32 or
+ * DPINN_PREC_TF32X3, the latter for width 128 only) on a live handle: the
+ * step, the value items and the queries then launch the other kernel family
+ * (the same work, Eqs. (2)-(16) and Algorithm 1; both meet the same error
+ * bounds against FP64).  Parameters, Adam moments, step count and points are
+ * kept; the work lists and the captured step are rebuilt for the new kernels'
+ * tiles.  Synchronises the device.  Used by the autotuner, which times both
+ * and keeps the faster.  Errors: INVALID_ARG (unknown precision, TF32X3 at
+ * another width), CUDA, OOM.  dpinn_get_precision reports the current one. */
+int dpinn_set_precision(dpinn_t* h, int precision);
+int dpinn_get_precision(dpinn_t* h, int* precision);
+
+/* Point tiles of the grouped kernels.  dpinn_tile_options lists the tile
+ * sizes (points per tile) available for the jet training kernel and for the
+ * value kernels (observation / ghost training and the exchange) of the
+ * current precision, default first: up to 2 each (the FP32 kernels are
+ * instantiated with a default and an alternate register tile; the
+ * tensor-core kernels have one).  dpinn_set_tiles selects them (0 = the
+ * default); the work lists and the captured step are rebuilt, results are
+ * the same up to float rounding of the gradient sums.  Used by the
+ * autotuner.  Errors: INVALID_ARG (a size not offered), CUDA, OOM. */
+int dpinn_tile_options(dpinn_t* h, int* jet_points, int* n_jet, int* val_points, int* n_val);
+int dpinn_set_tiles(dpinn_t* h, int jet_points, int val_points);
+
 /* Current schedule and the tile sizes (points) of the jet and value kernels
  * (tile_points[2]). */
 int dpinn_get_schedule(dpinn_t* h, int* jet_tiles, int* val_tiles, int* order, int* tile_points);

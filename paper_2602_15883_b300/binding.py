@@ -31,7 +31,7 @@ EXPORTS = (
     "dpinn_qctx_create", "dpinn_qctx_destroy", "dpinn_qctx_query", "dpinn_qctx_status",
     "dpinn_set_resampling", "dpinn_get_points", "dpinn_set_partial_budget", "dpinn_loss_ext",
     "dpinn_set_points_async", "dpinn_selftest_wait", "dpinn_loss_async", "dpinn_probe_fp32",
-    "dpinn_query_jets",
+    "dpinn_query_jets", "dpinn_set_precision", "dpinn_get_precision", "dpinn_tile_options", "dpinn_set_tiles",
 )
 
 
@@ -90,6 +90,10 @@ def load_library(path: str = LIB_PATH):
         "dpinn_get_grad": ([vp, vp], i32),
         "dpinn_query": ([vp, vp, i64, i32, vp, vp], i32),
         "dpinn_query_jets": ([vp, vp, i64, vp, vp], i32),
+        "dpinn_set_precision": ([vp, i32], i32),
+        "dpinn_get_precision": ([vp, vp], i32),
+        "dpinn_tile_options": ([vp, vp, vp, vp, vp], i32),
+        "dpinn_set_tiles": ([vp, i32, i32], i32),
         "dpinn_query_status": ([vp, vp], i32),
         "dpinn_get_state": ([vp, vp, vp, vp, vp], i32),
         "dpinn_set_state": ([vp, vp, vp, vp, i64], i32),
@@ -378,6 +382,26 @@ class Dpinn:
 
     def set_schedule(self, jet_tiles=0, val_tiles=0, order=0):
         self._check(self.lib.dpinn_set_schedule(self.h, int(jet_tiles), int(val_tiles), int(order)))
+
+    def set_precision(self, precision):
+        """Switch the contraction arithmetic (0 FP32, 1 TF32x3 at width 128)."""
+        self._check(self.lib.dpinn_set_precision(self.h, int(precision)))
+        self.cfg = dict(self.cfg, precision=int(precision))
+
+    def tile_options(self):
+        """(jet tile sizes, value tile sizes) in points, default first."""
+        jo, vo = (C.c_int * 2)(), (C.c_int * 2)()
+        nj, nv = C.c_int(), C.c_int()
+        self._check(self.lib.dpinn_tile_options(self.h, jo, C.addressof(nj), vo, C.addressof(nv)))
+        return list(jo[:nj.value]), list(vo[:nv.value])
+
+    def set_tiles(self, jet_points=0, val_points=0):
+        self._check(self.lib.dpinn_set_tiles(self.h, int(jet_points), int(val_points)))
+
+    def get_precision(self):
+        p = C.c_int()
+        self._check(self.lib.dpinn_get_precision(self.h, C.addressof(p)))
+        return p.value
 
     def get_schedule(self):
         v = [C.c_int() for _ in range(3)]

@@ -80,6 +80,7 @@ struct dpinn {
   dk::Shape shape{};
   KernelSet ks;
   int dev = 0, n_sms = 0;
+  int tile_jet = 0, tile_val = 0;   // FP32 point tiles: 0 default, 1 alternate
   std::string err;
 
   // parameters and optimiser state
@@ -393,6 +394,72 @@ int capture(dpinn* h, int mode, cudaGraphExec_t* out) {
   return DPINN_OK;
 }
 
+// The kernels the step, the value items and the queries launch for an
+// arithmetic (precision): the FP32 kernels, or at width 128 the tcgen05
+// 3xTF32 ones, with their launch shapes and shared memory.
+int select_kernels(dpinn* h, int precision) {
+  if (precision == DPINN_PREC_TF32X3) {
+    h->ks.train_jet_run = h->ks.train_jet_tc;
+    h->ks.threads_train_jet = h->ks.threads_tc;
+    h->ks.smem_train_jet = h->ks.smem_tc;
+    h->ks.P_train_jet = h->ks.P_tc;
+    h->ks.stash_train_jet = h->ks.stash_tc;
+    h->ks.train_val_run = h->ks.train_val_tc;
+    h->ks.eval_val_run = h->ks.eval_val_tc;
+    h->ks.threads_val_run = h->ks.threads_tcv;
+    h->ks.smem_val_run = h->ks.smem_tcv;
+    h->ks.P_val_run = h->ks.P_tcv;
+    h->ks.stash_val_run = h->ks.stash_tcv;
+    h->ks.query_val_run = h->ks.query_val_tc;
+    h->ks.query_jet_run = h->ks.query_jet_tc;
+    h->ks.threads_qval = h->ks.threads_qjet = h->ks.threads_tcv;
+    h->ks.P_qval = h->ks.P_tcv;
+    h->ks.P_qjet = h->ks.P_tc;
+    h->ks.smem_qval = h->ks.smem_tcv;
+    h->ks.smem_qjet = h->ks.smem_tc;
+  } else {
+    // FP32: the default point tiles or, when selected and instantiated, the
+    // alternate ones (dpinn_set_tiles)
+    const bool aj = h->tile_jet != 0 && h->ks.train_jet_alt;
+    const bool av = h->tile_val != 0 && h->ks.train_val_alt;
+    h->ks.train_jet_run = aj ? h->ks.train_jet_alt : h->ks.train_jet;
+    h->ks.threads_train_jet = dk::NT;
+    h->ks.smem_train_jet = aj ? h->ks.smem_jet_alt : h->ks.smem_jet;
+    h->ks.P_train_jet = aj ? h->ks.P_jet_alt : h->ks.P_jet;
+    h->ks.stash_train_jet = aj ? h->ks.stash_jet_alt : h->ks.stash_jet;
+    h->ks.train_val_run = av ? h->ks.train_val_alt : h->ks.train_val;
+    h->ks.eval_val_run = av ? h->ks.eval_val_alt : h->ks.eval_val;
+    h->ks.threads_val_run = dk::NT;
+    h->ks.smem_val_run = av ? h->ks.smem_val_alt : h->ks.smem_val;
+    h->ks.P_val_run = av ? h->ks.P_val_alt : h->ks.P_val;
+    h->ks.stash_val_run = av ? h->ks.stash_val_alt : h->ks.stash_val;
+    h->ks.query_val_run = h->ks.query_val;
+    h->ks.query_jet_run = h->ks.query_jet;
+    h->ks.threads_qval = h->ks.threads_qjet = dk::NT;
+    h->ks.P_qval = h->ks.P_val;
+    h->ks.P_qjet = h->ks.P_jet;
+    h->ks.smem_qval = h->ks.smem_val;
+    h->ks.smem_qjet = h->ks.smem_jet;
+  }
+  if (h->dev >= 0) {   // after creation: the chosen kernels' shared-memory limits
+    if (h->ks.train_val_run != h->ks.train_val) {
+      CK(h, cudaFuncSetAttribute(h->ks.query_val_run, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)h->ks.smem_qval));
+      CK(h, cudaFuncSetAttribute(h->ks.query_jet_run, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)h->ks.smem_qjet));
+      CK(h, cudaFuncSetAttribute(h->ks.train_val_run, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)h->ks.smem_val_run));
+      CK(h, cudaFuncSetAttribute(h->ks.eval_val_run, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)h->ks.smem_val_run));
+    }
+    if (h->ks.train_jet_run != h->ks.train_jet)
+      CK(h, cudaFuncSetAttribute(h->ks.train_jet_run, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)h->ks.smem_train_jet));
+  }
+  h->cfg.precision = precision;
+  return DPINN_OK;
+}
+
 int build_plan(dpinn* h) {
   h->plan_ok = false;
   if (!(h->have[0] && h->have[1] && (h->have[2] || h->n_faces == 0)))
@@ -686,16 +753,18 @@ int handle_query(dpinn* h, const float* pts, int64_t n, int mode, float* out, cu
 
 // Query context: its own scratch (sized once at creation) and error words, so
 // that queries on several streams can be in flight together.
+// All of a context's device scratch is one allocation (its parts 256-byte
+// aligned), so that a caller budgeting device memory (the serving loop) pays
+// the allocator's rounding once per context.
 struct dpinn_qctx {
   dpinn* h = nullptr;
   int64_t cap = 0;
   size_t items_cap = 0;
-  DevBuf<int> net_of, perm, counts, offsets, cursor, nitems, err;
-  DevBuf<dk::Item> items;
-  ~dpinn_qctx() {
-    for (auto* b : {&net_of, &perm, &counts, &offsets, &cursor, &nitems, &err}) b->free_();
-    items.free_();
-  }
+  DevBuf<unsigned char> mem;
+  int *net_of = nullptr, *perm = nullptr, *counts = nullptr, *offsets = nullptr, *cursor = nullptr,
+      *nitems = nullptr, *err = nullptr;
+  dk::Item* items = nullptr;
+  ~dpinn_qctx() { mem.free_(); }
 };
 
 // =================================================================== ABI ===
@@ -762,45 +831,8 @@ int dpinn_create(const dpinn_config* cfg, dpinn_t** out) {
   h->n_nets = (int)nn;
   if (!pick_kernels(h->W, h->ds, h->unst, h->L, c.activation, &h->ks))
     return fail(nullptr, DPINN_ERR_INVALID_ARG, "unsupported shape");
-  if (c.precision == DPINN_PREC_TF32X3) {
-    h->ks.train_jet_run = h->ks.train_jet_tc;
-    h->ks.threads_train_jet = h->ks.threads_tc;
-    h->ks.smem_train_jet = h->ks.smem_tc;
-    h->ks.P_train_jet = h->ks.P_tc;
-    h->ks.stash_train_jet = h->ks.stash_tc;
-    h->ks.train_val_run = h->ks.train_val_tc;
-    h->ks.eval_val_run = h->ks.eval_val_tc;
-    h->ks.threads_val_run = h->ks.threads_tcv;
-    h->ks.smem_val_run = h->ks.smem_tcv;
-    h->ks.P_val_run = h->ks.P_tcv;
-    h->ks.stash_val_run = h->ks.stash_tcv;
-    h->ks.query_val_run = h->ks.query_val_tc;
-    h->ks.query_jet_run = h->ks.query_jet_tc;
-    h->ks.threads_qval = h->ks.threads_qjet = h->ks.threads_tcv;
-    h->ks.P_qval = h->ks.P_tcv;
-    h->ks.P_qjet = h->ks.P_tc;
-    h->ks.smem_qval = h->ks.smem_tcv;
-    h->ks.smem_qjet = h->ks.smem_tc;
-  } else {
-    h->ks.train_jet_run = h->ks.train_jet;
-    h->ks.threads_train_jet = dk::NT;
-    h->ks.smem_train_jet = h->ks.smem_jet;
-    h->ks.P_train_jet = h->ks.P_jet;
-    h->ks.stash_train_jet = h->ks.stash_jet;
-    h->ks.train_val_run = h->ks.train_val;
-    h->ks.eval_val_run = h->ks.eval_val;
-    h->ks.threads_val_run = dk::NT;
-    h->ks.smem_val_run = h->ks.smem_val;
-    h->ks.P_val_run = h->ks.P_val;
-    h->ks.stash_val_run = h->ks.stash_val;
-    h->ks.query_val_run = h->ks.query_val;
-    h->ks.query_jet_run = h->ks.query_jet;
-    h->ks.threads_qval = h->ks.threads_qjet = dk::NT;
-    h->ks.P_qval = h->ks.P_val;
-    h->ks.P_qjet = h->ks.P_jet;
-    h->ks.smem_qval = h->ks.smem_val;
-    h->ks.smem_qjet = h->ks.smem_jet;
-  }
+  h->dev = -1;
+  select_kernels(h.get(), c.precision);
   // decomposition
   int s = 1;
   for (int a = 0; a < din; ++a) { h->stride.push_back(s); s *= c.splits[a]; }
@@ -1272,6 +1304,62 @@ int dpinn_set_schedule(dpinn_t* h, int jet_tiles, int val_tiles, int order) {
   return build_plan(h);
 }
 
+int dpinn_set_precision(dpinn_t* h, int precision) {
+  if (!h) return DPINN_ERR_INVALID_ARG;
+  if (precision != DPINN_PREC_FP32 && precision != DPINN_PREC_TF32X3)
+    return fail(h, DPINN_ERR_INVALID_ARG, "precision must be FP32 or TF32x3");
+  if (precision == DPINN_PREC_TF32X3 && h->W != 128)
+    return fail(h, DPINN_ERR_INVALID_ARG, "TF32x3 tensor-core kernels need width 128");
+  if (precision == DPINN_PREC_TF32X3)
+    for (int l = 1; l < h->L; ++l)
+      if (h->shape.woff[l] % 4 != 0) return fail(h, DPINN_ERR_INVALID_ARG, "weight-gradient tile not 16-byte aligned");
+  if (precision == h->cfg.precision) return DPINN_OK;
+  CK(h, cudaDeviceSynchronize());
+  if (int rc = select_kernels(h, precision)) return rc;
+  return build_plan(h);
+}
+
+int dpinn_tile_options(dpinn_t* h, int* jet_points, int* n_jet, int* val_points, int* n_val) {
+  if (!h || !jet_points || !n_jet || !val_points || !n_val) return DPINN_ERR_INVALID_ARG;
+  if (h->cfg.precision == DPINN_PREC_TF32X3) {
+    jet_points[0] = h->ks.P_tc;
+    val_points[0] = h->ks.P_tcv;
+    *n_jet = *n_val = 1;
+    return DPINN_OK;
+  }
+  jet_points[0] = h->ks.P_jet;
+  val_points[0] = h->ks.P_val;
+  *n_jet = *n_val = 1;
+  if (h->ks.train_jet_alt) jet_points[(*n_jet)++] = h->ks.P_jet_alt;
+  if (h->ks.train_val_alt) val_points[(*n_val)++] = h->ks.P_val_alt;
+  return DPINN_OK;
+}
+
+int dpinn_set_tiles(dpinn_t* h, int jet_points, int val_points) {
+  if (!h) return DPINN_ERR_INVALID_ARG;
+  int jo[2], vo[2], nj = 0, nv = 0;
+  dpinn_tile_options(h, jo, &nj, vo, &nv);
+  int tj = -1, tv = -1;
+  for (int i = 0; i < nj; ++i)
+    if (jet_points == 0 || jet_points == jo[i]) { tj = jet_points == 0 ? 0 : i; break; }
+  for (int i = 0; i < nv; ++i)
+    if (val_points == 0 || val_points == vo[i]) { tv = val_points == 0 ? 0 : i; break; }
+  if (tj < 0 || tv < 0) return fail(h, DPINN_ERR_INVALID_ARG, "tile size not available (see dpinn_tile_options)");
+  if (h->cfg.precision == DPINN_PREC_TF32X3) return DPINN_OK;   // one tile per tensor-core kernel
+  if (tj == h->tile_jet && tv == h->tile_val) return DPINN_OK;
+  CK(h, cudaDeviceSynchronize());
+  h->tile_jet = tj;
+  h->tile_val = tv;
+  if (int rc = select_kernels(h, h->cfg.precision)) return rc;
+  return build_plan(h);
+}
+
+int dpinn_get_precision(dpinn_t* h, int* precision) {
+  if (!h || !precision) return DPINN_ERR_INVALID_ARG;
+  *precision = h->cfg.precision;
+  return DPINN_OK;
+}
+
 int dpinn_get_schedule(dpinn_t* h, int* jet_tiles, int* val_tiles, int* order, int* tile_points) {
   if (!h) return DPINN_ERR_INVALID_ARG;
   if (jet_tiles) *jet_tiles = h->sched_jet;
@@ -1462,16 +1550,24 @@ int dpinn_qctx_create(dpinn_t* h, int64_t max_points, dpinn_qctx_t** out) {
   q->h = h;
   q->cap = max_points;
   const int Pmin = std::min(h->ks.P_qjet, h->ks.P_qval);
-  CK(h, q->net_of.ensure(max_points));
-  CK(h, q->perm.ensure(max_points));
-  CK(h, q->counts.ensure(h->n_nets));
-  CK(h, q->offsets.ensure(h->n_nets));
-  CK(h, q->cursor.ensure(h->n_nets));
-  CK(h, q->nitems.ensure(2));
-  CK(h, q->err.ensure(4));
   q->items_cap = (size_t)(max_points / (4 * Pmin)) + h->n_nets + 1;
-  CK(h, q->items.ensure(q->items_cap));
-  CK(h, cudaMemset(q->err.p, 0, 4 * sizeof(int)));
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t sz[8] = {(size_t)max_points * 4, (size_t)max_points * 4, (size_t)h->n_nets * 4,
+                        (size_t)h->n_nets * 4, (size_t)h->n_nets * 4, 2 * 4, 4 * 4,
+                        q->items_cap * sizeof(dk::Item)};
+  size_t off[8], total = 0;
+  for (int i = 0; i < 8; ++i) { off[i] = total; total += up(sz[i]); }
+  CK(h, q->mem.ensure(total));
+  unsigned char* b = q->mem.p;
+  q->net_of = reinterpret_cast<int*>(b + off[0]);
+  q->perm = reinterpret_cast<int*>(b + off[1]);
+  q->counts = reinterpret_cast<int*>(b + off[2]);
+  q->offsets = reinterpret_cast<int*>(b + off[3]);
+  q->cursor = reinterpret_cast<int*>(b + off[4]);
+  q->nitems = reinterpret_cast<int*>(b + off[5]);
+  q->err = reinterpret_cast<int*>(b + off[6]);
+  q->items = reinterpret_cast<dk::Item*>(b + off[7]);
+  CK(h, cudaMemset(q->err, 0, 4 * sizeof(int)));
   *out = q.release();
   return DPINN_OK;
 }
@@ -1490,8 +1586,7 @@ int dpinn_qctx_query(dpinn_qctx_t* q, const float* pts, int64_t n, int want_resi
   if (n < 0 || n > q->cap) return fail(h, DPINN_ERR_INVALID_ARG, "more points than the context was created for");
   if (n == 0) return DPINN_OK;
   if (!pts || !out) return fail(h, DPINN_ERR_INVALID_ARG, "null pointer");
-  QueryScratch qs{q->net_of.p, q->perm.p, q->counts.p, q->offsets.p, q->cursor.p, q->nitems.p, q->items.p,
-                  q->err.p, q->items_cap};
+  QueryScratch qs{q->net_of, q->perm, q->counts, q->offsets, q->cursor, q->nitems, q->items, q->err, q->items_cap};
   return enqueue_query(h, qs, pts, n, want_residual ? Q_RESIDUAL : Q_VALUES, out, (cudaStream_t)stream);
 }
 
@@ -1500,10 +1595,10 @@ int dpinn_qctx_status(dpinn_qctx_t* q, dpinn_stream_t stream) {
   dpinn* h = q->h;
   CK(h, cudaStreamSynchronize((cudaStream_t)stream));
   int e[3] = {0, 0, 0};
-  CK(h, cudaMemcpy(e, q->err.p, sizeof(e), cudaMemcpyDeviceToHost));
+  CK(h, cudaMemcpy(e, q->err, sizeof(e), cudaMemcpyDeviceToHost));
   if (e[dk::ERR_TIMEOUT]) return fail(h, DPINN_ERR_TIMEOUT, "a device wait gave up");
   if (e[dk::ERR_DOMAIN]) {
-    CK(h, cudaMemset(q->err.p + dk::ERR_DOMAIN, 0, sizeof(int)));
+    CK(h, cudaMemset(q->err + dk::ERR_DOMAIN, 0, sizeof(int)));
     return fail(h, DPINN_ERR_INVALID_ARG, "query point outside the domain");
   }
   return DPINN_OK;

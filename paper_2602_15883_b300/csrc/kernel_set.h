@@ -16,6 +16,14 @@ struct KernelSet {
   size_t smem_jet = 0, smem_val = 0;
   int P_jet = 0, P_val = 0;
   long long stash_jet = 0, stash_val = 0;   // floats per CTA
+  // alternate point tiles of the FP32 jet training kernel and of the value
+  // training / exchange kernels (null where the family has none)
+  const void* train_jet_alt = nullptr;
+  const void* train_val_alt = nullptr;
+  const void* eval_val_alt = nullptr;
+  size_t smem_jet_alt = 0, smem_val_alt = 0;
+  int P_jet_alt = 0, P_val_alt = 0;
+  long long stash_jet_alt = 0, stash_val_alt = 0;
   // the jet training kernel actually launched (the FP32 one above, or the
   // tensor-core one below), its shared memory, tile and stash
   const void* train_jet_run = nullptr;

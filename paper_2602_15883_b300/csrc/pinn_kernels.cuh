@@ -103,14 +103,18 @@ struct Bufs {
 // thread for values: 256-point value tiles, measured 11 % faster than 128 on
 // the TGV value and exchange items); W = 128 is held to 4 neurons by the
 // shared-memory capacity of its activation buffers.
-template <int W, int C>
+// TV selects the point tile: 0 the default, 1 an alternate with fewer points
+// per thread (half the tile, or the same where the default is already one
+// point per thread); the autotuner times both.
+template <int W, int C, int TV = 0>
 struct Tile {
   static constexpr int TM = (W == 64) ? 8 : 4;    // neurons per thread
   static constexpr int NG = W / TM;               // neuron groups
   static constexpr int PG = NT / NG;              // point groups
-  static constexpr int TP = (W == 128) ? (C == 1 ? 8 : (C == 4 ? 4 : 2))
-                          : (W == 64) ? (C == 1 ? 8 : (C == 6 ? 1 : 2))
-                          : 2;                    // points per thread
+  static constexpr int TP0 = (W == 128) ? (C == 1 ? 8 : (C == 4 ? 4 : 2))
+                           : (W == 64) ? (C == 1 ? 8 : (C == 6 ? 1 : 2))
+                           : 2;
+  static constexpr int TP = (TV == 0 || TP0 == 1) ? TP0 : TP0 / 2;   // points per thread
   static constexpr int P = PG * TP;               // points per tile
   static constexpr int NCOL = TP * C;             // columns per thread
   static constexpr int PC = P * C;
@@ -137,9 +141,9 @@ struct Tile {
   static_assert(KS >= 1 && KS <= 32 && NTI * NTI * KS == NT, "weight-gradient tile");
 };
 
-template <int W, int C, int DOUT>
+template <int W, int C, int DOUT, int TV = 0>
 constexpr size_t smem_floats(int L) {
-  using T = Tile<W, C>;
+  using T = Tile<W, C, TV>;
   return (size_t)2 * W * T::RS + (size_t)W * W + (size_t)2 * DOUT * T::RS + (size_t)T::P * 4 +
          (size_t)W * 4 + W + 4 + (size_t)(L > 1 ? L - 1 : 0) * W;
 }
@@ -594,13 +598,13 @@ __device__ __forceinline__ void point_epilogue(const Shape& sh, const Bufs& b, c
 }
 
 // ------------------------------------------------------ the kernel ---
-template <int W, int DS, int UNST, bool JETS, int MODE, int ACT>
+template <int W, int DS, int UNST, bool JETS, int MODE, int ACT, int TV = 0>
 __global__ void __launch_bounds__(NT, 1)
     k_pinn(const Shape sh, const Bufs b, const Item* __restrict__ items, const int* __restrict__ n_items_ptr) {
   constexpr int DIN = DS + UNST;
   constexpr int C = JETS ? DIN + 2 : 1;
   constexpr int DOUT = DS + 1;
-  using T = Tile<W, C>;
+  using T = Tile<W, C, TV>;
   constexpr int P = T::P, RS = T::RS, TP = T::TP, NCOL = T::NCOL, VEC = T::VEC, PC = T::PC;
   constexpr int TM = T::TM;
   constexpr bool TRAIN = (MODE == M_TRAIN);

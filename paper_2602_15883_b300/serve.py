@@ -3,8 +3,13 @@
 Requests (point clouds of any size, asking for (u, v, [w], p) and optionally
 the Navier-Stokes residuals) arrive at any time.  A dispatcher thread keeps
 ``slots`` batches in flight, each with its own query contexts, pre-allocated
-buffers and two CUDA streams: whenever a slot is free it admits the oldest
-waiting requests that fit the slot and the in-flight memory cap, copies
+buffers and two CUDA streams.  All device memory the server holds - every
+slot's point, value and residual buffers and the routing scratch of its two
+query contexts - is sized at start-up from the memory cap, so the server
+never holds more than the cap whatever the load; a request larger than a
+slot is split into slot-sized chunks that complete together as one request.
+Whenever a slot is free it admits the oldest waiting requests (or chunks)
+that fit the slot and the in-flight memory budget, copies
 their points into one pinned staging buffer, and issues one host-to-device
 copy, the value launch (requests without residual) with its device-to-host
 copy on a high-priority stream, and the residual launch (jets, several times
@@ -44,6 +49,9 @@ class Request:
     final: bool = False             # its outcome is being delivered: too late to cancel
     out: np.ndarray | None = None   # caller-owned result rows, filled in place
     done: threading.Event = field(default_factory=threading.Event)
+    parent: "Request | None" = None  # a chunk of a request larger than a slot
+    chunks: list = field(default_factory=list)
+    remaining: int = 0
 
     @property
     def n(self) -> int:
@@ -54,6 +62,25 @@ class Request:
         return 1e3 * (self.t_done - self.t_arrival)
 
 
+def slot_bytes_per_point(d_in: int, w_val: int, w_res: int) -> int:
+    """Device bytes per point of one slot's capacity: the points, the value
+    and residual rows, and the routing scratch of the slot's two query
+    contexts (net index and order: two ints per point each, plus at most one
+    32-byte work item per 64 points each)."""
+    return 4 * (d_in + w_val + w_res) + 2 * (8 + 1)
+
+
+ALLOC_GRANULE = 2 << 20   # device allocations are counted rounded up to 2 MiB
+
+
+def slot_fixed_bytes(n_nets: int) -> int:
+    """Device bytes of one slot independent of its capacity: per-net counts,
+    offsets and cursors and one work item per net in each query context, and
+    the rounding of the slot's five device allocations (three buffers, one
+    per query context) up to the allocation granule."""
+    return 2 * (12 * n_nets + 32 * (n_nets + 1) + 8 * 256) + 5 * ALLOC_GRANULE
+
+
 def request_bytes(n: int, d_in: int, width: int) -> int:
     """Device bytes a request holds while in flight: its points, its output
     rows and the routing scratch (net index and order, two ints per point)."""
@@ -62,8 +89,8 @@ def request_bytes(n: int, d_in: int, width: int) -> int:
 
 def plan_batch(pending, max_points: int, budget_left: int, d_in: int, width_of):
     """FIFO admission: the longest prefix of ``pending`` that fits both the
-    slot's point capacity and the remaining memory budget.  A request larger
-    than the slot is never admitted (it is rejected at submission)."""
+    slot's point capacity and the remaining memory budget.  Requests larger
+    than a slot arrive here as slot-sized chunks (split at submission)."""
     take, pts, mem = [], 0, 0
     for r in pending:
         b = request_bytes(r.n, d_in, width_of(r))
@@ -76,7 +103,12 @@ def plan_batch(pending, max_points: int, budget_left: int, d_in: int, width_of):
 
 
 class Server:
-    def __init__(self, handle, slots: int = 4, mem_cap_bytes: int = 8 << 30, max_batch_points: int = 1 << 21):
+    """``mem_cap_bytes`` bounds all device memory the server allocates: the
+    slots' capacity in points is the largest that fits ``slots`` slots under
+    the cap (at most ``max_batch_points`` when given).  ``device_bytes`` is
+    the resulting reservation."""
+
+    def __init__(self, handle, slots: int = 4, mem_cap_bytes: int = 8 << 30, max_batch_points: int | None = 1 << 21):
         import torch
         from .binding import QueryContext
         self.torch = torch
@@ -84,8 +116,14 @@ class Server:
         self.d_in, self.d_out, self.ds = handle.d_in, handle.d_out, handle.d_space
         self.w_val = self.d_out
         self.w_res = self.d_out + self.ds + 1
-        self.max_points = int(max_batch_points)
         self.mem_cap = int(mem_cap_bytes)
+        per_pt = slot_bytes_per_point(self.d_in, self.w_val, self.w_res)
+        fixed = slot_fixed_bytes(handle.n_nets)
+        fit = (self.mem_cap // max(1, slots) - fixed) // per_pt
+        self.max_points = int(min(fit, max_batch_points) if max_batch_points else fit)
+        if self.max_points < 1024:
+            raise ValueError(f"a memory cap of {self.mem_cap} bytes leaves fewer than 1024 points per slot")
+        self.device_bytes = slots * (self.max_points * per_pt + fixed)
         cfg = handle.cfg
         self.lo = np.array([np.float32(cfg["lo"][a]) for a in range(self.d_in)], np.float32)
         self.hi = np.array([np.float32(cfg["hi"][a]) for a in range(self.d_in)], np.float32)
@@ -135,17 +173,48 @@ class Server:
         # The domain is checked on the device while routing; only a batch that
         # reports an outside point is checked request by request on the host
         # (see _complete), which keeps the check off the common path.
-        if r.n > self.max_points:
-            r.error = f"request of {r.n} points exceeds the batch capacity {self.max_points}"
-        if r.error or r.n == 0:
-            r.result = np.zeros((0, self._width(r)), np.float32) if not r.error else None
+        if r.n == 0:
+            r.result = np.zeros((0, self._width(r)), np.float32)
             r.t_done = time.perf_counter()
             r.done.set()
+            return r
+        if r.n > self.max_points:
+            # larger than a slot: slot-sized chunks writing into rows of one
+            # result, queued together; the request completes with its last chunk
+            if r.out is None:
+                r.out = np.empty((r.n, self._width(r)), np.float32)
+            for a in range(0, r.n, self.max_points):
+                b = min(r.n, a + self.max_points)
+                r.chunks.append(Request(pts=r.pts[a:b], want_residual=r.want_residual, t_arrival=r.t_arrival,
+                                        rid=r.rid, out=r.out[a:b], parent=r))
+            r.remaining = len(r.chunks)
+            with self.lock:
+                self.pending.extend(r.chunks)
+                self.lock.notify()
             return r
         with self.lock:
             self.pending.append(r)
             self.lock.notify()
         return r
+
+    def _deliver(self, r: Request):
+        """Completion of a request or chunk (outcome already set; the lock is
+        held): a chunk completes its parent with the last of its chunks."""
+        p = r.parent
+        if p is None:
+            r.done.set()
+            self.completed.append(r)
+            return
+        if r.error and not p.error:
+            p.error = r.error
+        p.remaining -= 1
+        if p.remaining == 0:
+            p.t_done = max(c.t_done for c in p.chunks)
+            p.final = True
+            if not p.error:
+                p.result = p.out
+            p.done.set()
+            self.completed.append(p)
 
     def cancel(self, r: Request) -> bool:
         """Withdraw a request: a waiting one leaves the queue at once; one
@@ -156,6 +225,21 @@ class Server:
             if r.done.is_set() or r.final:
                 return False
             r.cancelled = True
+            if r.chunks:   # every chunk: waiting ones leave the queue, running ones are dropped
+                if all(c.final for c in r.chunks):
+                    r.cancelled = False
+                    return False
+                r.error = "cancelled"
+                for c in r.chunks:
+                    if c.final or c.done.is_set():
+                        continue
+                    c.cancelled = True
+                    if c in self.pending:
+                        self.pending.remove(c)
+                        c.error = "cancelled"
+                        c.t_done = time.perf_counter()
+                        self._deliver(c)
+                return True
             if r in self.pending:
                 self.pending.remove(r)
                 r.error = "cancelled"
@@ -269,7 +353,7 @@ class Server:
                 off = 0
                 for r in b[key_reqs]:
                     with self.lock:   # decided once: a later cancel() returns False
-                        cancelled = r.cancelled
+                        cancelled = r.cancelled or (r.parent is not None and r.parent.cancelled)
                         r.final = True
                     if cancelled:
                         r.error = "cancelled"
@@ -293,10 +377,9 @@ class Server:
                     off += r.n
                     r.t_done = t
                     finished.append(r)
-                for r in finished:
-                    r.done.set()
                 with self.lock:
-                    self.completed.extend(finished)
+                    for r in finished:
+                        self._deliver(r)
                     for r in reversed(retry):
                         self.pending.appendleft(r)
                 b[key_ev] = None

@@ -33,3 +33,10 @@ def test_key_separates_precision_activation_and_build():
     assert k(base) != k(dict(base, activation=1))
     assert k(base) != k(base, "b2")
     assert k(base) == k(dict(base))
+
+
+def test_key_separates_searched_precisions():
+    base = synth.config("beltrami32")
+    k = lambda cfg, precisions=None: autotune.schedule_key(cfg, 262144, 65536, 32, "B300", "b1", precisions)
+    assert k(base, (0, 1)) == k(dict(base, precision=1), (1, 0))   # the handle's own precision is not the key
+    assert k(base, (0, 1)) != k(base) and k(base, (0, 1)) != k(dict(base, precision=1))

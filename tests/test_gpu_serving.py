@@ -63,18 +63,55 @@ def test_alone_equals_in_the_mix_and_matches_oracle():
 
 
 def test_memory_cap_is_respected_and_everything_completes():
-    from paper_2602_15883_b300.serve import request_bytes
-    cap = request_bytes(40000, 4, 8) + 1
-    cfg, pb, d, srv = _server(slots=4, mem_cap=cap)
+    """All device memory the server allocates (every slot's buffers and query
+    contexts, measured by the device's free memory) stays under the cap, with
+    a 1M-point residual request - larger than a slot, so served in chunks -
+    in a mix of others; every result equals the regular query's."""
+    import threading
+    import time
+    import torch
+    from paper_2602_15883_b300.serve import Server
+    Dpinn = _gpu()
+    cfg = synth.config("beltrami32")
+    pb = synth.make_problem(cfg, seed=0, res_counts=[64] * 32, obs_counts=[16] * 32, face_counts=[8] * 72,
+                            bias_std=0.1)
+    d = Dpinn(cfg)
+    d.set_problem(pb)
+    big_pts = synth.query_points(cfg, 1 << 20, seed=40)
+    ref_big = d.query(torch.from_numpy(big_pts).cuda(), want_residual=True).cpu().numpy()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    free0 = torch.cuda.mem_get_info()[0]
+    cap = 96 << 20
+    srv = Server(d, slots=3, mem_cap_bytes=cap, max_batch_points=None).start()
+    assert srv.device_bytes <= cap and srv.max_points < (1 << 20)
+    peak = [0]
+    stop = threading.Event()
+
+    def watch():
+        while not stop.is_set():
+            peak[0] = max(peak[0], free0 - torch.cuda.mem_get_info()[0])
+            time.sleep(0.0005)
+    w = threading.Thread(target=watch)
+    w.start()
     try:
-        reqs = [srv.submit(synth.query_points(cfg, n, seed=n), bool(n % 3 == 0)) for n in
-                [30000, 39000, 1000, 25000, 12000, 40000, 5000]]
-        for r in reqs:
+        mix = [srv.submit(synth.query_points(cfg, n, seed=n), bool(n % 3 == 0)) for n in
+               [30000, 39000, 1000, 25000, 12000, 40000, 5000]]
+        big = srv.submit(big_pts, True)
+        mix += [srv.submit(synth.query_points(cfg, n, seed=n + 1), bool(n % 2)) for n in (3000, 90001, 7)]
+        for r in mix + [big]:
             r.done.wait()
-        assert all(r.error is None and r.result.shape[0] == r.n for r in reqs)
+        assert all(r.error is None and r.result.shape[0] == r.n for r in mix)
+        assert big.error is None and len(big.chunks) >= 4
+        np.testing.assert_array_equal(big.result, ref_big)
+        ref = d.query(torch.from_numpy(mix[1].pts).cuda()).cpu().numpy()
+        np.testing.assert_array_equal(mix[1].result, ref)
         assert 0 < srv.max_in_flight_bytes <= cap
     finally:
+        stop.set()
+        w.join()
         srv.stop()
+    assert 0 < peak[0] <= cap, (peak[0], cap)
 
 
 def test_bad_requests_fail_alone():
@@ -83,12 +120,12 @@ def test_bad_requests_fail_alone():
         bad = synth.query_points(cfg, 100, seed=1)
         bad[5, 0] = 3.0
         r_bad = srv.submit(bad)
-        big = srv.submit(np.zeros(((1 << 18) + 1, 4), np.float32))
+        big = srv.submit(np.zeros(((1 << 18) + 1, 4), np.float32))    # two slot-sized chunks
         good = srv.submit(synth.query_points(cfg, 100, seed=2))
         for r in (r_bad, big, good):
             r.done.wait()
         assert r_bad.error and "outside" in r_bad.error
-        assert big.error and "capacity" in big.error
+        assert big.error is None and big.result.shape == ((1 << 18) + 1, 4) and len(big.chunks) == 2
         assert good.error is None and good.result.shape == (100, 4)
     finally:
         srv.stop()
@@ -131,5 +168,21 @@ def test_caller_buffers_receive_the_same_results():
             srv.submit(pts_v, out=np.zeros((5000, 8), np.float32))   # residual width for a value query
         with pytest.raises(ValueError):
             srv.submit(pts_v, out=np.zeros((5000, 4), np.float64))
+    finally:
+        srv.stop()
+
+
+def test_cancelling_a_chunked_request():
+    cfg, pb, d, srv = _server(slots=1, max_batch=1 << 16)
+    try:
+        first = srv.submit(synth.query_points(cfg, 200000, seed=3), True)   # 4 chunks, the slot stays busy
+        big = srv.submit(synth.query_points(cfg, 300000, seed=6))           # 5 chunks, waiting
+        after = srv.submit(synth.query_points(cfg, 1000, seed=7))
+        assert srv.cancel(big)
+        for r in (first, big, after):
+            r.done.wait()
+        assert big.error == "cancelled" and big.result is None
+        assert first.error is None and first.result.shape == (200000, 8)
+        assert after.error is None and after.result.shape == (1000, 4)
     finally:
         srv.stop()
