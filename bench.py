@@ -353,6 +353,11 @@ def measure(args, workload, precision, rank, world, local, dist, stream, clocks=
     from paper_2602_15883_b300.binding import POINTS_RESIDUAL, Dpinn
     cfg = synth.config(workload)
     pb = synth.make_problem(cfg, seed=args.seed + rank)
+    if args.scale > 1:   # profiling captures only: every point set divided by the factor
+        base = pb
+        pb = synth.make_problem(cfg, seed=args.seed + rank, res_counts=np.maximum(base.res_counts // args.scale, 1),
+                                obs_counts=np.maximum(base.obs_counts // args.scale, 1),
+                                face_counts=np.maximum(base.face_counts // args.scale, 1))
     cfg["device"] = local
     auto = precision == "auto"   # the autotuner picks the arithmetic (width 128: FP32 or 3xTF32)
     if auto and cfg["width"] != 128:
@@ -365,7 +370,7 @@ def measure(args, workload, precision, rank, world, local, dist, stream, clocks=
         from paper_2602_15883_b300 import autotune
         n_val = int(pb.obs_counts.sum() + 2 * pb.face_counts.sum())
         res = autotune.autotune(d, pb.n_res, n_val, reps=3, precisions=(0, 1) if auto else None)
-        schedule = {k: res[k] for k in ("jet_tiles", "val_tiles", "order")}
+        schedule = {k: res.get(k, 0) for k in ("jet_tiles", "val_tiles", "order", "jet_tile", "val_tile")}
         schedule.update(tuned=True, cached=res.get("cached", False), trials=res.get("trials"),
                         jet_tile_options=d.tile_options()[0], val_tile_options=d.tile_options()[1])
         if auto:
@@ -373,10 +378,13 @@ def measure(args, workload, precision, rank, world, local, dist, stream, clocks=
                                       for k, v in res.get("precision_ms", {}).items()}
     elif auto:
         d.set_precision(1)
+    if args.no_autotune and args.tiles and not auto:
+        d.set_tiles(*[int(x) for x in args.tiles.split(",")])
     precision = "tf32x3" if d.get_precision() == 1 else "fp32"
     cfg["precision"] = PRECISIONS[precision]
     schedule["variant"] = precision + (" (autotuned)" if auto and not args.no_autotune else "")
     schedule["tile_points"] = d.get_schedule()["tile_points"]
+    schedule["jet_tile"], schedule["val_tile"] = d.get_tiles()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     d.step(args.warmup, stream)
     d.loss()
@@ -494,7 +502,9 @@ def measure(args, workload, precision, rank, world, local, dist, stream, clocks=
                     "residual_points": pb.n_res, "precision": precision,
                     "obs_points": int(pb.obs_counts.sum()), "face_points": int(pb.face_counts.sum()),
                     "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                    "l2": "flushed between steps (512 MiB write)", "schedule": schedule},
+                    "l2": "flushed between steps (512 MiB write)", "schedule": schedule,
+                    **({"scale": f"1/{args.scale} of every point set (profiling capture, not a bench value)"}
+                       if args.scale > 1 else {})},
          "roofline": roofline, "e2e": e2e, "gpu_launches": d.launches_per_step * args.steps,
          "step_gflop": step_flops(cfg, pb) / 1e9}
     if clocks:
@@ -518,6 +528,10 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the extra measurements (the TF32x3 variant at width 128, the TGV workload)")
     ap.add_argument("--serving-seconds", type=float, default=5.0)
+    ap.add_argument("--tiles", default="",
+                    help="with --no-autotune: register tiles 'jet,val' as indices into the tile options")
+    ap.add_argument("--scale", type=int, default=1,
+                    help="divide every point set by this factor (reduced cases for profiling captures only)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule")
     ap.add_argument("--precision", default="fp32", choices=["auto", "fp32", "tf32x3"],
                     help="hidden-layer contractions of the headline's jet kernel: FP32 FMA (the paper's "

@@ -392,17 +392,21 @@ int dpinn_set_schedule(dpinn_t* h, int jet_tiles, int val_tiles, int order);
 int dpinn_set_precision(dpinn_t* h, int precision);
 int dpinn_get_precision(dpinn_t* h, int* precision);
 
-/* Point tiles of the grouped kernels.  dpinn_tile_options lists the tile
- * sizes (points per tile) available for the jet training kernel and for the
- * value kernels (observation / ghost training and the exchange) of the
- * current precision, default first: up to 2 each (the FP32 kernels are
- * instantiated with a default and an alternate register tile; the
- * tensor-core kernels have one).  dpinn_set_tiles selects them (0 = the
- * default); the work lists and the captured step are rebuilt, results are
- * the same up to float rounding of the gradient sums.  Used by the
- * autotuner.  Errors: INVALID_ARG (a size not offered), CUDA, OOM. */
+/* Register tiles of the grouped kernels.  dpinn_tile_options lists, for the
+ * current precision, the tiles available for the jet training kernel and for
+ * the value kernels (observation / ghost training and the exchange) as their
+ * sizes in points, default first: up to 2 each (the FP32 kernels are
+ * instantiated with a default and an alternate register tile - at width 128
+ * with jets the alternate keeps the 16-point tile with 8 neurons x 1 point
+ * per thread instead of 4 x 2, so two options can have the same size; the
+ * tensor-core kernels have one).  dpinn_set_tiles selects them by index into
+ * those lists (0 = the default); the work lists and the captured step are
+ * rebuilt, results are the same up to float rounding of the gradient sums.
+ * dpinn_get_tiles reports the indices in use.  Used by the autotuner.
+ * Errors: INVALID_ARG (an index not offered), CUDA, OOM. */
 int dpinn_tile_options(dpinn_t* h, int* jet_points, int* n_jet, int* val_points, int* n_val);
-int dpinn_set_tiles(dpinn_t* h, int jet_points, int val_points);
+int dpinn_set_tiles(dpinn_t* h, int jet_tile, int val_tile);
+int dpinn_get_tiles(dpinn_t* h, int* jet_tile, int* val_tile);
 
 /* Current schedule and the tile sizes (points) of the jet and value kernels
  * (tile_points[2]). */

@@ -8,8 +8,8 @@ tuning leaves the state untouched - and the fastest kept):
 1. the arithmetic of the contractions, where the width offers two kernel
    families (width 128: FP32 FFMA or the tcgen05 3xTF32 kernels, which meet
    the same error bounds), when the caller asks for it (``precisions``);
-2. the point tiles of the jet and value kernels of that family (the FP32
-   kernels are instantiated with two register tiles, ``dpinn_tile_options``);
+2. the register tiles of the jet and value kernels of that family (the FP32
+   kernels are instantiated with two each, ``dpinn_tile_options``);
 3. how many tiles a work item holds, which trades load balance (many small
    items finish together) against per-item overhead (the net's small
    tensors, one gradient partial per item to reduce), for the jet and the
@@ -107,7 +107,7 @@ def _apply(handle, c):
     """Set a full candidate (precision, tiles, schedule) on the handle."""
     if "precision" in c and handle.get_precision() != c["precision"]:
         handle.set_precision(c["precision"])
-    handle.set_tiles(c.get("jet_points", 0), c.get("val_points", 0))
+    handle.set_tiles(c.get("jet_tile", 0), c.get("val_tile", 0))
     handle.set_schedule(c["jet_tiles"], c["val_tiles"], c["order"])
 
 
@@ -139,7 +139,7 @@ def autotune(handle, n_res: int, n_val: int, reps: int = 3, use_cache: bool = Tr
             print("autotune", c, f"{ms:.3f} ms")
         return ms
 
-    best = {"precision": handle.get_precision(), "jet_points": 0, "val_points": 0,
+    best = {"precision": handle.get_precision(), "jet_tile": 0, "val_tile": 0,
             "jet_tiles": 0, "val_tiles": 0, "order": 0}
     best_ms = run(best)
     # 1. arithmetic
@@ -150,12 +150,12 @@ def autotune(handle, n_res: int, n_val: int, reps: int = 3, use_cache: bool = Tr
             if ms < best_ms:
                 best, best_ms = c, ms
     _apply(handle, best)
-    # 2. point tiles of the chosen family (all combinations, at most 2 x 2)
+    # 2. register tiles of the chosen family (all combinations, at most 2 x 2)
     jo, vo = handle.tile_options()
-    for j in jo:
-        for v in vo:
-            c = dict(best, jet_points=j, val_points=v)
-            if (j, v) == (jo[0], vo[0]) and best["jet_points"] in (0, jo[0]) and best["val_points"] in (0, vo[0]):
+    for j in range(len(jo)):
+        for v in range(len(vo)):
+            c = dict(best, jet_tile=j, val_tile=v)
+            if c == best:
                 continue   # the default tiles, already timed
             ms = run(c)
             if ms < best_ms:
@@ -174,7 +174,7 @@ def autotune(handle, n_res: int, n_val: int, reps: int = 3, use_cache: bool = Tr
     sched = handle.get_schedule()
     out = dict(best, ms=best_ms, trials=len(trials), tile_points=sched["tile_points"],
                precision_ms={str(c["precision"]): round(m, 4) for c, m in trials
-                             if c.get("jet_points", 0) == 0 and c.get("val_points", 0) == 0
+                             if c.get("jet_tile", 0) == 0 and c.get("val_tile", 0) == 0
                              and c["jet_tiles"] == 0 and c["val_tiles"] == 0 and c["order"] == 0})
     if use_cache:
         store_cache(key, out)

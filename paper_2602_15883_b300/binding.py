@@ -32,6 +32,7 @@ EXPORTS = (
     "dpinn_set_resampling", "dpinn_get_points", "dpinn_set_partial_budget", "dpinn_loss_ext",
     "dpinn_set_points_async", "dpinn_selftest_wait", "dpinn_loss_async", "dpinn_probe_fp32",
     "dpinn_query_jets", "dpinn_set_precision", "dpinn_get_precision", "dpinn_tile_options", "dpinn_set_tiles",
+    "dpinn_get_tiles",
 )
 
 
@@ -94,6 +95,7 @@ def load_library(path: str = LIB_PATH):
         "dpinn_get_precision": ([vp, vp], i32),
         "dpinn_tile_options": ([vp, vp, vp, vp, vp], i32),
         "dpinn_set_tiles": ([vp, i32, i32], i32),
+        "dpinn_get_tiles": ([vp, vp, vp], i32),
         "dpinn_query_status": ([vp, vp], i32),
         "dpinn_get_state": ([vp, vp, vp, vp, vp], i32),
         "dpinn_set_state": ([vp, vp, vp, vp, i64], i32),
@@ -395,8 +397,14 @@ class Dpinn:
         self._check(self.lib.dpinn_tile_options(self.h, jo, C.addressof(nj), vo, C.addressof(nv)))
         return list(jo[:nj.value]), list(vo[:nv.value])
 
-    def set_tiles(self, jet_points=0, val_points=0):
-        self._check(self.lib.dpinn_set_tiles(self.h, int(jet_points), int(val_points)))
+    def set_tiles(self, jet_tile=0, val_tile=0):
+        """Select the register tiles by index into tile_options() (0 = default)."""
+        self._check(self.lib.dpinn_set_tiles(self.h, int(jet_tile), int(val_tile)))
+
+    def get_tiles(self):
+        j, v = C.c_int(), C.c_int()
+        self._check(self.lib.dpinn_get_tiles(self.h, C.addressof(j), C.addressof(v)))
+        return j.value, v.value
 
     def get_precision(self):
         p = C.c_int()

@@ -1335,23 +1335,27 @@ int dpinn_tile_options(dpinn_t* h, int* jet_points, int* n_jet, int* val_points,
   return DPINN_OK;
 }
 
-int dpinn_set_tiles(dpinn_t* h, int jet_points, int val_points) {
+int dpinn_set_tiles(dpinn_t* h, int jet_tile, int val_tile) {
   if (!h) return DPINN_ERR_INVALID_ARG;
   int jo[2], vo[2], nj = 0, nv = 0;
   dpinn_tile_options(h, jo, &nj, vo, &nv);
-  int tj = -1, tv = -1;
-  for (int i = 0; i < nj; ++i)
-    if (jet_points == 0 || jet_points == jo[i]) { tj = jet_points == 0 ? 0 : i; break; }
-  for (int i = 0; i < nv; ++i)
-    if (val_points == 0 || val_points == vo[i]) { tv = val_points == 0 ? 0 : i; break; }
-  if (tj < 0 || tv < 0) return fail(h, DPINN_ERR_INVALID_ARG, "tile size not available (see dpinn_tile_options)");
+  if (jet_tile < 0 || jet_tile >= nj || val_tile < 0 || val_tile >= nv)
+    return fail(h, DPINN_ERR_INVALID_ARG, "tile index not available (see dpinn_tile_options)");
   if (h->cfg.precision == DPINN_PREC_TF32X3) return DPINN_OK;   // one tile per tensor-core kernel
-  if (tj == h->tile_jet && tv == h->tile_val) return DPINN_OK;
+  if (jet_tile == h->tile_jet && val_tile == h->tile_val) return DPINN_OK;
   CK(h, cudaDeviceSynchronize());
-  h->tile_jet = tj;
-  h->tile_val = tv;
+  h->tile_jet = jet_tile;
+  h->tile_val = val_tile;
   if (int rc = select_kernels(h, h->cfg.precision)) return rc;
   return build_plan(h);
+}
+
+int dpinn_get_tiles(dpinn_t* h, int* jet_tile, int* val_tile) {
+  if (!h || !jet_tile || !val_tile) return DPINN_ERR_INVALID_ARG;
+  const bool tc = h->cfg.precision == DPINN_PREC_TF32X3;
+  *jet_tile = tc ? 0 : h->tile_jet;
+  *val_tile = tc ? 0 : h->tile_val;
+  return DPINN_OK;
 }
 
 int dpinn_get_precision(dpinn_t* h, int* precision) {

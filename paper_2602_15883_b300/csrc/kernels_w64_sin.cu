@@ -21,13 +21,13 @@ KernelSet make_set(int L) {
   k.P_val = Tile<W, 1>::P;
   k.stash_jet = (long long)L * Tile<W, CJ>::NQ * NT * 4;
   k.stash_val = (long long)L * Tile<W, 1>::NQ * NT * 4;
-  if constexpr (Tile<W, CJ, 1>::P != Tile<W, CJ>::P) {
+  if constexpr (Tile<W, CJ, 1>::P != Tile<W, CJ>::P || Tile<W, CJ, 1>::TM != Tile<W, CJ>::TM) {
     k.train_jet_alt = (const void*)k_pinn<W, DS, UNST, true, M_TRAIN, ACT, 1>;
     k.smem_jet_alt = smem_floats<W, CJ, DOUT, 1>(L) * sizeof(float);
     k.P_jet_alt = Tile<W, CJ, 1>::P;
     k.stash_jet_alt = (long long)L * Tile<W, CJ, 1>::NQ * NT * 4;
   }
-  if constexpr (Tile<W, 1, 1>::P != Tile<W, 1>::P) {
+  if constexpr (Tile<W, 1, 1>::P != Tile<W, 1>::P || Tile<W, 1, 1>::TM != Tile<W, 1>::TM) {
     k.train_val_alt = (const void*)k_pinn<W, DS, UNST, false, M_TRAIN, ACT, 1>;
     k.eval_val_alt = (const void*)k_pinn<W, DS, UNST, false, M_EVAL, ACT, 1>;
     k.smem_val_alt = smem_floats<W, 1, DOUT, 1>(L) * sizeof(float);

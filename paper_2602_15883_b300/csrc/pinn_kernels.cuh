@@ -103,18 +103,22 @@ struct Bufs {
 // thread for values: 256-point value tiles, measured 11 % faster than 128 on
 // the TGV value and exchange items); W = 128 is held to 4 neurons by the
 // shared-memory capacity of its activation buffers.
-// TV selects the point tile: 0 the default, 1 an alternate with fewer points
-// per thread (half the tile, or the same where the default is already one
-// point per thread); the autotuner times both.
+// TV selects the register tile: 0 the default, 1 an alternate - at width 128
+// with jets 8 neurons x 1 point per thread (the same 16-point tile, half the
+// points per thread, twice the neurons), elsewhere half the points per thread
+// (a tile of half the points).  The autotuner times both.
 template <int W, int C, int TV = 0>
 struct Tile {
-  static constexpr int TM = (W == 64) ? 8 : 4;    // neurons per thread
+  static constexpr bool WIDE_TM = (W == 64) || (W == 128 && TV == 1 && C > 1);
+  static constexpr int TM = WIDE_TM ? 8 : 4;      // neurons per thread
   static constexpr int NG = W / TM;               // neuron groups
   static constexpr int PG = NT / NG;              // point groups
   static constexpr int TP0 = (W == 128) ? (C == 1 ? 8 : (C == 4 ? 4 : 2))
                            : (W == 64) ? (C == 1 ? 8 : (C == 6 ? 1 : 2))
                            : 2;
-  static constexpr int TP = (TV == 0 || TP0 == 1) ? TP0 : TP0 / 2;   // points per thread
+  static constexpr int TP = (TV == 0) ? TP0
+                          : (W == 128 && C > 1) ? 1
+                          : (TP0 == 1 ? TP0 : TP0 / 2);   // points per thread
   static constexpr int P = PG * TP;               // points per tile
   static constexpr int NCOL = TP * C;             // columns per thread
   static constexpr int PC = P * C;
@@ -125,8 +129,8 @@ struct Tile {
   // shared-memory phase store (8 rows apart when TM = 8).  Chosen with a
   // wavefront model of every access pattern of the kernel.
   static constexpr int RS0 = ((PC + 27) / 32) * 32 + 4;
-  static constexpr int SK = (W == 64) ? ((C == 1 || C == 4) ? 4 : 8) : 0;
-  static constexpr int SKM = (W == 64) ? ((C == 1 || C == 4) ? 2 : 4) : 1;
+  static constexpr int SK = WIDE_TM ? ((C == 1 || C == 4) ? 4 : 8) : 0;
+  static constexpr int SKM = WIDE_TM ? ((C == 1 || C == 4) ? 2 : 4) : 1;
   static constexpr int RS = (RS0 >= PC + SK * (SKM - 1)) ? RS0 : RS0 + 32 * ((PC + SK * (SKM - 1) - RS0 + 31) / 32);
   __host__ __device__ static constexpr int row(int i) { return i * RS + SK * ((i / TM) % SKM); }
   static constexpr int NQ = TM * NCOL / 4;        // stashed float4 per thread per layer

@@ -43,10 +43,11 @@ def test_every_tile_option_matches_oracle(name):
         assert d.get_precision() == p
         jo, vo = d.tile_options()
         assert 1 <= len(jo) <= 2 and 1 <= len(vo) <= 2
-        for j in jo:
-            for v in vo:
+        for j in range(len(jo)):
+            for v in range(len(vo)):
                 d.set_tiles(j, v)
-                assert tuple(d.get_schedule()["tile_points"]) == (j, v)
+                assert d.get_tiles() == ((j, v) if p == 0 else (0, 0))
+                assert tuple(d.get_schedule()["tile_points"]) == (jo[j], vo[v])
                 _check(d, ref)
                 seen += 1
     assert seen >= 1
@@ -59,7 +60,7 @@ def test_tile_and_precision_errors():
     d.set_problem(pb)
     from paper_2602_15883_b300.binding import DpinnError
     with pytest.raises(DpinnError):
-        d.set_tiles(7, 0)          # not an offered size
+        d.set_tiles(2, 0)          # not an offered tile
     with pytest.raises(DpinnError):
         d.set_precision(1)         # tensor-core kernels need width 128
     assert d.get_precision() == 0
@@ -81,6 +82,7 @@ def test_autotuner_picks_variant_and_tiles_and_keeps_parity(tmp_path, monkeypatc
     assert set(res["precision_ms"]) == {"0", "1"}
     assert d.get_precision() == res["precision"]
     assert tuple(d.get_schedule()["tile_points"]) == tuple(res["tile_points"])
+    assert d.get_tiles() == ((res["jet_tile"], res["val_tile"]) if res["precision"] == 0 else (0, 0))
     _check(d, _oracle(cfg, pb))
     # a fresh handle takes the cached choice
     d2 = Dpinn(cfg)

@@ -104,8 +104,9 @@ def test_memory_cap_is_respected_and_everything_completes():
         assert all(r.error is None and r.result.shape[0] == r.n for r in mix)
         assert big.error is None and len(big.chunks) >= 4
         np.testing.assert_array_equal(big.result, ref_big)
-        ref = d.query(torch.from_numpy(mix[1].pts).cuda()).cpu().numpy()
-        np.testing.assert_array_equal(mix[1].result, ref)
+        for r in mix[:2]:
+            ref = d.query(torch.from_numpy(r.pts).cuda(), want_residual=r.want_residual).cpu().numpy()
+            np.testing.assert_array_equal(r.result, ref)
         assert 0 < srv.max_in_flight_bytes <= cap
     finally:
         stop.set()
