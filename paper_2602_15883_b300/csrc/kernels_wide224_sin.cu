@@ -21,6 +21,15 @@ KernelSet make_set(int L) {
   k.P_val = WideTile<WP, 1>::P;
   k.stash_jet = (long long)L * WideTile<WP, CJ>::NQ * NTW;
   k.stash_val = (long long)L * WideTile<WP, 1>::NQ * NTW;
+  k.train_jet_alt = (const void*)k_pinn_w<WP, DS, UNST, true, M_TRAIN, ACT, 1>;
+  k.smem_jet_alt = smem_floats_wide<WP, CJ, DOUT, 1>(L) * sizeof(float);
+  k.P_jet_alt = WideTile<WP, CJ, 1>::P;
+  k.stash_jet_alt = (long long)L * WideTile<WP, CJ, 1>::NQ * NTW;
+  k.train_val_alt = (const void*)k_pinn_w<WP, DS, UNST, false, M_TRAIN, ACT, 1>;
+  k.eval_val_alt = (const void*)k_pinn_w<WP, DS, UNST, false, M_EVAL, ACT, 1>;
+  k.smem_val_alt = smem_floats_wide<WP, 1, DOUT, 1>(L) * sizeof(float);
+  k.P_val_alt = WideTile<WP, 1, 1>::P;
+  k.stash_val_alt = (long long)L * WideTile<WP, 1, 1>::NQ * NTW;
   return k;
 }
 

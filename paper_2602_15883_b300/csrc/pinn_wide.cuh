@@ -24,11 +24,14 @@ constexpr int NTW = 256;   // threads per CTA of the wide kernel
 template <int N> struct IntC { static constexpr int value = N; };   // a block size as a type
 static_assert(NTW == NT, "the block sums and launches assume NT threads");
 
-template <int WP, int C>
+// TV selects the register tile: 0 the default (2 points per warp with jets,
+// 8 with values), 1 an alternate with half of that (1 and 4); the autotuner
+// times both.
+template <int WP, int C, int TV = 0>
 struct WideTile {
   static_assert(WP % 32 == 0, "padded width");
   static constexpr int TMG = WP / 32;                                              // neurons per thread
-  static constexpr int TPG = (C == 1) ? 8 : 2;                                    // points per column group
+  static constexpr int TPG = (C == 1) ? (TV ? 4 : 8) : (TV ? 1 : 2);             // points per column group
   static constexpr int P = 8 * TPG;                                                // points per tile
   static constexpr int NCOL = TPG * C;                                             // columns per thread
   static constexpr int PC = P * C;
@@ -40,9 +43,9 @@ struct WideTile {
   static_assert(STASH_LAYER_BYTES % 128 == 0, "stash blocks are whole 128-byte lines");
 };
 
-template <int WP, int C, int DOUT>
+template <int WP, int C, int DOUT, int TV = 0>
 constexpr size_t smem_floats_wide(int L) {
-  using T = WideTile<WP, C>;
+  using T = WideTile<WP, C, TV>;
   return (size_t)2 * WP * T::RS + (size_t)2 * T::KC * WP + (size_t)2 * DOUT * T::RS + (size_t)T::P * 4 +
          (size_t)WP * 4 + WP + 4 + (size_t)(L > 1 ? L - 1 : 0) * WP;
 }
@@ -90,10 +93,10 @@ __device__ __forceinline__ void wide_chunk_issue(float* dst, const float* __rest
 // acc[m][j] += sum_{k < K} M[k][lane + 32 m] * X[k * RS + col0 + j], M a
 // row-major K x ncols matrix in global memory streamed in chunks of KC rows.
 // Ends with a barrier (the buffers and X may be rewritten afterwards).
-template <int WP, int C, int NCOL>
+template <int WP, int C, int NCOL, int TV>
 __device__ __forceinline__ void wide_contract(float (&acc)[WP / 32][NCOL], const float* __restrict__ M, int K,
                                               int ncols, float* wch, const float* X, int col0) {
-  using T = WideTile<WP, C>;
+  using T = WideTile<WP, C, TV>;
   constexpr int KC = T::KC, TMG = T::TMG, RS = T::RS;
   const int lane = threadIdx.x & 31;
   const int nch = (K + KC - 1) / KC;
@@ -141,13 +144,13 @@ __device__ __forceinline__ void wide_contract(float (&acc)[WP / 32][NCOL], const
   }
 }
 
-template <int WP, int DS, int UNST, bool JETS, int MODE, int ACT>
+template <int WP, int DS, int UNST, bool JETS, int MODE, int ACT, int TV = 0>
 __global__ void __launch_bounds__(NTW, 1)
     k_pinn_w(const Shape sh, const Bufs b, const Item* __restrict__ items, const int* __restrict__ n_items_ptr) {
   constexpr int DIN = DS + UNST;
   constexpr int C = JETS ? DIN + 2 : 1;
   constexpr int DOUT = DS + 1;
-  using T = WideTile<WP, C>;
+  using T = WideTile<WP, C, TV>;
   constexpr int P = T::P, RS = T::RS, TPG = T::TPG, NCOL = T::NCOL, PC = T::PC, TMG = T::TMG, KC = T::KC;
   constexpr bool TRAIN = (MODE == M_TRAIN);
 
@@ -310,7 +313,7 @@ __global__ void __launch_bounds__(NTW, 1)
         for (int l = 1; l < L; ++l) {
           float z[TMG][NCOL];
           zero_acc(z);
-          wide_contract<WP, C, NCOL>(z, thT + (size_t)(l - 1) * W * W, W, W, wch, cur, col0);
+          wide_contract<WP, C, NCOL, TV>(z, thT + (size_t)(l - 1) * W * W, W, W, wch, cur, col0);
 #pragma unroll
           for (int m = 0; m < TMG; ++m)
 #pragma unroll
@@ -499,7 +502,7 @@ __global__ void __launch_bounds__(NTW, 1)
         stash_ld(l - 1, z);
         float a[TMG][NCOL];
         zero_acc(a);
-        wide_contract<WP, C, NCOL>(a, th + sh.woff[l], W, W, wch, zb, col0);
+        wide_contract<WP, C, NCOL, TV>(a, th + sh.woff[l], W, W, wch, zb, col0);
         stash_discard(l);   // last read in the layer above, before this contraction's barriers
 #pragma unroll
         for (int m = 0; m < TMG; ++m) {

@@ -13,7 +13,7 @@ from tests.test_gpu_parity import GRAD_TOL, LOSS_TOL, _gpu, compare_losses, smal
 pytestmark = pytest.mark.gpu
 
 SHAPES = ["kovasznay", "tgv", "unsteady3d_w32", "unsteady3d_w64", "steady3d_w64", "beltrami32", "beltrami128",
-          "unsteady2d_w128_deep", "tgv_sin", "cyl2d_w150"]
+          "unsteady2d_w128_deep", "tgv_sin", "cyl2d_w150", "cyl3d_w200"]
 
 
 def _oracle(cfg, pb):
