@@ -328,13 +328,15 @@ __device__ __forceinline__ void sts_vec(float* p, const float* x) {
 
 // acc[m][j] += sum_k Ws[k][n0 + m] * Xs[k][col0 + j],  m < TM, j < NCOL.
 // Ws rows have stride ws, row k of Xs starts at rowx(k) (multiples of 4).
-template <int TM, int NCOL, int VEC, class RowX>
+// The k loop is unrolled UNR deep so that the shared loads of later k steps
+// issue under the FMAs of earlier ones.  Measured (jet training kernel, no
+// spills at any depth): width 128 (beltrami128) 131.6 / 126.9 / 123.1 /
+// 120.8 ms at depths 2 / 4 / 8 / 16; width 64 (TGV) 3.64 / 3.61 / 3.60 /
+// 3.63 ms.  The kernel takes 16 at width 128 and 8 below.
+template <int TM, int NCOL, int VEC, int UNR, class RowX>
 __device__ __forceinline__ void contract(float (&acc)[TM][NCOL], const float* __restrict__ Ws, int ws, int n0,
                                          const float* __restrict__ Xs, RowX rowx, int col0, int K) {
-  // unrolled 4 deep: the shared loads of later k steps issue under the FMAs
-  // of earlier ones (measured against 2 deep: beltrami128 jet kernel 131.6 ->
-  // 126.9 ms, TGV 3.64 -> 3.61 ms; no spills at either width)
-#pragma unroll 4
+#pragma unroll UNR
   for (int k = 0; k < K; ++k) {
     float w[TM];
     lds_vec<TM, 4>(w, Ws + k * ws + n0);
@@ -362,10 +364,10 @@ __device__ __forceinline__ void contract(float (&acc)[TM][NCOL], const float* __
 }
 
 // contract() over the k-range [k0, k1) only.
-template <int TM, int NCOL, int VEC, class RowX>
+template <int TM, int NCOL, int VEC, int UNR, class RowX>
 __device__ __forceinline__ void contract_range(float (&acc)[TM][NCOL], const float* __restrict__ Ws, int ws, int n0,
                                                const float* __restrict__ Xs, RowX rowx, int col0, int k0, int k1) {
-  contract<TM, NCOL, VEC>(acc, Ws + k0 * ws, ws, n0, Xs, [&](int k) { return rowx(k + k0); }, col0, k1 - k0);
+  contract<TM, NCOL, VEC, UNR>(acc, Ws + k0 * ws, ws, n0, Xs, [&](int k) { return rowx(k + k0); }, col0, k1 - k0);
 }
 
 // Deterministic block sum of one float per thread (fixed tree order).
@@ -614,6 +616,7 @@ __global__ void __launch_bounds__(NT, 1)
   using T = Tile<W, C, TV>;
   constexpr int P = T::P, RS = T::RS, TP = T::TP, NCOL = T::NCOL, VEC = T::VEC, PC = T::PC;
   constexpr int TM = T::TM;
+  constexpr int KU = (W >= 128) ? 16 : 8;   // unroll depth of the contractions' k loops
   constexpr bool TRAIN = (MODE == M_TRAIN);
 
   extern __shared__ float4 sm4[];
@@ -786,7 +789,7 @@ __global__ void __launch_bounds__(NT, 1)
           for (int m = 0; m < TM; ++m)
 #pragma unroll
             for (int j = 0; j < NCOL; ++j) z[m][j] = 0.f;
-          contract<TM, NCOL, VEC>(z, wbuf, W, n0, cur, ROW, col0, W);
+          contract<TM, NCOL, VEC, KU>(z, wbuf, W, n0, cur, ROW, col0, W);
 #pragma unroll
           for (int m = 0; m < TM; ++m)
 #pragma unroll
@@ -891,7 +894,7 @@ __global__ void __launch_bounds__(NT, 1)
         for (int m = 0; m < TM; ++m)
 #pragma unroll
           for (int j = 0; j < NCOL; ++j) a[m][j] = 0.f;
-        contract<TM, NCOL, VEC>(a, wbuf, W, n0, ybsm, ROW, col0, DOUT);
+        contract<TM, NCOL, VEC, KU>(a, wbuf, W, n0, ybsm, ROW, col0, DOUT);
         __syncthreads();
         if (t == 0 && L >= 2) bulk_load(wbuf, th + sh.woff[L - 1], W * W * 4, &mbar);
         float z[TM][NCOL];
@@ -993,7 +996,7 @@ __global__ void __launch_bounds__(NT, 1)
           constexpr int NCH = 8, NEH = (NE + NCH - 1) / NCH;
 #pragma unroll
           for (int ch = 0; ch < NCH; ++ch) {
-            contract_range<TM, NCOL, VEC>(a, wbuf, W, n0, zb, ROW, col0, ch * (W / NCH), (ch + 1) * (W / NCH));
+            contract_range<TM, NCOL, VEC, KU>(a, wbuf, W, n0, zb, ROW, col0, ch * (W / NCH), (ch + 1) * (W / NCH));
 #pragma unroll
             for (int q = 0; q < NEH; ++q) {
               const int i = ch * NEH + q;
