@@ -342,14 +342,13 @@ __global__ void __launch_bounds__(NTC, 1)
   };
   // M x N result (main + corrections) of the thread's points
   auto ld_result = [&](float (&r)[C][HP]) {
+    float v[C][4], x[C][4];   // channel c: columns c P + p0 .. + 3 of each accumulator
+    tc::ld4_rows<C>(tm + lrow + TD + (uint32_t)p0, (uint32_t)P, v);
+    tc::ld4_rows<C>(tm + lrow + TG + (uint32_t)p0, (uint32_t)P, x);
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
-      float v[4], x[4];
-      tc::ld4(tm + lrow + TD + (uint32_t)(c * P + p0), v);
-      tc::ld4(tm + lrow + TG + (uint32_t)(c * P + p0), x);
+    for (int c = 0; c < C; ++c)
 #pragma unroll
-      for (int u = 0; u < HP; ++u) r[c][u] = v[u] + x[u];
-    }
+      for (int u = 0; u < HP; ++u) r[c][u] = v[c][u] + x[c][u];
   };
 
   for (;;) {
@@ -624,8 +623,8 @@ __global__ void __launch_bounds__(NTC, 1)
 #pragma unroll
           for (int h2 = 0; h2 < 2; ++h2) {
             float v[16], x[16];
-            tc::ld16(tm + lrow + TG + (uint32_t)(hq * KQ + h2 * 16), v);
-            tc::ld16(tm + lrow + TD + (uint32_t)(hq * KQ + h2 * 16), x);
+            tc::ld16_pair(tm + lrow + TG + (uint32_t)(hq * KQ + h2 * 16), tm + lrow + TD + (uint32_t)(hq * KQ + h2 * 16),
+                          v, x);
 #pragma unroll
             for (int j = 0; j < 4; ++j)
               q[h2 * 4 + j] = make_float4(v[4 * j] + x[4 * j], v[4 * j + 1] + x[4 * j + 1], v[4 * j + 2] + x[4 * j + 2],

@@ -204,8 +204,7 @@ __global__ void __launch_bounds__(NTC, 1)
   };
   auto ld_result = [&](float (&r)[HP]) {
     float v[16], x[16];
-    tc::ld16(tm + lrow + TD + (uint32_t)p0, v);
-    tc::ld16(tm + lrow + TG + (uint32_t)p0, x);
+    tc::ld16_pair(tm + lrow + TD + (uint32_t)p0, tm + lrow + TG + (uint32_t)p0, v, x);
 #pragma unroll
     for (int u = 0; u < HP; ++u) r[u] = v[u] + x[u];
   };
@@ -457,8 +456,8 @@ __global__ void __launch_bounds__(NTC, 1)
 #pragma unroll
           for (int h2 = 0; h2 < 2; ++h2) {
             float v[16], x[16];
-            tc::ld16(tm + lrow + TG + (uint32_t)(hq * KQ + h2 * 16), v);
-            tc::ld16(tm + lrow + TD + (uint32_t)(hq * KQ + h2 * 16), x);
+            tc::ld16_pair(tm + lrow + TG + (uint32_t)(hq * KQ + h2 * 16), tm + lrow + TD + (uint32_t)(hq * KQ + h2 * 16),
+                          v, x);
 #pragma unroll
             for (int j = 0; j < 4; ++j)
               q[h2 * 4 + j] = make_float4(v[4 * j] + x[4 * j], v[4 * j + 1] + x[4 * j + 1], v[4 * j + 2] + x[4 * j + 2],
