@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(NTC, 1)
   float* const xpart = bLs + 4;           // [NQ][W][8] column-group partial sums
   float* const bls = xpart + NQ * W * 8;  // [L-1][W]
   __shared__ __align__(8) uint64_t mbar;   // MMA completion
+  __shared__ __align__(8) uint64_t dbar;   // drain after a time-out
   __shared__ __align__(8) uint64_t wbar;   // weight staging copies
   __shared__ uint32_t s_tmem;
   __shared__ int s_item, s_abort;
@@ -206,6 +207,7 @@ __global__ void __launch_bounds__(NTC, 1)
 
   if (t == 0) {
     mbar_init(&mbar, 1);
+    mbar_init(&dbar, 1);
     mbar_init(&wbar, 1);
     s_abort = 0;
   }
@@ -709,8 +711,13 @@ __global__ void __launch_bounds__(NTC, 1)
     }
   }   // items
   // drain: after a time-out, give the outstanding MMAs a bounded time before
-  // the tensor memory is released
-  if (t == 0 && s_abort) mbar_wait_ok(&mbar, (phase + 1) & 1);
+  // the tensor memory is released.  The waits skipped after the time-out leave
+  // mbar's parity unknown, so the drain commits to a barrier of its own (a
+  // commit tracks every MMA the thread issued before it).
+  if (t == 0 && s_abort) {
+    tc::commit(&dbar);
+    mbar_wait_ok(&dbar, 0);
+  }
   tc::fence_before();
   __syncthreads();
   tc::fence_after();

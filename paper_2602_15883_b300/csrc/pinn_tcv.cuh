@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(NTC, 1)
   float* const bls = xpart + NQ * W * 8;  // [L-1][W]
   __shared__ __align__(8) uint64_t mbar;
   __shared__ __align__(8) uint64_t wbar;
+  __shared__ __align__(8) uint64_t dbar;   // drain after a time-out
   __shared__ uint32_t s_tmem;
   __shared__ int s_item, s_abort, s_other_master, s_is_time;
   __shared__ float s_red[NTC / 32];
@@ -100,6 +101,7 @@ __global__ void __launch_bounds__(NTC, 1)
   if (t == 0) {
     mbar_init(&mbar, 1);
     mbar_init(&wbar, 1);
+    mbar_init(&dbar, 1);
     s_abort = 0;
   }
   if (warp == 0) tc::alloc(&s_tmem, TCOLS);
@@ -531,7 +533,12 @@ __global__ void __launch_bounds__(NTC, 1)
       }
     }
   }   // items
-  if (t == 0 && s_abort) mbar_wait_ok(&mbar, (phase + 1) & 1);
+  // drain after a time-out: mbar's parity is unknown once waits were skipped,
+  // so a commit to a barrier of its own tracks every MMA issued before it
+  if (t == 0 && s_abort) {
+    tc::commit(&dbar);
+    mbar_wait_ok(&dbar, 0);
+  }
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
