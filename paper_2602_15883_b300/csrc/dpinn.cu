@@ -648,7 +648,7 @@ int copy_state_out(dpinn* h, float* dst, const float* src) {
 
 int refresh_transpose(dpinn* h) {
   if (h->L < 2) return DPINN_OK;
-  const int nblk = ((h->L - 1) * h->W * h->W + dk::NT - 1) / dk::NT;
+  const int nblk = (h->nTp + dk::NT - 1) / dk::NT;
   dk::k_transpose<<<dim3(nblk, h->n_nets), dk::NT>>>(h->shape, h->theta.p, h->thetaT.p);
   CK(h, cudaGetLastError());
   CK(h, cudaDeviceSynchronize());
@@ -885,7 +885,10 @@ int dpinn_create(const dpinn_config* cfg, dpinn_t** out) {
   if (c.precision == DPINN_PREC_TF32X3)
     for (int l = 1; l < h->L; ++l)
       if (sh.woff[l] % 4 != 0) return fail(nullptr, DPINN_ERR_INVALID_ARG, "weight-gradient tile not 16-byte aligned");
-  h->nTp = std::max(1, (h->L - 1) * h->W * h->W);
+  // widths 129-224 run the streamed-weight kernels (padded to 160 or 224),
+  // whose hidden weights are kept in their own lane-blocked layout
+  sh.twp = (h->W > 128) ? (h->W <= 160 ? 160 : 224) : 0;
+  h->nTp = std::max(1, sh.twp ? (h->L - 1) * 2 * h->W * sh.twp : (h->L - 1) * h->W * h->W);
   sh.npp = h->npp; sh.nTp = h->nTp;
   sh.act = (c.activation == DPINN_ACT_SIN) ? dk::ACT_SIN : dk::ACT_TANH;
   sh.nu = (float)c.nu; sh.p_ref = (float)c.p_ref;

@@ -90,19 +90,38 @@ __global__ void k_adam(const Shape sh, AdamArgs ar, float* __restrict__ theta, f
   for (int l = 1; l < sh.L; ++l) {
     if (j >= sh.woff[l] && j < sh.boff[l]) {
       const int r = j - sh.woff[l], i = r / W, c = r % W;
-      thetaT[(size_t)k * sh.nTp + (size_t)(l - 1) * W * W + (size_t)c * W + i] = th;
+      if (sh.twp == 0) {
+        thetaT[(size_t)k * sh.nTp + (size_t)(l - 1) * W * W + (size_t)c * W + i] = th;
+      } else {   // streamed-weight layout: forward block row c, reverse block row i
+        float* const tl = thetaT + (size_t)k * sh.nTp + (size_t)(l - 1) * 2 * W * sh.twp;
+        tl[(size_t)c * sh.twp + wide_pos(i, sh.twp)] = th;
+        tl[(size_t)(W + i) * sh.twp + wide_pos(c, sh.twp)] = th;
+      }
     }
   }
 }
 
 // Rebuild the transposed hidden weights from theta (after set_state/init).
+// The streamed-weight layout is written whole, its padded entries as zeros
+// (k_adam rewrites only the others).
 __global__ void k_transpose(const Shape sh, const float* __restrict__ theta, float* __restrict__ thetaT) {
   const int k = blockIdx.y;
   const int W = sh.W;
   const int e = blockIdx.x * NT + threadIdx.x;
-  if (e >= (sh.L - 1) * W * W) return;
-  const int l = 1 + e / (W * W), r = e % (W * W), i = r / W, c = r % W;
-  thetaT[(size_t)k * sh.nTp + (size_t)(l - 1) * W * W + (size_t)c * W + i] = theta[(size_t)k * sh.npp + sh.woff[l] + r];
+  const float* const th = theta + (size_t)k * sh.npp;
+  if (sh.twp == 0) {
+    if (e >= (sh.L - 1) * W * W) return;
+    const int l = 1 + e / (W * W), r = e % (W * W), i = r / W, c = r % W;
+    thetaT[(size_t)k * sh.nTp + (size_t)(l - 1) * W * W + (size_t)c * W + i] = th[sh.woff[l] + r];
+  } else {
+    const int WP = sh.twp;
+    if (e >= (sh.L - 1) * 2 * W * WP) return;
+    const int l = 1 + e / (2 * W * WP), r = e % (2 * W * WP), row = r / WP, n = r % WP;
+    float v = 0.f;
+    if (n < W) v = (row < W) ? th[sh.woff[l] + n * W + row]           // forward: W_l^T[row][n]
+                             : th[sh.woff[l] + (row - W) * W + n];    // reverse: W_l[row - W][n]
+    thetaT[(size_t)k * sh.nTp + (size_t)(l - 1) * 2 * W * WP + (size_t)row * WP + wide_pos(n, WP)] = v;
+  }
 }
 
 // Loss record per net: fixed-order sum of the item partials, 1/N factors,

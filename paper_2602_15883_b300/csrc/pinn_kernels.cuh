@@ -43,6 +43,9 @@ struct Shape {
   int ds, unst, din, dout, W, L;
   int npp;                     // padded per-net parameter stride (floats)
   int nTp;                     // per-net stride of the transposed hidden weights
+  int twp;                     // 0: thetaT holds W_l^T (W x W); > 0: the streamed-weight layout of
+                               // padded width twp (wide_pos below), a forward block W_l^T and a
+                               // reverse block W_l per hidden layer, each W rows of twp floats
   int woff[MAXL + 1], boff[MAXL + 1];
   int act;                     // ACT_TANH or ACT_SIN
   float nu, p_ref;
@@ -55,6 +58,20 @@ struct Shape {
 // loss numerators per work item: obs, PDE, gh_u, gh_p space, gh_p time,
 // gh_r (residual matching), gh_c1 (first-derivative matching)
 constexpr int LP = 7;
+
+// Column position of neuron n in a row of the streamed-weight layout of
+// padded width WP (a multiple of 32).  Lane l of a warp owns the neurons
+// l + 32 m, m < WP / 32; the row holds them lane-blocked so that a lane reads
+// its neurons' entries with vector loads: m = 4a + r (a < WP / 128) at
+// 128 a + 4 l + r (float4 groups), the next two m (if there are two left) at
+// a float2 block of 64, the last odd m at a block of 32.  A bijection of
+// [0, WP).
+__host__ __device__ constexpr int wide_pos(int n, int WP) {
+  const int m = n >> 5, l = n & 31, tmg = WP / 32, g4 = tmg / 4, rem = tmg - 4 * g4;
+  if (m < 4 * g4) return (m >> 2) * 128 + l * 4 + (m & 3);
+  if (rem >= 2 && m < 4 * g4 + 2) return g4 * 128 + l * 2 + (m - 4 * g4);
+  return g4 * 128 + (rem >= 2 ? 64 : 0) + l;
+}
 
 struct NetInfo {
   float center[4], scale[4];

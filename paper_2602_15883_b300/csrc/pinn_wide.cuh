@@ -9,7 +9,11 @@
 //   * a W x W weight matrix does not fit in shared memory next to the
 //     activations (200 x 200 fp32 = 160 KB), so it is streamed through two
 //     buffers of 32 rows (16 above width 160) with cp.async while the
-//     previous chunk is contracted;
+//     previous chunk is contracted.  The streamed copies (W_l^T for the
+//     forward product, W_l for the adjoint one) are kept per step in a
+//     padded, lane-blocked column order (wide_pos): a chunk is one
+//     contiguous run of 16-byte pieces, and a lane reads its TMG weights of
+//     a row with float4 / float2 loads;
 //   * the weight gradient is accumulated per block of 8 output neurons per
 //     warp (4 for the last rows) and added to the item's slot with
 //     coalesced L2 reductions (lanes = input neurons).
@@ -68,43 +72,51 @@ __device__ __forceinline__ void wide_l2_discard(const void* p) {
   asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
 }
 
-template <int WP, int VW>
-__device__ __forceinline__ void wide_chunk_copy(float* dst, const float* __restrict__ src, int nr, int ncols) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nv = ncols / VW;
-  for (int r = warp; r < nr; r += NTW / 32)
-    for (int v = lane; v < nv; v += 32) cp_async<4 * VW>(dst + r * WP + v * VW, src + (size_t)r * ncols + v * VW);
-}
-
-// Rows [r0, r0 + nr) of a row-major matrix (row length ncols) into a
-// streamed-weight buffer of KC rows x WP columns (columns >= ncols untouched):
-// warp w copies rows w, w + 8, ..., its lanes 16-, 8- or 4-byte pieces (the
-// widest that the row length and the addresses allow).
+// Rows [r0, r0 + nr) of a streamed-weight block (rows of WP floats, 16-byte
+// aligned, contiguous) into a buffer of KC rows: 16-byte pieces, consecutive
+// threads on consecutive pieces.
 template <int WP>
-__device__ __forceinline__ void wide_chunk_issue(float* dst, const float* __restrict__ src, int r0, int nr, int ncols) {
-  const float* s0 = src + (size_t)r0 * ncols;
-  const uintptr_t a = reinterpret_cast<uintptr_t>(s0);
-  if (ncols % 4 == 0 && a % 16 == 0) wide_chunk_copy<WP, 4>(dst, s0, nr, ncols);
-  else if (ncols % 2 == 0 && a % 8 == 0) wide_chunk_copy<WP, 2>(dst, s0, nr, ncols);
-  else wide_chunk_copy<WP, 1>(dst, s0, nr, ncols);
+__device__ __forceinline__ void wide_chunk_issue(float* dst, const float* __restrict__ src, int r0, int nr) {
+  static_assert(WP % 4 == 0, "16-byte rows");
+  const float* s0 = src + (size_t)r0 * WP;
+  for (int e = threadIdx.x; e < nr * (WP / 4); e += NTW) cp_async<16>(dst + 4 * e, s0 + 4 * e);
   cp_async_commit();
 }
 
+// The weights of row k of a streamed chunk for the thread's neurons
+// lane + 32 m (the lane-blocked order of wide_pos): float4 groups, then a
+// float2 pair and a single entry as the width requires.
+template <int WP>
+__device__ __forceinline__ void wide_row_weights(const float* row, int lane, float (&w)[WP / 32]) {
+  constexpr int TMG = WP / 32, G4 = TMG / 4, REM = TMG - 4 * G4;
+#pragma unroll
+  for (int a = 0; a < G4; ++a) {
+    const float4 v = *reinterpret_cast<const float4*>(row + a * 128 + lane * 4);
+    w[4 * a] = v.x; w[4 * a + 1] = v.y; w[4 * a + 2] = v.z; w[4 * a + 3] = v.w;
+  }
+  if constexpr (REM >= 2) {
+    const float2 v = *reinterpret_cast<const float2*>(row + G4 * 128 + lane * 2);
+    w[4 * G4] = v.x; w[4 * G4 + 1] = v.y;
+  }
+  if constexpr (REM % 2 == 1) w[TMG - 1] = row[G4 * 128 + (REM >= 2 ? 64 : 0) + lane];
+}
+
 // acc[m][j] += sum_{k < K} M[k][lane + 32 m] * X[k * RS + col0 + j], M a
-// row-major K x ncols matrix in global memory streamed in chunks of KC rows.
-// Ends with a barrier (the buffers and X may be rewritten afterwards).
+// K x WP block of the streamed-weight layout (wide_pos column order, padded
+// neurons zero) in global memory, streamed in chunks of KC rows.  Ends with a
+// barrier (the buffers and X may be rewritten afterwards).
 template <int WP, int C, int NCOL, int TV>
 __device__ __forceinline__ void wide_contract(float (&acc)[WP / 32][NCOL], const float* __restrict__ M, int K,
-                                              int ncols, float* wch, const float* X, int col0) {
+                                              float* wch, const float* X, int col0) {
   using T = WideTile<WP, C, TV>;
   constexpr int KC = T::KC, TMG = T::TMG, RS = T::RS;
   const int lane = threadIdx.x & 31;
   const int nch = (K + KC - 1) / KC;
-  wide_chunk_issue<WP>(wch, M, 0, min(KC, K), ncols);
+  wide_chunk_issue<WP>(wch, M, 0, min(KC, K));
   for (int ch = 0; ch < nch; ++ch) {
     float* const buf = wch + (ch & 1) * KC * WP;
     if (ch + 1 < nch) {
-      wide_chunk_issue<WP>(wch + ((ch + 1) & 1) * KC * WP, M, (ch + 1) * KC, min(KC, K - (ch + 1) * KC), ncols);
+      wide_chunk_issue<WP>(wch + ((ch + 1) & 1) * KC * WP, M, (ch + 1) * KC, min(KC, K - (ch + 1) * KC));
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
@@ -117,8 +129,7 @@ __device__ __forceinline__ void wide_contract(float (&acc)[WP / 32][NCOL], const
 #pragma unroll UNR
     for (int k = 0; k < nk; ++k) {
       float w[TMG];
-#pragma unroll
-      for (int m = 0; m < TMG; ++m) w[m] = buf[k * WP + lane + 32 * m];
+      wide_row_weights<WP>(buf + k * WP, lane, w);
       const float* xr = X + (k0 + k) * RS + col0;
       if constexpr (NCOL % 2 == 0) {
 #pragma unroll
@@ -177,8 +188,8 @@ __global__ void __launch_bounds__(NTW, 1)
   const int n_items = *n_items_ptr;
   if (MODE == M_EVAL && b.comm_interval > 1 && (*b.step % b.comm_interval) != 0) return;
 
-  // padded neurons (>= W) see zero weights and biases, so every value stays finite
-  for (int e = t; e < 2 * KC * WP; e += NTW) wch[e] = 0.f;
+  // padded neurons (>= W) see zero weights (the streamed layout holds zeros
+  // there) and zero biases, so every value stays finite
   for (int e = t; e < WP * 4; e += NTW) w0s[e] = 0.f;
   for (int e = t; e < WP; e += NTW) b0s[e] = 0.f;
   for (int e = t; e < (L - 1) * WP; e += NTW) bls[e] = 0.f;
@@ -313,7 +324,7 @@ __global__ void __launch_bounds__(NTW, 1)
         for (int l = 1; l < L; ++l) {
           float z[TMG][NCOL];
           zero_acc(z);
-          wide_contract<WP, C, NCOL, TV>(z, thT + (size_t)(l - 1) * W * W, W, W, wch, cur, col0);
+          wide_contract<WP, C, NCOL, TV>(z, thT + (size_t)(l - 1) * 2 * W * WP, W, wch, cur, col0);
 #pragma unroll
           for (int m = 0; m < TMG; ++m)
 #pragma unroll
@@ -502,7 +513,7 @@ __global__ void __launch_bounds__(NTW, 1)
         stash_ld(l - 1, z);
         float a[TMG][NCOL];
         zero_acc(a);
-        wide_contract<WP, C, NCOL, TV>(a, th + sh.woff[l], W, W, wch, zb, col0);
+        wide_contract<WP, C, NCOL, TV>(a, thT + (size_t)(l - 1) * 2 * W * WP + (size_t)W * WP, W, wch, zb, col0);
         stash_discard(l);   // last read in the layer above, before this contraction's barriers
 #pragma unroll
         for (int m = 0; m < TMG; ++m) {
