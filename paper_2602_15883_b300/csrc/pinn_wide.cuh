@@ -17,8 +17,10 @@
 //   * the weight gradient is accumulated per block of 8 output neurons per
 //     warp (4 for the last rows) and added to the item's slot with
 //     coalesced L2 reductions (lanes = input neurons).
-// Rows of the activation buffers are 2 (mod 32) floats apart, so the
-// lane-strided 8-byte row loads of the weight gradient are conflict-free.
+// Rows of the activation buffers are 4 (mod 32) floats apart when a warp's
+// columns come in 4-aligned groups (16-byte column accesses), else 2 (mod
+// 32): either way the lane-strided row accesses of the weight gradient and
+// of the activation stores are conflict-free.
 #pragma once
 #include "pinn_kernels.cuh"
 
@@ -39,11 +41,16 @@ struct WideTile {
   static constexpr int P = 8 * TPG;                                                // points per tile
   static constexpr int NCOL = TPG * C;                                             // columns per thread
   static constexpr int PC = P * C;
-  static constexpr int RS = ((PC + 29) / 32) * 32 + 2;                            // row stride, 2 (mod 32)
+  // 16-byte column accesses when a warp's columns are 4-aligned; the row
+  // stride is then 4 (mod 32), else 2 (mod 32), so that lane-strided rows
+  // (32 rows RS apart) read or written 16 (else 8) bytes per lane are
+  // conflict-free
+  static constexpr bool V4 = (NCOL % 4 == 0);
+  static constexpr int RS = V4 ? ((PC + 27) / 32) * 32 + 4 : ((PC + 29) / 32) * 32 + 2;   // row stride
   static constexpr int KC = (WP > 160) ? 16 : 32;                                 // streamed weight rows
   static constexpr int NQ = TMG * NCOL;                                            // stashed floats per thread
   static constexpr uint32_t STASH_LAYER_BYTES = (uint32_t)NQ * NTW * 4;           // one layer of a CTA's stash
-  static_assert(RS >= PC && RS % 2 == 0 && P <= NTW && PC % 2 == 0, "wide tile");
+  static_assert(RS >= PC && RS % 2 == 0 && P <= NTW && PC % 4 == 0, "wide tile");
   static_assert(STASH_LAYER_BYTES % 128 == 0, "stash blocks are whole 128-byte lines");
 };
 
@@ -131,7 +138,23 @@ __device__ __forceinline__ void wide_contract(float (&acc)[WP / 32][NCOL], const
       float w[TMG];
       wide_row_weights<WP>(buf + k * WP, lane, w);
       const float* xr = X + (k0 + k) * RS + col0;
-      if constexpr (NCOL % 2 == 0) {
+      if constexpr (T::V4) {
+#pragma unroll
+        for (int j = 0; j < NCOL; j += 4) {
+          const float4 x = *reinterpret_cast<const float4*>(xr + j);
+#pragma unroll
+          for (int m = 0; m < TMG; ++m) {
+            const float2 r0 = __ffma2_rn(make_float2(w[m], w[m]), make_float2(x.x, x.y),
+                                         make_float2(acc[m][j], acc[m][j + 1]));
+            const float2 r1 = __ffma2_rn(make_float2(w[m], w[m]), make_float2(x.z, x.w),
+                                         make_float2(acc[m][j + 2], acc[m][j + 3]));
+            acc[m][j] = r0.x;
+            acc[m][j + 1] = r0.y;
+            acc[m][j + 2] = r1.x;
+            acc[m][j + 3] = r1.y;
+          }
+        }
+      } else if constexpr (NCOL % 2 == 0) {
 #pragma unroll
         for (int j = 0; j < NCOL; j += 2) {
           const float2 x = *reinterpret_cast<const float2*>(xr + j);
@@ -214,15 +237,24 @@ __global__ void __launch_bounds__(NTW, 1)
 #pragma unroll
       for (int pp = 0; pp < TPG; ++pp) z[m][pp * C] = stash_value<ACT>(z[m][pp * C]);
   };
+  // the thread's NCOL columns of neuron lane + 32 m -> its row of buf
+  auto row_store = [&](float* buf, int m, const float (&a)[NCOL]) {
+    float* row = buf + (lane + 32 * m) * RS + col0;
+    if constexpr (T::V4) {
+#pragma unroll
+      for (int j = 0; j < NCOL; j += 4) *reinterpret_cast<float4*>(row + j) = make_float4(a[j], a[j + 1], a[j + 2], a[j + 3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < NCOL; ++j) row[j] = a[j];
+    }
+  };
   auto act_store = [&](float* buf, const float (&h)[TMG][NCOL]) {
 #pragma unroll
     for (int m = 0; m < TMG; ++m) {
       float a[NCOL];
 #pragma unroll
       for (int pp = 0; pp < TPG; ++pp) act_from_stash<C, DS, DIN, ACT>(&h[m][pp * C], &a[pp * C]);
-      float* row = buf + (lane + 32 * m) * RS + col0;
-#pragma unroll
-      for (int j = 0; j < NCOL; ++j) row[j] = a[j];
+      row_store(buf, m, a);
     }
   };
   auto stash_prefetch = [&](int l) {
@@ -443,9 +475,7 @@ __global__ void __launch_bounds__(NTW, 1)
           float zz[NCOL];
 #pragma unroll
           for (int pp = 0; pp < TPG; ++pp) act_bwd<C, DS, DIN, ACT>(&z[m][pp * C], &a[m][pp * C], &zz[pp * C]);
-          float* row = zb + (lane + 32 * m) * RS + col0;
-#pragma unroll
-          for (int j = 0; j < NCOL; ++j) row[j] = zz[j];
+          row_store(zb, m, zz);
         }
       }
       for (int l = L - 1; l >= 1; --l) {
@@ -458,10 +488,12 @@ __global__ void __launch_bounds__(NTW, 1)
         __syncthreads();
         // dW_l[i][k] += sum_pc Zb[i][pc] A_{l-1}[k][pc]: lanes take the input
         // neurons k = lane + 32 m, warp w the output neurons w + 8 r in blocks
-        // of IB; column pairs in order (a fixed summation order).  Per column
-        // pair a block loads IB broadcast and TMG lane-strided 8-byte rows
-        // (IB + 2 TMG shared-memory wavefronts) for IB TMG packed FMAs: with
-        // IB = 8 that stays under the SM's half a wavefront per packed FMA.
+        // of IB; even and odd columns summed in order apart (a fixed
+        // summation order).  Per column pair a block loads IB broadcast and
+        // TMG lane-strided 8-byte rows (IB + 2 TMG shared-memory wavefronts)
+        // for IB TMG packed FMAs: with IB = 8 that stays under the SM's half a
+        // wavefront per packed FMA; with 16-byte rows (4 columns per step) it
+        // takes half the load instructions for the same sums.
         {
           float* const gw = g + sh.woff[l];
           const int nr = (W + 7) / 8;
@@ -475,16 +507,33 @@ __global__ void __launch_bounds__(NTW, 1)
             int irow[IB];
 #pragma unroll
             for (int q = 0; q < IB; ++q) irow[q] = min(warp + 8 * (r0 + q), WP - 1) * RS;
-            for (int pc = 0; pc < PC; pc += 2) {
-              float2 zv[IB], av[TMG];
+            if constexpr (T::V4) {   // 4 columns per step: 16-byte rows (same per-column order)
+              for (int pc = 0; pc < PC; pc += 4) {
+                float4 zv[IB], av[TMG];
 #pragma unroll
-              for (int q = 0; q < IB; ++q) zv[q] = *reinterpret_cast<const float2*>(zb + irow[q] + pc);
+                for (int q = 0; q < IB; ++q) zv[q] = *reinterpret_cast<const float4*>(zb + irow[q] + pc);
 #pragma unroll
-              for (int m = 0; m < TMG; ++m) av[m] = *reinterpret_cast<const float2*>(ab + (lane + 32 * m) * RS + pc);
+                for (int m = 0; m < TMG; ++m) av[m] = *reinterpret_cast<const float4*>(ab + (lane + 32 * m) * RS + pc);
 #pragma unroll
-              for (int m = 0; m < TMG; ++m)
+                for (int m = 0; m < TMG; ++m)
 #pragma unroll
-                for (int q = 0; q < IB; ++q) acc[m][q] = __ffma2_rn(zv[q], av[m], acc[m][q]);
+                  for (int q = 0; q < IB; ++q) {
+                    acc[m][q] = __ffma2_rn(make_float2(zv[q].x, zv[q].y), make_float2(av[m].x, av[m].y), acc[m][q]);
+                    acc[m][q] = __ffma2_rn(make_float2(zv[q].z, zv[q].w), make_float2(av[m].z, av[m].w), acc[m][q]);
+                  }
+              }
+            } else {
+              for (int pc = 0; pc < PC; pc += 2) {
+                float2 zv[IB], av[TMG];
+#pragma unroll
+                for (int q = 0; q < IB; ++q) zv[q] = *reinterpret_cast<const float2*>(zb + irow[q] + pc);
+#pragma unroll
+                for (int m = 0; m < TMG; ++m) av[m] = *reinterpret_cast<const float2*>(ab + (lane + 32 * m) * RS + pc);
+#pragma unroll
+                for (int m = 0; m < TMG; ++m)
+#pragma unroll
+                  for (int q = 0; q < IB; ++q) acc[m][q] = __ffma2_rn(zv[q], av[m], acc[m][q]);
+              }
             }
 #pragma unroll
             for (int q = 0; q < IB; ++q) {
@@ -520,9 +569,7 @@ __global__ void __launch_bounds__(NTW, 1)
           float zz[NCOL];
 #pragma unroll
           for (int pp = 0; pp < TPG; ++pp) act_bwd<C, DS, DIN, ACT>(&z[m][pp * C], &a[m][pp * C], &zz[pp * C]);
-          float* row = zb + (lane + 32 * m) * RS + col0;
-#pragma unroll
-          for (int j = 0; j < NCOL; ++j) row[j] = zz[j];
+          row_store(zb, m, zz);
         }
       }
       __syncthreads();
