@@ -110,8 +110,11 @@ __device__ __forceinline__ void wide_row_weights(const float* row, int lane, flo
 
 // acc[m][j] += sum_{k < K} M[k][lane + 32 m] * X[k * RS + col0 + j], M a
 // K x WP block of the streamed-weight layout (wide_pos column order, padded
-// neurons zero) in global memory, streamed in chunks of KC rows.  Ends with a
-// barrier (the buffers and X may be rewritten afterwards).
+// neurons zero) in global memory, streamed in chunks of KC rows through two
+// buffers.  One barrier per chunk: it makes chunk ch visible and shows that
+// every warp has finished chunk ch - 1, whose buffer then takes chunk ch + 1
+// while chunk ch is contracted.  Ends with a barrier (the buffers and X may
+// be rewritten afterwards).
 template <int WP, int C, int NCOL, int TV>
 __device__ __forceinline__ void wide_contract(float (&acc)[WP / 32][NCOL], const float* __restrict__ M, int K,
                                               float* wch, const float* X, int col0) {
@@ -122,13 +125,10 @@ __device__ __forceinline__ void wide_contract(float (&acc)[WP / 32][NCOL], const
   wide_chunk_issue<WP>(wch, M, 0, min(KC, K));
   for (int ch = 0; ch < nch; ++ch) {
     float* const buf = wch + (ch & 1) * KC * WP;
-    if (ch + 1 < nch) {
-      wide_chunk_issue<WP>(wch + ((ch + 1) & 1) * KC * WP, M, (ch + 1) * KC, min(KC, K - (ch + 1) * KC));
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
+    cp_async_wait<0>();   // the thread's copies of chunk ch
     __syncthreads();
+    if (ch + 1 < nch)
+      wide_chunk_issue<WP>(wch + ((ch + 1) & 1) * KC * WP, M, (ch + 1) * KC, min(KC, K - (ch + 1) * KC));
     const int k0 = ch * KC, nk = min(KC, K - k0);
     // unrolled 8 deep above width 160 (16-row chunks), 4 below (measured:
     // 8 is 2 % faster on 8 x 200 nets and 1.5 % slower on 6 x 150 nets)
@@ -174,8 +174,8 @@ __device__ __forceinline__ void wide_contract(float (&acc)[WP / 32][NCOL], const
         }
       }
     }
-    __syncthreads();
   }
+  __syncthreads();
 }
 
 template <int WP, int DS, int UNST, bool JETS, int MODE, int ACT, int TV = 0>
