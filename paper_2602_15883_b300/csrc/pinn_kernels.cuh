@@ -223,6 +223,24 @@ __device__ __forceinline__ void mbar_wait(uint64_t* bar, uint32_t parity, int* e
   }
 }
 
+// Bounded wait for phase `parity` of `bar` (about 2 s); false on time-out.
+__device__ __forceinline__ bool mbar_wait_ok(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  uint64_t t0 = 0;
+  for (int it = 0;; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (it == 0) t0 = global_ns();
+    else if (global_ns() - t0 > 2000000000ull) return false;
+  }
+}
+
 // ------------------------------------------------------ jet algebra ---
 // Activation jets per neuron, a = sigma(z) with s1, s2, s3 the first three
 // derivatives of sigma:  d_q a = s1 d_q z,  lap a = s2 * sum_{spatial q}

@@ -67,24 +67,6 @@ constexpr size_t tc_smem_bytes(int L) {
 template <int C>
 constexpr long long tc_stash_floats(int L) { return (long long)L * C * NTC * 4; }
 
-// Bounded wait for phase `parity` of `bar` (about 2 s); false on time-out.
-__device__ __forceinline__ bool mbar_wait_ok(uint64_t* bar, uint32_t parity) {
-  const uint32_t a = smem_u32(bar);
-  uint64_t t0 = 0;
-  for (int it = 0;; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (it == 0) t0 = global_ns();
-    else if (global_ns() - t0 > 2000000000ull) return false;
-  }
-}
-
 // A (tmem a_hi / a_lo) * B^T (smem b_hi / b_lo, K-major, 128-byte swizzle,
 // 32-value K blocks blk bytes apart), K = 8 ksteps, 3xTF32: the main products
 // A_hi B_hi accumulate in d, the correction products A_hi B_lo + A_lo B_hi in

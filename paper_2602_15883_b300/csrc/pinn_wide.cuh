@@ -12,8 +12,9 @@
 //     previous chunk is contracted.  The streamed copies (W_l^T for the
 //     forward product, W_l for the adjoint one) are kept per step in a
 //     padded, lane-blocked column order (wide_pos): a chunk is one
-//     contiguous run of 16-byte pieces, and a lane reads its TMG weights of
-//     a row with float4 / float2 loads;
+//     contiguous block, moved by one bulk asynchronous copy (the copy
+//     engine, not the threads) completing on the buffer's mbarrier, and a
+//     lane reads its TMG weights of a row with float4 / float2 loads;
 //   * the weight gradient is accumulated per block of 8 output neurons per
 //     warp (4 for the last rows) and added to the item's slot with
 //     coalesced L2 reductions (lanes = input neurons).
@@ -61,14 +62,6 @@ constexpr size_t smem_floats_wide(int L) {
          (size_t)WP * 4 + WP + 4 + (size_t)(L > 1 ? L - 1 : 0) * WP;
 }
 
-template <int BYTES>
-__device__ __forceinline__ void cp_async(float* dst, const float* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
 // L2 residency of the stash: a block is prefetched into L2 (one bulk
 // prefetch, two reverse layers ahead of its reads) and discarded from L2
 // after its last read (no write-back of dead lines).
@@ -79,15 +72,38 @@ __device__ __forceinline__ void wide_l2_discard(const void* p) {
   asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
 }
 
+// Streaming state of the two weight-chunk buffers.  Buffer b's copies
+// complete on bar[b], one copy outstanding at most (a copy into b is issued
+// only after every thread has waited for b's previous one).  A wait that
+// runs out (about 2 s) records ERR_TIMEOUT and sets *abort: no later copy is
+// issued and no later wait taken, so the kernel ends (with invalid results,
+// which the host reports) instead of spinning.
+struct WStream {
+  uint64_t* bar;        // [2] shared: copy completion per buffer
+  int* abort;           // shared
+  int* err;             // global error words
+  uint32_t waited[2];   // per thread: copies of buffer b waited for
+  uint32_t issued[2];   // thread 0: copies issued into buffer b
+};
+
 // Rows [r0, r0 + nr) of a streamed-weight block (rows of WP floats, 16-byte
-// aligned, contiguous) into a buffer of KC rows: 16-byte pieces, consecutive
-// threads on consecutive pieces.
+// aligned, contiguous) into buffer b: one bulk copy by thread 0.  Every
+// earlier read of the buffer precedes a CTA barrier before the call.
 template <int WP>
-__device__ __forceinline__ void wide_chunk_issue(float* dst, const float* __restrict__ src, int r0, int nr) {
+__device__ __forceinline__ void wide_chunk_issue(WStream& ws, int b, float* dst, const float* __restrict__ src, int r0,
+                                                 int nr) {
   static_assert(WP % 4 == 0, "16-byte rows");
-  const float* s0 = src + (size_t)r0 * WP;
-  for (int e = threadIdx.x; e < nr * (WP / 4); e += NTW) cp_async<16>(dst + 4 * e, s0 + 4 * e);
-  cp_async_commit();
+  if (threadIdx.x == 0 && !*(volatile int*)ws.abort) {
+    bulk_load(dst, src + (size_t)r0 * WP, (uint32_t)(nr * WP * 4), &ws.bar[b]);
+    ++ws.issued[b];
+  }
+}
+__device__ __forceinline__ void wide_chunk_wait(WStream& ws, int b) {
+  if (!*(volatile int*)ws.abort && !mbar_wait_ok(&ws.bar[b], ws.waited[b] & 1)) {
+    *ws.abort = 1;
+    atomicExch(ws.err + ERR_TIMEOUT, 1);
+  }
+  ++ws.waited[b];
 }
 
 // The weights of row k of a streamed chunk for the thread's neurons
@@ -111,30 +127,28 @@ __device__ __forceinline__ void wide_row_weights(const float* row, int lane, flo
 // acc[m][j] += sum_{k < K} M[k][lane + 32 m] * X[k * RS + col0 + j], M a
 // K x WP block of the streamed-weight layout (wide_pos column order, padded
 // neurons zero) in global memory, streamed in chunks of KC rows through two
-// buffers.  One barrier per chunk: it makes chunk ch visible and shows that
-// every warp has finished chunk ch - 1, whose buffer then takes chunk ch + 1
-// while chunk ch is contracted.  Ends with a barrier (the buffers and X may
-// be rewritten afterwards).
+// buffers.  One barrier per chunk, after the wait for its copy: it shows
+// that every warp has finished chunk ch - 1, whose buffer then takes chunk
+// ch + 1 while chunk ch is contracted.  (A second loop of compile-time
+// length for full chunks measured 1-5 % slower in this kernel: code size.)
+// Ends with a barrier (the buffers and X may be rewritten afterwards).
 template <int WP, int C, int NCOL, int TV>
 __device__ __forceinline__ void wide_contract(float (&acc)[WP / 32][NCOL], const float* __restrict__ M, int K,
-                                              float* wch, const float* X, int col0) {
+                                              float* wch, const float* X, int col0, WStream& ws) {
   using T = WideTile<WP, C, TV>;
   constexpr int KC = T::KC, TMG = T::TMG, RS = T::RS;
   const int lane = threadIdx.x & 31;
   const int nch = (K + KC - 1) / KC;
-  wide_chunk_issue<WP>(wch, M, 0, min(KC, K));
+  wide_chunk_issue<WP>(ws, 0, wch, M, 0, min(KC, K));
   for (int ch = 0; ch < nch; ++ch) {
     float* const buf = wch + (ch & 1) * KC * WP;
-    cp_async_wait<0>();   // the thread's copies of chunk ch
+    wide_chunk_wait(ws, ch & 1);
     __syncthreads();
     if (ch + 1 < nch)
-      wide_chunk_issue<WP>(wch + ((ch + 1) & 1) * KC * WP, M, (ch + 1) * KC, min(KC, K - (ch + 1) * KC));
+      wide_chunk_issue<WP>(ws, (ch + 1) & 1, wch + ((ch + 1) & 1) * KC * WP, M, (ch + 1) * KC,
+                           min(KC, K - (ch + 1) * KC));
     const int k0 = ch * KC, nk = min(KC, K - k0);
-    // unrolled 8 deep above width 160 (16-row chunks), 4 below (measured:
-    // 8 is 2 % faster on 8 x 200 nets and 1.5 % slower on 6 x 150 nets)
-    constexpr int UNR = (WP > 160) ? 8 : 4;
-#pragma unroll UNR
-    for (int k = 0; k < nk; ++k) {
+    auto row = [&](int k) {
       float w[TMG];
       wide_row_weights<WP>(buf + k * WP, lane, w);
       const float* xr = X + (k0 + k) * RS + col0;
@@ -173,7 +187,12 @@ __device__ __forceinline__ void wide_contract(float (&acc)[WP / 32][NCOL], const
           for (int m = 0; m < TMG; ++m) acc[m][j] = fmaf(w[m], x, acc[m][j]);
         }
       }
-    }
+    };
+    // unrolled 8 deep above width 160 (16-row chunks), 4 below (measured:
+    // 8 is 2 % faster on 8 x 200 nets and 1.5 % slower on 6 x 150 nets)
+    constexpr int UNR = (WP > 160) ? 8 : 4;
+#pragma unroll UNR
+    for (int k = 0; k < nk; ++k) row(k);
   }
   __syncthreads();
 }
@@ -204,6 +223,8 @@ __global__ void __launch_bounds__(NTW, 1)
   __shared__ float s_red[NTW / 32];
   __shared__ float s_scale[4];
   __shared__ int s_other_master, s_is_time;
+  __shared__ __align__(8) uint64_t s_wbar[2];   // weight-chunk copies
+  __shared__ int s_wabort;
 
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int W = sh.W, L = sh.L;
@@ -211,6 +232,12 @@ __global__ void __launch_bounds__(NTW, 1)
   const int n_items = *n_items_ptr;
   if (MODE == M_EVAL && b.comm_interval > 1 && (*b.step % b.comm_interval) != 0) return;
 
+  if (t == 0) {
+    mbar_init(&s_wbar[0], 1);
+    mbar_init(&s_wbar[1], 1);
+    s_wabort = 0;
+  }
+  WStream ws{s_wbar, &s_wabort, b.err, {0u, 0u}, {0u, 0u}};
   // padded neurons (>= W) see zero weights (the streamed layout holds zeros
   // there) and zero biases, so every value stays finite
   for (int e = t; e < WP * 4; e += NTW) w0s[e] = 0.f;
@@ -356,7 +383,7 @@ __global__ void __launch_bounds__(NTW, 1)
         for (int l = 1; l < L; ++l) {
           float z[TMG][NCOL];
           zero_acc(z);
-          wide_contract<WP, C, NCOL, TV>(z, thT + (size_t)(l - 1) * 2 * W * WP, W, wch, cur, col0);
+          wide_contract<WP, C, NCOL, TV>(z, thT + (size_t)(l - 1) * 2 * W * WP, W, wch, cur, col0, ws);
 #pragma unroll
           for (int m = 0; m < TMG; ++m)
 #pragma unroll
@@ -546,9 +573,17 @@ __global__ void __launch_bounds__(NTW, 1)
               }
             }
           };
+          // blocks of 8 rows and a tail of 4, or, for 16-byte rows and a row
+          // count that 5 divides (25 at width 200), blocks of 5: no padded
+          // row and still compute-bound (measured 3 % faster on 8 x 200 nets;
+          // other splits into 5-8 rows measured slower on 6 x 150 nets)
           int r0 = 0;
-          for (; r0 + 8 <= nr; r0 += 8) dw_block(IntC<8>(), r0);
-          for (; r0 < nr; r0 += 4) dw_block(IntC<4>(), r0);
+          if (T::V4 && nr % 5 == 0) {
+            for (; r0 < nr; r0 += 5) dw_block(IntC<5>(), r0);
+          } else {
+            for (; r0 + 8 <= nr; r0 += 8) dw_block(IntC<8>(), r0);
+            for (; r0 < nr; r0 += 4) dw_block(IntC<4>(), r0);
+          }
         }
         for (int e = t; e < W; e += NTW) {
           float s = 0.f;
@@ -562,7 +597,7 @@ __global__ void __launch_bounds__(NTW, 1)
         stash_ld(l - 1, z);
         float a[TMG][NCOL];
         zero_acc(a);
-        wide_contract<WP, C, NCOL, TV>(a, thT + (size_t)(l - 1) * 2 * W * WP + (size_t)W * WP, W, wch, zb, col0);
+        wide_contract<WP, C, NCOL, TV>(a, thT + (size_t)(l - 1) * 2 * W * WP + (size_t)W * WP, W, wch, zb, col0, ws);
         stash_discard(l);   // last read in the layer above, before this contraction's barriers
 #pragma unroll
         for (int m = 0; m < TMG; ++m) {
@@ -604,6 +639,11 @@ __global__ void __launch_bounds__(NTW, 1)
       }
     }
   }   // items
+  // after a time-out: the last copy issued into each buffer, waited for with
+  // the same bound, before the block's shared memory is released
+  if (t == 0 && s_wabort)
+    for (int q = 0; q < 2; ++q)
+      if (ws.issued[q] > 0) mbar_wait_ok(&s_wbar[q], (ws.issued[q] - 1) & 1);
 }
 
 }  // namespace dk
