@@ -8,8 +8,10 @@ from a truncated power law n^-1.2 on [2,048, 65,536] (about 1.97 M in all),
 2,048 noisy velocity points per net and 1,024 points per shared face (352
 faces); the headline runs the FP32 kernels (the paper's arithmetic).  The
 same line carries the tcgen05 3xTF32 variant of that workload (key
-"tf32x3") and the 32-net Taylor-Green workload (key "tgv") measured the same
-way.  --workload picks another headline configuration.
+"tf32x3"), the 32-net Taylor-Green workload (key "tgv") and the paper's 3-D
+cylinder network shape (key "cylinder3d": 8 nets of 8 x 200 sin, the
+streamed-weight kernel, at most 10 timed steps) measured the same way.
+--workload picks another headline configuration.
 
 Prints one JSON line (rank 0).  `value` is device-timed with CUDA events
 around each step, L2 flushed (a 512 MiB buffer is written) between steps;
@@ -497,7 +499,8 @@ def measure(args, workload, precision, rank, world, local, dist, stream, clocks=
         (e2e_s,) = max_over_ranks(dist, [e2e_s], "cuda")
     e2e = {"value": world * pb.n_res * e2e_steps / e2e_s, "unit": "residual-points/s",
            "h2d_bytes_per_step": int(pinned[0].numel() * 4), "d2h_bytes_per_step": int(out.nbytes)}
-    r = {"value": value, "ms_per_step": step_ms, "dtype": "f32" if precision == "fp32" else "tf32x3",
+    r = {"value": value, "ms_per_step": step_ms, "steps": args.steps,
+         "dtype": "f32" if precision == "fp32" else "tf32x3",
          "config": {"workload": workload, "n_nets": d.n_nets, "width": cfg["width"], "depth": cfg["depth"],
                     "residual_points": pb.n_res, "precision": precision,
                     "obs_points": int(pb.obs_counts.sum()), "face_points": int(pb.face_counts.sum()),
@@ -571,6 +574,12 @@ def main():
                 extras[key] = r
         if args.workload != "tgv":
             extras["tgv"] = measure(args, "tgv", "fp32", rank, world, local, dist, stream, clocks=False)[2]
+        if args.workload != "cylinder3d":
+            # the paper's own 3-D network shape; a step takes about 0.2 s
+            a3 = argparse.Namespace(**vars(args))
+            a3.steps = min(args.steps, 10)
+            extras["cylinder3d"] = measure(a3, "cylinder3d", "fp32", rank, world, local, dist, stream,
+                                           clocks=False)[2]
 
     if rank == 0:
         line = {"metric": METRIC, "value": head["value"], "unit": "residual-points/s", "n_gpus": world,
