@@ -251,9 +251,15 @@ def test_deterministic_bitwise():
     np.testing.assert_array_equal(l1, l2)
 
 
-def test_state_roundtrip_and_resume():
+@pytest.mark.parametrize("name,precision", [("tgv", 0), ("cyl2d_w150", 0), ("cyl3d_w200", 0), ("beltrami32", 1)])
+def test_state_roundtrip_and_resume(name, precision):
+    """Resuming from get_state/set_state equals training on, bit for bit.  The
+    resumed handle's weight copies come from the transpose kernel, the
+    continuing one's from Adam: at widths 129-224 both write the
+    streamed-weight layout, at width 128 (tensor cores) the plain one."""
     Dpinn = _gpu()
-    cfg, pb = small_case("tgv")
+    cfg, pb = small_case(name)
+    cfg = dict(cfg, precision=precision)
     a = Dpinn(cfg)
     a.set_problem(pb)
     a.step(4)
