@@ -181,10 +181,13 @@ def kernel_source_sha256(files):
     return h.hexdigest()
 
 
-def captured_traffic(workload, precision):
+def captured_traffic(workload, precision, scale=1):
     """DRAM bytes (read + write) per launch of the jet kernel from an ncu
-    capture of this workload, or None when there is none or the sources that
-    define the kernel changed since it was taken."""
+    capture of this workload, or None when there is none, the sources that
+    define the kernel changed since it was taken, or the run is a reduced
+    (--scale) case that the capture does not describe."""
+    if scale != 1:
+        return None
     try:
         with open(TRAFFIC_FILE) as fh:
             rec = json.load(fh)
@@ -442,7 +445,7 @@ def measure(args, workload, precision, rank, world, local, dist, stream, clocks=
         probe_tflops = p_flop / (p_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "probe_tflops": probe_tflops, "frac_of_probe": achieved / probe_tflops,
-                    "frac": achieved / peak, "traffic": captured_traffic(workload, "fp32"),
+                    "frac": achieved / peak, "traffic": captured_traffic(workload, "fp32", args.scale),
                     "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                     "kernel": "k_pinn train (jets)" if cfg["width"] in (32, 64, 128) else "k_pinn_w train (jets)",
                     "work_per_launch": f"{flops_per_point(cfg, True)} FLOP per residual point x {pb.n_res} points",
@@ -452,7 +455,7 @@ def measure(args, workload, precision, rank, world, local, dist, stream, clocks=
         peak = tf32_tensor_peak_tflops(pk)
         hidden = 3 * 2 * (synth.d_in(cfg) + 2) * cfg["width"] ** 2 * (cfg["depth"] - 1) * pb.n_res
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": captured_traffic(workload, "tf32x3"),
+                    "frac": achieved / peak, "traffic": captured_traffic(workload, "tf32x3", args.scale),
                     "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                     "kernel": "k_pinn_tc train (jets, tcgen05 3xTF32)",
                     "work_per_launch": f"{flops_per_point(cfg, True)} FLOP per residual point x {pb.n_res} points",
