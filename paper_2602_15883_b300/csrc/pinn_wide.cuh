@@ -8,16 +8,17 @@
 //     group), so the activation jets of a (neuron, point) stay in one thread;
 //   * a W x W weight matrix does not fit in shared memory next to the
 //     activations (200 x 200 fp32 = 160 KB), so it is streamed through two
-//     buffers of 32 rows (16 above width 160) with cp.async while the
-//     previous chunk is contracted.  The streamed copies (W_l^T for the
+//     buffers of 32 rows (16 above width 160), the next chunk arriving while
+//     the previous one is contracted.  The streamed copies (W_l^T for the
 //     forward product, W_l for the adjoint one) are kept per step in a
 //     padded, lane-blocked column order (wide_pos): a chunk is one
 //     contiguous block, moved by one bulk asynchronous copy (the copy
 //     engine, not the threads) completing on the buffer's mbarrier, and a
 //     lane reads its TMG weights of a row with float4 / float2 loads;
-//   * the weight gradient is accumulated per block of 8 output neurons per
-//     warp (4 for the last rows) and added to the item's slot with
-//     coalesced L2 reductions (lanes = input neurons).
+//   * the weight gradient is accumulated per block of output neurons per
+//     warp (8, and 4 for the last rows; 5 where that pads no row) and added
+//     to the item's slot with coalesced L2 reductions (lanes = input
+//     neurons).
 // Rows of the activation buffers are 4 (mod 32) floats apart when a warp's
 // columns come in 4-aligned groups (16-byte column accesses), else 2 (mod
 // 32): either way the lane-strided row accesses of the weight gradient and
