@@ -202,6 +202,17 @@ int dpinn_set_points(dpinn_t* h, int kind, const float* pts, const float* vals,
  * up.  Synchronises the device. */
 int dpinn_selftest_wait(dpinn_t* h);
 
+/* Self-test of the sine and cosine that the sin-activation kernels evaluate
+ * (the activation of the paper's cylinder networks; the evaluation itself
+ * has no counterpart in the paper): out[2 i] = sin x[i], out[2 i + 1] =
+ * cos x[i], computed exactly as the kernels do (a Cody-Waite reduction by
+ * pi/2 in three parts and Taylor series on [-pi/4, pi/4]; within a few ulp
+ * for |x| < 6400, NaN for NaN and infinite x).  x: n floats, out: 2 n
+ * floats, both device memory on `device`, owned by the caller.  n = 0 is a
+ * no-op.  Synchronises.  Errors: INVALID_ARG (n < 0, or null pointers with
+ * n > 0), CUDA. */
+int dpinn_selftest_sincos(int device, const float* x, long long n, float* out);
+
 /* Asynchronous upload of the residual points for the next step/* Asynchronous upload of the residual points for the next step (same
  * counts as the current set; other layouts fall back to dpinn_set_points).
  * The host -> device copy runs on an internal stream into a staging buffer,

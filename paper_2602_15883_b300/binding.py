@@ -32,7 +32,7 @@ EXPORTS = (
     "dpinn_set_resampling", "dpinn_get_points", "dpinn_set_partial_budget", "dpinn_loss_ext",
     "dpinn_set_points_async", "dpinn_selftest_wait", "dpinn_loss_async", "dpinn_probe_fp32",
     "dpinn_query_jets", "dpinn_set_precision", "dpinn_get_precision", "dpinn_tile_options", "dpinn_set_tiles",
-    "dpinn_get_tiles",
+    "dpinn_get_tiles", "dpinn_selftest_sincos",
 )
 
 
@@ -119,6 +119,7 @@ def load_library(path: str = LIB_PATH):
         "dpinn_selftest_wait": ([vp], i32),
         "dpinn_loss_async": ([vp, vp, vp], i32),
         "dpinn_probe_fp32": ([i32, i32, i64, vp, vp], i32),
+        "dpinn_selftest_sincos": ([i32, vp, i64, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -166,6 +167,22 @@ def probe_fp32(iters, blocks_per_sm=4, device=0):
     if rc:
         raise DpinnError(rc, "dpinn_probe_fp32 failed")
     return ms.value, flop.value
+
+
+def selftest_sincos(x):
+    """(sin x, cos x) as the sin-activation kernels evaluate them
+    (dpinn_selftest_sincos); x: a float32 CUDA tensor, returns an [n][2]
+    float32 CUDA tensor on the same device."""
+    import torch
+    lib = load_library()
+    x = x.contiguous()
+    assert x.is_cuda and x.dtype == torch.float32
+    out = torch.empty((x.numel(), 2), dtype=torch.float32, device=x.device)
+    rc = lib.dpinn_selftest_sincos(int(x.device.index or 0), C.c_void_p(x.data_ptr()), int(x.numel()),
+                                   C.c_void_p(out.data_ptr()))
+    if rc:
+        raise DpinnError(rc, "dpinn_selftest_sincos failed")
+    return out
 
 
 def _ptr(a):

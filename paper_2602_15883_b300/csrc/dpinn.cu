@@ -1183,6 +1183,16 @@ int dpinn_selftest_wait(dpinn_t* h) {
   return fail(h, DPINN_ERR_STATE, "self-test: a wait that nothing completes returned without a time-out");
 }
 
+int dpinn_selftest_sincos(int device, const float* x, long long n, float* out) {
+  if (n < 0 || (n > 0 && (!x || !out))) return DPINN_ERR_INVALID_ARG;
+  if (n == 0) return DPINN_OK;
+  if (cudaSetDevice(device) != cudaSuccess) return DPINN_ERR_CUDA;
+  const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+  dk::k_selftest_sincos<<<(unsigned)blocks, 256>>>(x, n, out);
+  if (cudaGetLastError() != cudaSuccess) return DPINN_ERR_CUDA;
+  return cudaDeviceSynchronize() == cudaSuccess ? DPINN_OK : DPINN_ERR_CUDA;
+}
+
 int dpinn_set_resampling(dpinn_t* h, const int64_t* counts, int n_counts, uint64_t seed) {
   if (!h) return DPINN_ERR_INVALID_ARG;
   if (!counts) {

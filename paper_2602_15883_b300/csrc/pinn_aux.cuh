@@ -282,6 +282,17 @@ __global__ void k_sample(int din, uint64_t seed, const long long* __restrict__ s
   }
 }
 
+// Self-test of the sin activation's sine and cosine: out[2 i], out[2 i + 1]
+// = sincos_act(x[i]).
+__global__ void k_selftest_sincos(const float* __restrict__ x, long long n, float* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float s, c;
+    sincos_act(x[i], &s, &c);
+    out[2 * i] = s;
+    out[2 * i + 1] = c;
+  }
+}
+
 // Self-test of the bounded device waits: an mbarrier that nothing ever
 // completes.  mbar_wait gives up after about 2 s and raises ERR_TIMEOUT in
 // `err`; the kernel then returns normally.

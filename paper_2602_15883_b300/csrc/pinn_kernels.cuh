@@ -256,13 +256,52 @@ struct ActD {
   float a, s1, s2, s3;
 };
 
+// sin x and cos x for the sin activation.  Every layer of a sin network
+// evaluates both at each neuron and point; the library sincosf, which serves
+// arguments of any magnitude, measured 8-9 % of the streamed-weight jet
+// kernels in code weight alone.  Pre-activations are O(1-10), so a
+// reduction by pi/2 in three parts suffices (the Cody-Waite method, Cody and
+// Waite, "Software Manual for the Elementary Functions", 1980):
+// k = rint(x 2/pi), r = x - k P1 - k P2 - k P3 with P1 + P2 + P3 = pi/2 to
+// 6e-18, P1 and P2 of 12 significant bits (k P1, k P2 exact for |k| < 2^12,
+// |x| < 6400), each step one fused multiply-add; then the Taylor series of
+// sin and cos on |r| <= pi/4, to r^9 and r^10 (truncation below 3e-9
+// relative), and the quadrant k mod 4.  Within a few ulp of sin x, cos x for
+// |x| < 6400 (tested against float64 through dpinn_selftest_sincos); NaN
+// and inf give NaN.
+__device__ __forceinline__ void sincos_act(float x, float* sn, float* cs) {
+  constexpr float TWO_OVER_PI = 0x1.45f306p-1f;
+  constexpr float P1 = 0x1.922p+0f, P2 = -0x1.2aep-18f, P3 = -0x1.de973ep-31f;
+  const float k = rintf(x * TWO_OVER_PI);
+  float r = fmaf(-k, P1, x);
+  r = fmaf(-k, P2, r);
+  r = fmaf(-k, P3, r);
+  const float r2 = r * r;
+  // sin r = r - r^3/3! + r^5/5! - r^7/7! + r^9/9!
+  float ps = fmaf(r2, 1.f / 362880.f, -1.f / 5040.f);
+  ps = fmaf(r2, ps, 1.f / 120.f);
+  ps = fmaf(r2, ps, -1.f / 6.f);
+  const float sr = fmaf(r * r2, ps, r);
+  // cos r = 1 - r^2/2! + r^4/4! - r^6/6! + r^8/8! - r^10/10!
+  float pc = fmaf(r2, -1.f / 3628800.f, 1.f / 40320.f);
+  pc = fmaf(r2, pc, -1.f / 720.f);
+  pc = fmaf(r2, pc, 1.f / 24.f);
+  pc = fmaf(r2, pc, -0.5f);
+  const float cr = fmaf(r2, pc, 1.f);
+  // x = k pi/2 + r: quadrant q = k mod 4 (two's complement keeps k < 0 right)
+  const int q = static_cast<int>(k) & 3;
+  const float s0 = (q & 1) ? cr : sr, c0 = (q & 1) ? sr : cr;
+  *sn = (q & 2) ? -s0 : s0;
+  *cs = ((q + 1) & 2) ? -c0 : c0;
+}
+
 // derivatives from the stashed value channel h0 (a for tanh, z for sin)
 template <int ACT>
 __device__ __forceinline__ ActD act_derivs(float h0) {
   ActD d;
   if constexpr (ACT == ACT_SIN) {
     float sn, cs;
-    sincosf(h0, &sn, &cs);
+    sincos_act(h0, &sn, &cs);
     d.a = sn; d.s1 = cs; d.s2 = -sn; d.s3 = -cs;
   } else {
     d.a = h0;
@@ -284,8 +323,12 @@ __device__ __forceinline__ float stash_value(float z) {
 template <int C, int DS, int DIN, int ACT>
 __device__ __forceinline__ void act_from_stash(const float* h, float* a) {
   if constexpr (C == 1) {
-    if constexpr (ACT == ACT_SIN) a[0] = sinf(h[0]);
-    else a[0] = h[0];
+    if constexpr (ACT == ACT_SIN) {
+      float c;
+      sincos_act(h[0], &a[0], &c);
+    } else {
+      a[0] = h[0];
+    }
   } else {
     const ActD d = act_derivs<ACT>(h[0]);
     a[0] = d.a;
@@ -304,7 +347,10 @@ template <int C, int DS, int DIN, int ACT>
 __device__ __forceinline__ void act_bwd(const float* z, const float* ab, float* zb) {
   if constexpr (C == 1) {
     float s1;
-    if constexpr (ACT == ACT_SIN) s1 = cosf(z[0]);
+    if constexpr (ACT == ACT_SIN) {
+      float sn;
+      sincos_act(z[0], &sn, &s1);
+    }
     else s1 = 1.f - z[0] * z[0];
     zb[0] = ab[0] * s1;
   } else {

@@ -147,8 +147,13 @@ __global__ void __launch_bounds__(NTC, 1)
     }
   };
   auto act = [&](float h) {
-    if constexpr (ACT == ACT_SIN) return sinf(h);
-    else return h;
+    if constexpr (ACT == ACT_SIN) {
+      float sn, cs;
+      sincos_act(h, &sn, &cs);
+      return sn;
+    } else {
+      return h;
+    }
   };
   auto put_row = [&](int u, float v) {   // point p0 + u, neuron nrn -> [n][neuron]
     const int n = p0 + u;
