@@ -805,7 +805,9 @@ __global__ void __launch_bounds__(NT, 1)
     for (int e = t; e < W; e += NT) b0s[e] = th[sh.boff[0] + e];
     for (int e = t; e < (L - 1) * W; e += NT) bls[e] = th[sh.boff[1 + e / W] + e % W];
     if (t < DOUT) bLs[t] = th[sh.boff[L] + t];
-    if (t < 4) s_scale[t] = t < DIN ? ni.scale[t] : 0.f;
+    // scale from global memory: a run-time index into the local copy ni would
+    // move that copy to the stack
+    if (t < 4) s_scale[t] = t < DIN ? b.nets[net].scale[t] : 0.f;
     if (t == 0) {
       if (item.kind == K_FACE) {
         const int other = b.face_info[item.face * 3 + (1 - item.side)];

@@ -350,7 +350,9 @@ __global__ void __launch_bounds__(NTC, 1)
     for (int e = t; e < (L - 1) * W; e += NTC) bls[e] = th[sh.boff[1 + e / W] + e % W];
     for (int e = t; e < DOUT * W; e += NTC) wLs[e] = th[sh.woff[L] + e];
     if (t < DOUT) bLs[t] = th[sh.boff[L] + t];
-    if (t < 4) s_scale[t] = t < DIN ? ni.scale[t] : 0.f;
+    // scale from global memory: a run-time index into the local copy ni would
+    // move that copy to the stack
+    if (t < 4) s_scale[t] = t < DIN ? b.nets[net].scale[t] : 0.f;
     double lsum0 = 0.0;   // thread 0: sum of r^2 over the item
     const int npass = (!TRAIN && ni.master && !b.q_jets) ? 2 : 1;
 

@@ -80,12 +80,14 @@ __device__ __forceinline__ void wide_l2_discard(const void* p) {
 // issued and no later wait taken, so the kernel ends (with invalid results,
 // which the host reports) instead of spinning.
 struct WStream {
-  uint64_t* bar;        // [2] shared: copy completion per buffer
-  int* abort;           // shared
-  int* err;             // global error words
-  uint32_t waited[2];   // per thread: copies of buffer b waited for
-  uint32_t issued[2];   // thread 0: copies issued into buffer b
+  uint64_t* bar;                // [2] shared: copy completion per buffer
+  int* abort;                   // shared
+  int* err;                     // global error words
+  uint32_t waited0, waited1;    // per thread: copies of buffer 0 / 1 waited for
+  uint32_t issued0, issued1;    // thread 0: copies issued into buffer 0 / 1
 };
+// (scalar pairs, not arrays: a run-time buffer index into an array member
+// would move the whole struct to the stack)
 
 // Rows [r0, r0 + nr) of a streamed-weight block (rows of WP floats, 16-byte
 // aligned, contiguous) into buffer b: one bulk copy by thread 0.  Every
@@ -96,15 +98,18 @@ __device__ __forceinline__ void wide_chunk_issue(WStream& ws, int b, float* dst,
   static_assert(WP % 4 == 0, "16-byte rows");
   if (threadIdx.x == 0 && !*(volatile int*)ws.abort) {
     bulk_load(dst, src + (size_t)r0 * WP, (uint32_t)(nr * WP * 4), &ws.bar[b]);
-    ++ws.issued[b];
+    if (b) ++ws.issued1;
+    else ++ws.issued0;
   }
 }
 __device__ __forceinline__ void wide_chunk_wait(WStream& ws, int b) {
-  if (!*(volatile int*)ws.abort && !mbar_wait_ok(&ws.bar[b], ws.waited[b] & 1)) {
+  const uint32_t n = b ? ws.waited1 : ws.waited0;
+  if (!*(volatile int*)ws.abort && !mbar_wait_ok(&ws.bar[b], n & 1)) {
     *ws.abort = 1;
     atomicExch(ws.err + ERR_TIMEOUT, 1);
   }
-  ++ws.waited[b];
+  if (b) ++ws.waited1;
+  else ++ws.waited0;
 }
 
 // The weights of row k of a streamed chunk for the thread's neurons
@@ -238,7 +243,7 @@ __global__ void __launch_bounds__(NTW, 1)
     mbar_init(&s_wbar[1], 1);
     s_wabort = 0;
   }
-  WStream ws{s_wbar, &s_wabort, b.err, {0u, 0u}, {0u, 0u}};
+  WStream ws{s_wbar, &s_wabort, b.err, 0u, 0u, 0u, 0u};
   // padded neurons (>= W) see zero weights (the streamed layout holds zeros
   // there) and zero biases, so every value stays finite
   for (int e = t; e < WP * 4; e += NTW) w0s[e] = 0.f;
@@ -313,7 +318,9 @@ __global__ void __launch_bounds__(NTW, 1)
     for (int e = t; e < W; e += NTW) b0s[e] = th[sh.boff[0] + e];
     for (int e = t; e < (L - 1) * W; e += NTW) bls[(e / W) * WP + e % W] = th[sh.boff[1 + e / W] + e % W];
     if (t < DOUT) bLs[t] = th[sh.boff[L] + t];
-    if (t < 4) s_scale[t] = t < DIN ? ni.scale[t] : 0.f;
+    // scale from global memory: a run-time index into the local copy ni would
+    // move that copy to the stack
+    if (t < 4) s_scale[t] = t < DIN ? b.nets[net].scale[t] : 0.f;
     if (t == 0) {
       if (item.kind == K_FACE) {
         const int other = b.face_info[item.face * 3 + (1 - item.side)];
@@ -642,9 +649,10 @@ __global__ void __launch_bounds__(NTW, 1)
   }   // items
   // after a time-out: the last copy issued into each buffer, waited for with
   // the same bound, before the block's shared memory is released
-  if (t == 0 && s_wabort)
-    for (int q = 0; q < 2; ++q)
-      if (ws.issued[q] > 0) mbar_wait_ok(&s_wbar[q], (ws.issued[q] - 1) & 1);
+  if (t == 0 && s_wabort) {
+    if (ws.issued0 > 0) mbar_wait_ok(&s_wbar[0], (ws.issued0 - 1) & 1);
+    if (ws.issued1 > 0) mbar_wait_ok(&s_wbar[1], (ws.issued1 - 1) & 1);
+  }
 }
 
 }  // namespace dk
