@@ -194,9 +194,9 @@ __device__ __forceinline__ void wide_contract(float (&acc)[WP / 32][NCOL], const
         }
       }
     };
-    // unrolled 8 deep above width 160 (16-row chunks), 4 below (measured:
-    // 8 is 2 % faster on 8 x 200 nets and 1.5 % slower on 6 x 150 nets)
-    constexpr int UNR = (WP > 160) ? 8 : 4;
+    // unrolled 8 deep (measured: at width 224, 16 deep +0.2 %; at width 160,
+    // 4 deep 1.3 % slower once the sin evaluation and stack frames were gone)
+    constexpr int UNR = 8;
 #pragma unroll UNR
     for (int k = 0; k < nk; ++k) row(k);
   }
