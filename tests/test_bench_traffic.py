@@ -14,6 +14,7 @@ def test_traffic_only_for_matching_sources(tmp_path, monkeypatch):
     f.write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(f))
     assert bench.captured_traffic("tgv", "fp32") == 123
+    assert bench.captured_traffic("tgv", "fp32", scale=8) is None   # a reduced profiling run is another workload
     assert bench.captured_traffic("tgv", "tf32x3") is None
     assert bench.captured_traffic("beltrami32", "fp32") is None
     rec["captures"][0]["sources_sha256"] = "0" * 64          # sources changed since the capture
