@@ -15,8 +15,8 @@
 //     contiguous block, moved by one bulk asynchronous copy (the copy
 //     engine, not the threads) completing on the buffer's mbarrier, and a
 //     lane reads its TMG weights of a row with float4 / float2 loads;
-//   * the weight gradient is accumulated per block of output neurons per
-//     warp (8, and 4 for the last rows; 5 where that pads no row) and added
+//   * the weight gradient is accumulated per block of 5-8 output neurons
+//     per warp (sized so that no block pads a row beyond the width) and added
 //     to the item's slot with coalesced L2 reductions (lanes = input
 //     neurons).
 // Rows of the activation buffers are 4 (mod 32) floats apart when a warp's
@@ -581,16 +581,27 @@ __global__ void __launch_bounds__(NTW, 1)
               }
             }
           };
-          // blocks of 8 rows and a tail of 4, or, for 16-byte rows and a row
-          // count that 5 divides (25 at width 200), blocks of 5: no padded
-          // row and still compute-bound (measured 3 % faster on 8 x 200 nets;
-          // other splits into 5-8 rows measured slower on 6 x 150 nets)
-          int r0 = 0;
+          // row blocks that pad no row beyond the width: blocks of 5 for 16-byte
+          // rows and a row count that 5 divides (25 at width 200), else
+          // ceil(nr / 8) blocks of near-equal size, 5-8 rows at these widths
+          // (measured against blocks of 8 and a tail of 4: -3 % at width 200,
+          // -1.1 % at width 150)
           if (T::V4 && nr % 5 == 0) {
-            for (; r0 < nr; r0 += 5) dw_block(IntC<5>(), r0);
+            for (int r0 = 0; r0 < nr; r0 += 5) dw_block(IntC<5>(), r0);
           } else {
-            for (; r0 + 8 <= nr; r0 += 8) dw_block(IntC<8>(), r0);
-            for (; r0 < nr; r0 += 4) dw_block(IntC<4>(), r0);
+            const int nb = (nr + 7) / 8;
+            for (int bi = 0, r0 = 0; bi < nb; ++bi) {
+              const int sz = nr / nb + (bi < nr % nb ? 1 : 0);
+              switch (sz) {
+                case 8: dw_block(IntC<8>(), r0); break;
+                case 7: dw_block(IntC<7>(), r0); break;
+                case 6: dw_block(IntC<6>(), r0); break;
+                case 5: dw_block(IntC<5>(), r0); break;
+                default:   // fewer than 5 rows per block: never at widths 129-224
+                  for (int q = 0; q < sz; ++q) dw_block(IntC<1>(), r0 + q);
+              }
+              r0 += sz;
+            }
           }
         }
         for (int e = t; e < W; e += NTW) {
